@@ -1,0 +1,87 @@
+"""Pins for the update rule (Eq. 13 with Adam) and the batch schedule (Eq. 14)."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as orc
+from synth import recipes as S
+from tests.helpers import simulate
+
+
+def test_adam_first_step_closed_form():
+    # From zero moments, bias correction makes the first step lr * g / (|g| + eps).
+    rng = np.random.default_rng(0)
+    g = rng.normal(size=100) * 10.0 ** rng.uniform(-6, 3, 100)
+    w = np.zeros(100)
+    orc.adam_update(w, g, np.zeros(100), np.zeros(100), 1, 0.1, 0.9, 0.999, 1e-8)
+    np.testing.assert_allclose(w, -0.1 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+
+
+def test_adam_matches_torch_on_complex_and_real():
+    rng = np.random.default_rng(1)
+    w0 = rng.normal(size=(6, 5)) + 1j * rng.normal(size=(6, 5))
+    tw = torch.tensor(w0, dtype=torch.complex128, requires_grad=True)
+    opt = torch.optim.Adam([tw], lr=0.05, betas=(0.9, 0.999), eps=1e-8)
+    w = np.stack([w0.real, w0.imag], -1)
+    m = np.zeros_like(w)
+    v = np.zeros_like(w)
+    for t in range(1, 8):
+        g = rng.normal(size=(6, 5)) + 1j * rng.normal(size=(6, 5))
+        if t == 4:
+            g[:2] = 0.0                       # zero-gradient rows still move by momentum
+        opt.zero_grad()
+        tw.grad = torch.tensor(g, dtype=torch.complex128)
+        opt.step()
+        orc.adam_update(w, np.stack([g.real, g.imag], -1), m, v, t, 0.05, 0.9, 0.999, 1e-8)
+    np.testing.assert_allclose(w[..., 0] + 1j * w[..., 1], tw.detach().numpy(), rtol=1e-13, atol=1e-15)
+
+
+def test_adam_zero_state_zero_gradient_is_noop():
+    w = np.ones(4)
+    orc.adam_update(w, np.zeros(4), np.zeros(4), np.zeros(4), 3, 0.1, 0.9, 0.999, 1e-8)
+    assert np.all(w == 1.0)
+
+
+def test_splitmix64_published_vector(golden_dir):
+    ref = [int(l) for l in open(f"{golden_dir}/splitmix64_seed1234567.txt") if l.strip() and not l.startswith("#")]
+    gen = S.splitmix64(1234567)
+    assert [next(gen) for _ in range(5)] == ref
+
+
+def test_paper_batching_example(golden_dir):
+    lines = [l.split() for l in open(f"{golden_dir}/paper_batching_example.txt") if l.strip() and not l.startswith("#")]
+    order = [int(x) for x in lines[0][1:]]
+    batches = [[int(x) for x in l[1:]] for l in lines if l[0] == "batch"]
+    N, B, K, n = (int(x) for x in [l for l in lines if l[0] == "eq14"][0][1:])
+    assert [list(b) for b in S.chop(order, 3)] == batches
+    # Eq. (14) for a pass of the non-random schedule
+    sched = S.schedule(N, B, epochs=1, seed=0, shuffle=False)
+    assert len(sched) == K
+    counts = np.bincount(np.concatenate(sched), minlength=N)
+    assert np.all(counts == B * K // N) and B * K // N == n
+
+
+@pytest.mark.parametrize("n,B,epochs", [(49, 8, 30), (225, 16, 20), (9, 3, 4), (121, 40, 3)])
+def test_schedule_equal_counts(n, B, epochs):
+    sched = S.schedule(n, B, epochs, seed=123)
+    assert len(sched) == epochs * -(-n // B)
+    counts = np.bincount(np.concatenate(sched), minlength=n)
+    assert np.all(counts == epochs)                # Eq. (14): every image equally often
+    for e in range(epochs):                         # each pass is a permutation
+        per = np.concatenate(sched[e * -(-n // B):(e + 1) * -(-n // B)])
+        assert sorted(per) == list(range(n))
+    assert all(len(set(b)) == len(b) for b in sched)
+    assert S.epoch_permutation(n, 123, 0).tolist() != S.epoch_permutation(n, 123, 1).tolist()
+
+
+def test_oracle_reconstruction_reduces_loss():
+    c = S.config("c1")
+    I, o, g_n, g_t, prm_t = simulate(c)
+    rec = orc.Reconstruction(g_n, I, orc.Hparams(lr=dict(c.lr), learn=c.learn))
+    sched = S.schedule(g_n.n_leds, c.B, 3, c.seed)
+    per_epoch = len(sched) // 3
+    losses = rec.run(sched)
+    e0 = sum(losses[:per_epoch])
+    e2 = sum(losses[-per_epoch:])
+    assert e2 < 0.95 * e0
