@@ -1,0 +1,415 @@
+#!/usr/bin/env python
+"""Benchmark of the Batch-FPM mini-batch step on one or more GB300s.
+
+Workload: the paper-scale multi-parameter reconstruction (1024^2 object
+spectrum, 256^2 low-res images, 15x15 = 225 LEDs, batch 16, object, Zernike
+pupil, defocus, LED intensities and LED offsets all learned), on synthetic
+data shaped like the paper's simulation (Section 3.1).
+
+A step is one pass of the whole hot path over one batch: the fused per-LED
+forward model + adjoint kernel, then the batch-ordered gradient gather with
+Adam. The metric is LED forward+backward updates per second (batch size /
+step time), summed over ranks (one independent job per GPU, weak scaling).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl engine|reference]
+
+Prints one JSON line on rank 0.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LED fwd+bwd updates/s at 1024² ROI, 225 LEDs; %HBM roofline; serve p50/p99 TTC"
+UNIT = "LED-updates/s"
+WORKLOAD = ("c2_multiparam_1024: 1024x1024 object spectrum, 256x256 images, 15x15=225 LEDs "
+            "(pitch 12 px, +-0.5 px jitter), pupil r=50 px + Noll 2..15 aberrations, z=15 um, "
+            "gamma U(0.8,1.2), Poisson 2000/20 photons + read noise 2; batch 16; all parameters learned")
+FLUSH_BYTES = 256 << 20        # > 129 MB L2: cleared before every timed step
+L2_NOTE = "L2 flushed (256 MB device memset) before every timed step"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------
+# workload
+# --------------------------------------------------------------------------
+
+def workload(seed_shift: int = 0):
+    from synth import recipes as S
+    c = S.config("c2")
+    if seed_shift:
+        c = c.with_(seed=c.seed + 1000 * seed_shift)
+    nominal, truth = S.led_grid(c.grid, c.pitch, c.jitter, c.seed)
+    return c, nominal, truth
+
+
+def support_pixels(R: float) -> int:
+    """Lattice points of the anti-aliased pupil support |p| < R + 1/2."""
+    r = int(math.ceil(R + 1))
+    p = np.arange(-r, r + 1)
+    return int(np.sum(np.hypot(p[:, None], p[None, :]) < R + 0.5))
+
+
+def union_pixels(nominal, R: float, N: int) -> int:
+    """|union of LED supports| on the spectrum grid (the region where Adam acts)."""
+    mask = np.zeros((N, N), bool)
+    r = int(math.ceil(R + 1))
+    p = np.arange(-r, r + 1)
+    disk = np.hypot(p[:, None], p[None, :]) < R + 0.5
+    for n in np.rint(nominal).astype(int):
+        y0, x0 = N // 2 + n[0] - r, N // 2 + n[1] - r
+        mask[y0:y0 + 2 * r + 1, x0:x0 + 2 * r + 1] |= disk
+    return int(mask.sum())
+
+
+def make_stack_gpu(c, truth):
+    """Clean intensities from the engine's forward model at the truth, plus the camera noise."""
+    from paper_2408_13782_gb300 import Engine
+    from synth import recipes as S
+    eng = Engine(c.m, c.s, truth, c.R, c.lambda_um, c.dk_per_um, c.edge)
+    eng.set_object_field(S.make_object(c.N, c.seed))
+    eng.set(zernike=S.zernike_coeffs(c.zernike_sigma, c.seed), defocus=c.z_um,
+            gamma=S.led_gamma(c.n_leds, *c.gamma_range, c.seed), offset=truth - np.rint(truth))
+    I = np.concatenate([eng.forward(np.arange(k, min(k + 32, c.n_leds))) for k in range(0, c.n_leds, 32)])
+    eng.close()
+    nominal = S.led_grid(c.grid, c.pitch, c.jitter, c.seed)[0]
+    bright = S.brightfield_mask(nominal, c.R)
+    nz = c.noise
+    return S.add_noise(I, bright, nz["bf_mean"], nz["df_mean"], nz["read_sigma"], c.seed).astype(np.float32)
+
+
+def full_batches(n: int, B: int, n_steps: int, seed: int, first_epoch: int = 0) -> np.ndarray:
+    """n_steps consecutive full batches of the random schedule (Eq. 13-14): each pass
+    is a fresh permutation; its short tail batch is left out of the timed steps."""
+    from synth import recipes as S
+    out, e = [], first_epoch
+    while len(out) < n_steps:
+        perm = S.epoch_permutation(n, seed, e)
+        out.extend(perm[k:k + B] for k in range(0, n - B + 1, B))
+        e += 1
+    return np.stack(out[:n_steps]).astype(np.int32)
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax = float(parts[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, single thread
+# --------------------------------------------------------------------------
+
+def cpu_worker(stack_path: str, sample_s: float, leds_per_step: int, max_steps: int):
+    """Runs oracle steps on the workload (in a child process with 1 BLAS thread)."""
+    import oracle as orc
+    c, nominal, truth = workload()
+    I = np.load(stack_path)
+    g = orc.Geometry(c.N, c.m, nominal, c.R, c.edge, c.lambda_um, c.dk_per_um)
+    rec = orc.Reconstruction(g, I, orc.Hparams(lr=dict(c.lr), learn=c.learn))
+    sched = full_batches(c.n_leds, c.B, max_steps, c.seed)
+    t0 = time.perf_counter()
+    n_led, steps = 0, 0
+    while steps < max_steps:
+        b = sched[steps][:leds_per_step]
+        rec.step(b)
+        n_led += len(b)
+        steps += 1
+        if time.perf_counter() - t0 >= sample_s:
+            break
+    dt = time.perf_counter() - t0
+    print(json.dumps({"updates": n_led, "seconds": dt, "steps": steps}))
+
+
+def run_cpu_child(stack, sample_s: float, leds_per_step: int, max_steps: int):
+    with tempfile.TemporaryDirectory() as d:
+        path = os.path.join(d, "stack.npy")
+        np.save(path, stack)
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                   CUDA_VISIBLE_DEVICES="")
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", path,
+                            "--cpu-sample-s", str(sample_s), "--cpu-leds", str(leds_per_step),
+                            "--cpu-max-steps", str(max_steps)],
+                           capture_output=True, text=True, env=env, timeout=1800)
+        if r.returncode != 0:
+            raise RuntimeError("CPU baseline worker failed:\n" + r.stderr[-2000:])
+        return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+# --------------------------------------------------------------------------
+# distributed helpers (torchrun: one rank per GPU, independent jobs)
+# --------------------------------------------------------------------------
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = os.environ.get("FPM_BENCH_BACKEND", "nccl")
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def barrier(pg, device=None):
+    if pg is not None:
+        if device is not None:
+            pg.barrier(device_ids=[device])
+        else:
+            pg.barrier()
+
+
+def allreduce_max(pg, x: float, device) -> float:
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+# --------------------------------------------------------------------------
+# engine arm
+# --------------------------------------------------------------------------
+
+def engine_arm(args):
+    import torch
+
+    import __graft_entry__
+    from paper_2408_13782_gb300 import Engine
+
+    world, rank, local, pg = dist_setup()
+    assert torch.cuda.is_available(), "the engine arm needs a CUDA GPU"
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    __graft_entry__.build()
+
+    c, nominal, truth = workload(seed_shift=rank)
+    stack = make_stack_gpu(c, truth)
+    eng = Engine(c.m, c.s, nominal, c.R, c.lambda_um, c.dk_per_um, c.edge)
+    eng.set_hparams(lr=dict(c.lr), learn=c.learn)
+    eng.load(stack, init=True)
+    K, W, B = args.steps, args.warmup, c.B
+    sched = full_batches(c.n_leds, B, W + K, c.seed)
+    eng.run(sched[:W], losses=False)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize()
+    barrier(pg, local)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        led_ms, upd_ms, step_ms = eng.profile_run(sched[W:], flush=flush)
+        torch.cuda.synchronize()
+    barrier(pg, local)
+    total_ms = float(np.sum(step_ms))
+    total_ms_max = allreduce_max(pg, total_ms, dev)
+    value = world * K * B / (total_ms_max / 1e3)
+
+    # roofline of the dominant kernel (the fused per-LED kernel)
+    D = support_pixels(c.R)
+    A = union_pixels(nominal, c.R, c.N)
+    led_bytes = B * (4 * c.m * c.m + 16 * D)            # image read + O on support + gradient box
+    step_bytes = B * (4 * c.m * c.m + 24 * D) + 48 * A  # + gradient read and the Adam state of O
+    led_avg_s = float(np.mean(led_ms)) / 1e3
+    peak, peak_kind = _peaks()
+    achieved = led_bytes / led_avg_s / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "led_kernel_traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as fh:
+            traffic = json.load(fh).get("bytes_per_launch")
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": total_ms_max / K, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "global_batch": B * world, "l2": L2_NOTE,
+                   "parallelism": f"independent job per GPU x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "kernel": "led_kernel<256>",
+                     "peak_source": peak_kind, "algorithmic_bytes_per_launch": led_bytes,
+                     "avg_launch_ms": led_avg_s * 1e3},
+        "step_hbm_roofline": {"algorithmic_bytes_per_step": step_bytes,
+                              "achieved_gbs": step_bytes / (total_ms / K / 1e3) / 1e9,
+                              "frac": step_bytes / (total_ms / K / 1e3) / 1e9 / peak},
+        "kernel_ms": {"led_kernel": float(np.mean(led_ms)), "update_kernel": float(np.mean(upd_ms))},
+        "gpu_launches": 2 * K,
+        "clocks": clk.summary(),
+    }
+
+    # end to end through the C ABI with host buffers: a whole job (load, 20 passes, read back)
+    e2e_steps = full_batches(c.n_leds, B, 14 * c.epochs, c.seed)
+    pinned = torch.from_numpy(stack).pin_memory()
+    eng2 = Engine(c.m, c.s, nominal, c.R, c.lambda_um, c.dk_per_um, c.edge)
+    eng2.set_hparams(lr=dict(c.lr), learn=c.learn)
+    eng2.load(pinned, init=True)
+    eng2.run(e2e_steps, losses=True)          # warm: graphs built, caches populated
+    torch.cuda.synchronize()
+    barrier(pg, local)
+    t0 = time.perf_counter()
+    eng2.load(pinned, init=True)
+    losses = eng2.run(e2e_steps, losses=True)
+    out = eng2.get()
+    t1 = time.perf_counter()
+    barrier(pg, local)
+    e2e_s = allreduce_max(pg, t1 - t0, dev)
+    n_e2e = len(e2e_steps)
+    result["e2e"] = {"value": world * n_e2e * B / e2e_s, "unit": UNIT,
+                     "h2d_bytes_per_step": (stack.nbytes + e2e_steps.nbytes + 8) / n_e2e,
+                     "d2h_bytes_per_step": (losses.nbytes + c.N * c.N * 8 + 4 * (15 + 3 * c.n_leds)) / n_e2e,
+                     "what": f"one job of {n_e2e} steps: stack upload from pinned host memory, object "
+                             "initialisation, the steps, per-step losses and the final state read back"}
+    assert np.all(np.isfinite(losses)) and np.isfinite(out["object"]).all()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        r = run_cpu_child(stack, args.cpu_sample_s, B, 10_000)
+        result["cpu_baseline"] = {"value": r["updates"] / r["seconds"], "unit": UNIT, "cores": 1,
+                                  "kind": "oracle",
+                                  "sample": f"{r['steps']} oracle steps of 16 LEDs on this workload "
+                                            f"({r['seconds']:.1f} s, FP64 numpy, 1 thread)"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+# --------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# --------------------------------------------------------------------------
+
+def reference_arm(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle as orc
+    from tests.helpers import simulate
+    c, nominal, truth = workload()
+    I, o, g_n, g_t, prm_t = simulate(c)
+    g = orc.Geometry(c.N, c.m, nominal, c.R, c.edge, c.lambda_um, c.dk_per_um)
+    rec = orc.Reconstruction(g, I, orc.Hparams(lr=dict(c.lr), learn=c.learn))
+    K, W = args.steps, args.warmup
+    sched = full_batches(c.n_leds, c.B, K + W + 1, c.seed)
+    t = time.perf_counter()
+    rec.step(sched[0][:2])
+    per_led = (time.perf_counter() - t) / 2
+    leds = int(max(1, min(c.B, 150.0 / max(1, K + W) / max(per_led, 1e-3))))
+    for k in range(W):
+        rec.step(sched[1 + k][:leds])
+    t0 = time.perf_counter()
+    for k in range(K):
+        rec.step(sched[1 + W + k][:leds])
+    dt = time.perf_counter() - t0
+    value = K * leds / dt
+    cores = 1
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+           "warmup": W, "ms_per_step": dt / K * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "global_batch": c.B,
+                      "sample": f"{leds} of the 16 LEDs of each batch per step"},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                            "sample": f"{K} oracle steps of {leds} LEDs each (FP64 numpy)"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("engine", "reference"), default="engine")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    ap.add_argument("--cpu-worker", default=None)
+    ap.add_argument("--cpu-leds", type=int, default=16)
+    ap.add_argument("--cpu-max-steps", type=int, default=10_000)
+    args = ap.parse_args()
+    if args.cpu_worker:
+        cpu_worker(args.cpu_worker, args.cpu_sample_s, args.cpu_leds, args.cpu_max_steps)
+        return
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        engine_arm(args)
+
+
+if __name__ == "__main__":
+    main()

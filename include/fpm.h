@@ -1,0 +1,202 @@
+/*
+ * fpm.h -- C ABI of the GB300 Batch-FPM engine.
+ *
+ * The engine reconstructs a high-resolution complex object spectrum O (N x N)
+ * from a stack of low-resolution intensity images (one m x m image per LED),
+ * jointly with the pupil aberrations (Zernike coefficients), the defocus
+ * distance z, a per-LED intensity factor gamma_i and a per-LED sub-pixel
+ * spectral offset delta_i, by random mini-batch gradient steps with Adam.
+ * The method is Batch-FPM (Sun et al., arXiv 2408.13782):
+ *   forward model          Section 2.1, Eq. (1)-(3)
+ *       I_i = gamma_i |F^-1( O(k - k_mi) P(k) H(k, z) )|^2
+ *   loss over a batch      Section 2.2, Eq. (5); Eq. (4) for the intensity form
+ *   random batch update    Section 2.3, Eq. (13); equal use per pass, Eq. (14)
+ *   initial object         Section 2.3 (bilinear-interpolated centre image)
+ *
+ * Conventions
+ *   - Complex arrays are interleaved float pairs (re, im), row-major.
+ *   - O is the centred spectrum of the object transmission o(r):
+ *         O = fftshift(fft2(o)) / s^2,  s = N / m,  DC at (N/2, N/2).
+ *   - LED i: crop centred at DC + n_i (n_i = rounded nominal offset), pupil
+ *     evaluated at q = p - delta_i, p in [-m/2, m/2)^2:
+ *         M_i(p) = A(q) exp(i (sum_j c_j Z_j(q/R) + z kappa(q))),
+ *         kappa(q) = 2 pi (sqrt(lambda^-2 - |q dk|^2) - 1/lambda),
+ *         Z_j = Noll-ordered Zernike polynomials j = 2..15 (Noll 1976),
+ *         A = hard circle |q| <= R, or anti-aliased clamp(R + 1/2 - |q|, 0, 1).
+ *       psi_i = ifft2(ifftshift(crop_i(O) * M_i))   (1/m^2 normalised)
+ *       I_i   = gamma_i |psi_i|^2
+ *   - Loss (amplitude form, default):
+ *         L = sum_{i in batch} sum_r (sqrt(gamma_i)|psi_i| - sqrt(max(I_meas,0)))^2
+ *     Intensity form (Eq. 4): L = sum (gamma_i |psi_i|^2 - I_meas)^2.
+ *   - Gradients of real L w.r.t. complex w are dL/dRe w + i dL/dIm w.
+ *   - Adam (Kingma & Ba, bias corrected) per real component of every learnable
+ *     tensor, every step; delta is clamped to +-FPM_OFFSET_BOUND_PX per axis.
+ *
+ * Pointers: any buffer argument may be host memory (pageable or pinned) or
+ * device memory of the engine's device; the direction of each copy is taken
+ * from unified addressing. Buffers are borrowed for the duration of the call
+ * only; the engine owns all of its device state.
+ *
+ * Errors: every int-returning call returns FPM_OK (0) or a negative FPM_ERR_*
+ * code, and fpm_last_error() gives a one-line description. No call throws,
+ * aborts the process or leaves the handle unusable on an argument error.
+ *
+ * Threading: a handle is used by one host thread at a time. All device work
+ * of a handle is ordered on the CUDA stream given to fpm_create.
+ */
+#ifndef FPM_GB300_H
+#define FPM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FPM_OK             0
+#define FPM_ERR_ARG       -1  /* null handle/pointer, bad flag or hyper-parameter */
+#define FPM_ERR_SHAPE     -2  /* unsupported m, upsample, radius, LED geometry or batch size */
+#define FPM_ERR_RANGE     -3  /* batch index outside [0, n_leds) or repeated within a batch */
+#define FPM_ERR_OOM       -4  /* device allocation failed */
+#define FPM_ERR_NONFINITE -5  /* a loss came out NaN or Inf (state may hold non-finite values) */
+#define FPM_ERR_TIMEOUT   -6  /* a bounded device wait gave up */
+#define FPM_ERR_CUDA      -7  /* a CUDA runtime call failed (message in fpm_last_error) */
+#define FPM_ERR_STATE     -8  /* call out of order, e.g. a step before fpm_load */
+
+#define FPM_EDGE_AA        0  /* anti-aliased pupil edge: A = clamp(R + 1/2 - |q|, 0, 1) */
+#define FPM_EDGE_HARD      1  /* hard pupil edge: A = [|q| <= R] */
+
+#define FPM_LOSS_AMPLITUDE 0
+#define FPM_LOSS_INTENSITY 1
+
+#define FPM_LEARN_OBJECT   (1u << 0)
+#define FPM_LEARN_ZERNIKE  (1u << 1)
+#define FPM_LEARN_DEFOCUS  (1u << 2)
+#define FPM_LEARN_GAMMA    (1u << 3)
+#define FPM_LEARN_OFFSET   (1u << 4)
+#define FPM_LEARN_ALL      0x1Fu
+
+#define FPM_PRECISION_FP32_FFT 0  /* hand-written shared-memory FFTs, FP32 */
+
+#define FPM_LOAD_INIT      1  /* fpm_load flag: initialise O from the centre LED and reset parameters and Adam state */
+
+#define FPM_N_ZERNIKE     14  /* Noll j = 2..15 */
+#define FPM_OFFSET_BOUND_PX 1.0f
+
+typedef struct fpm_handle fpm_handle;
+
+/* Imaging geometry (Section 2.1). */
+typedef struct fpm_geometry {
+  int32_t m;                /* low-res image side: 32, 64, 128 or 256 */
+  int32_t n_leds;           /* number of LED images, >= 1 */
+  const float* led_offset;  /* [n_leds][2] (row, col) nominal spectral LED centre in px of the
+                               spectrum grid, relative to DC; host memory. The rounded value is
+                               the crop position n_i, the remainder the initial delta_i. */
+  float lambda_um;          /* wavelength, um */
+  float dk_per_um;          /* spectral bin of both grids, 1/um (= 1 / (m * low-res pixel)) */
+  int32_t pupil_edge;       /* FPM_EDGE_AA or FPM_EDGE_HARD */
+} fpm_geometry;
+
+/* Optimiser and loss settings (Section 2.2: Adam-family optimiser, free loss choice). */
+typedef struct fpm_hparams {
+  float lr_object, lr_zernike, lr_defocus, lr_gamma, lr_offset;
+  float beta1, beta2, eps;
+  int32_t loss;             /* FPM_LOSS_AMPLITUDE or FPM_LOSS_INTENSITY */
+  uint32_t learn_mask;      /* FPM_LEARN_* bits; cleared groups are held fixed */
+  int32_t precision;        /* FPM_PRECISION_FP32_FFT */
+} fpm_hparams;
+
+/* Create an engine for N = m * upsample, pupil radius R (spectral px).
+ * Requires every crop box (half-width floor(R + 1/2 + sqrt(2) * FPM_OFFSET_BOUND_PX) + 1)
+ * to lie inside the N x N spectrum and inside the m x m window.
+ * cuda_stream: a cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream); NULL = default.
+ * Default hyper-parameters: lr 0.1 / 0.01 / 0.1 / 0.01 / 0.01, betas 0.9 / 0.999,
+ * eps 1e-8, amplitude loss, learn object only. On success *out owns device memory
+ * until fpm_destroy. */
+int fpm_create(const fpm_geometry* g, float pupil_radius_px, int32_t upsample,
+               void* cuda_stream, fpm_handle** out);
+
+/* Replace the hyper-parameters. Takes effect at the next step. */
+int fpm_set_hparams(fpm_handle* h, const fpm_hparams* hp);
+int fpm_get_hparams(const fpm_handle* h, fpm_hparams* hp);
+
+/* Copy the measured stack [n_leds][m][m] (intensities, float) into the engine.
+ * With FPM_LOAD_INIT: O <- bilinear upsample (low-res pixel r on high-res pixel s*r,
+ * periodic) of sqrt(max(I_centre, 0)) with zero phase, transformed as above;
+ * centre = LED with the smallest |nominal offset|; zernike = 0, z = 0, gamma = 1,
+ * delta = fractional part of the nominal offsets; Adam moments and step count reset. */
+int fpm_load(fpm_handle* h, const float* stack, int32_t flags);
+
+/* One random-batch update (Eq. 13): loss and gradients over the B LEDs in
+ * batch_idx (host, [B], distinct, in [0, n_leds)), then Adam on every learnable
+ * tensor. The gradient of O is accumulated over the batch in batch order.
+ * loss_out (nullable, host): the batch loss before the update; when non-NULL the
+ * call waits for the step to finish. */
+int fpm_step(fpm_handle* h, const int32_t* batch_idx, int32_t B, double* loss_out);
+
+/* n_steps consecutive updates; schedule is [n_steps][B] (host). Launched as one
+ * CUDA graph per (n_steps, B), reused across calls. losses_out (nullable,
+ * host or device, [n_steps]) receives each batch loss; when it is host memory
+ * the call waits for the run to finish. */
+int fpm_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int32_t B, double* losses_out);
+
+/* Timing variant of fpm_run for profiling: the same steps, captured as one graph,
+ * with, before every step, a clear of flush_bytes of the device buffer `flush`
+ * (nullable: no clear; a buffer larger than the L2 cache evicts the working set so
+ * each step starts cold), and CUDA events on the engine's stream around each step
+ * and each of its two kernels. Outputs (host, [n_steps] each, nullable): elapsed
+ * ms of the per-LED kernel, of the update kernel and of the whole step (excluding
+ * the clear). Waits for completion. The state advances exactly as with fpm_run. */
+int fpm_profile_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int32_t B,
+                    void* flush, int64_t flush_bytes, float* led_ms, float* update_ms, float* step_ms);
+
+/* Sum of the batch losses since the last reset (FP64), optionally resetting it. */
+int fpm_epoch_loss(fpm_handle* h, double* out, int32_t reset);
+
+/* Forward model only: I_out[B][m][m] = gamma_i |psi_i|^2 for the LEDs in idx (host). */
+int fpm_forward(fpm_handle* h, const int32_t* idx, int32_t B, float* I_out);
+
+/* Gradients without an update. dL_dI (nullable, [B][m][m]): upstream gradient of
+ * the predicted intensities; NULL means the built-in loss against the loaded stack.
+ * Outputs (each nullable): g_object [N][N][2], g_zernike [14], g_defocus [1],
+ * g_gamma [n_leds], g_offset [n_leds][2]; LEDs outside idx get 0. loss_out
+ * (nullable): the built-in batch loss (only with dL_dI == NULL). */
+int fpm_backward(fpm_handle* h, const int32_t* idx, int32_t B, const float* dL_dI,
+                 float* g_object, float* g_zernike, float* g_defocus, float* g_gamma,
+                 float* g_offset, double* loss_out);
+
+/* Read / write the current estimate; each pointer nullable (skipped).
+ * O [N][N][2], zernike [14], defocus [1], gamma [n_leds], offset [n_leds][2] (delta). */
+int fpm_get(fpm_handle* h, float* O, float* zernike, float* defocus, float* gamma, float* offset);
+int fpm_set(fpm_handle* h, const float* O, const float* zernike, const float* defocus,
+            const float* gamma, const float* offset);
+
+/* O <- fftshift(fft2(o)) / s^2 for a real-space transmission o [N][N][2]. */
+int fpm_set_object_field(fpm_handle* h, const float* o);
+
+/* Full optimiser state for checkpoint / resume. Sizes in floats: */
+int64_t fpm_state_size(const fpm_handle* h);
+/* Layout: O, m_O, v_O ([N][N][2] each), then params, m_params, v_params
+ * ([15 + 3 n_leds] each: zernike, z, gamma, delta), then {step count, epoch loss}
+ * stored as two float64 in the last four floats. */
+int fpm_get_state(fpm_handle* h, float* state);
+int fpm_set_state(fpm_handle* h, const float* state);
+
+/* Sizes of this handle. */
+int fpm_dims(const fpm_handle* h, int32_t* N, int32_t* m, int32_t* n_leds, int32_t* box);
+
+/* Host-side random batch order (Eq. 13-14): the permutation of range(n) for
+ * pass `epoch`: SplitMix64 (Steele, Lea & Flood 2014) seeded with
+ * seed ^ ((epoch + 1) * 0xA0761D6478BD642F), driving a Durstenfeld shuffle of the
+ * identity (for i = n-1 .. 1: j = next() mod (i + 1); swap). No GPU needed. */
+int fpm_epoch_permutation(int32_t n, uint64_t seed, int32_t epoch, int32_t* out);
+
+void fpm_destroy(fpm_handle* h);
+
+/* Last error message of the handle (or of the last failed fpm_create when h is NULL). */
+const char* fpm_last_error(const fpm_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FPM_GB300_H */

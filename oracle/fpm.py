@@ -27,7 +27,9 @@ Readings where the paper is silent or garbled (each is listed in the design doc):
 * LED geometry: crop at the integer part n_i of the spectral offset, pupil,
   aberration and defocus evaluated at q = p - delta_i (sub-pixel part);
 * loss: amplitude form sum (sqrt(gamma)|psi| - sqrt(max(I_meas, 0)))^2 by
-  default, the intensity form of Eq. (4) as an option; plain sums;
+  default, the intensity form of Eq. (4) as an option; plain sums; a
+  'linear' form sum w I_pred (w given in place of I_meas) states the
+  gradient for an arbitrary upstream dL/dI;
 * psi / |psi| := 0 where psi = 0;
 * initial object: sqrt(max(I_centre, 0)) upsampled bilinearly with low-res
   pixel r on high-res pixel s*r and a periodic boundary, zero phase;
@@ -185,7 +187,7 @@ class Hparams:
     beta1: float = 0.9
     beta2: float = 0.999
     eps: float = 1e-8
-    loss: str = "amplitude"    # 'amplitude' | 'intensity'
+    loss: str = "amplitude"    # 'amplitude' | 'intensity' | 'linear'
     learn: tuple = ("object",)
     offset_bound: float = 1.0
 
@@ -326,6 +328,12 @@ def loss_and_grad(O, prm: Params, geom: Geometry, idx, I_meas, loss: str = "ampl
             Li = float(np.sum(res ** 2))
             g_psi = 4.0 * g * res * psi
             g_gamma[i] += float(np.sum(2.0 * res * mag ** 2))
+        elif loss == "linear":
+            # L = sum_r w(r) I_pred(r) with weights w = I_meas: the pairing of
+            # an upstream gradient dL/dI with the predicted intensities
+            Li = float(np.sum(meas * g * mag ** 2))
+            g_psi = 2.0 * g * meas * psi
+            g_gamma[i] += float(np.sum(meas * mag ** 2))
         else:
             raise ValueError(loss)
         per_led.append(Li)

@@ -1,0 +1,295 @@
+// Device helpers for the Batch-FPM engine (sm_103a): complex arithmetic, the
+// pupil model of Section 2.1 Eq. (3), and a shared-memory Stockham FFT run by
+// a group of M/8 threads, each holding 8 points per pass.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define FPM_HD __host__ __device__ __forceinline__
+#else
+#define FPM_HD inline
+#endif
+
+namespace fpmk {
+
+FPM_HD float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+FPM_HD float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+FPM_HD float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+FPM_HD float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+FPM_HD float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// ---------------------------------------------------------------------------
+// Zernike polynomials j = 2..15 in Noll's ordering and normalisation, written
+// out in Cartesian form on the unit disk (x = rho cos t, y = rho sin t), with
+// their partial derivatives. Index 0 of the arrays is j = 2.
+// ---------------------------------------------------------------------------
+struct Zern {
+  float v[14], dx[14], dy[14];
+};
+
+FPM_HD void zernike_eval(float x, float y, Zern& z) {
+  const float s3 = 1.7320508075688772f, s5 = 2.2360679774997896f, s6 = 2.449489742783178f;
+  const float s8 = 2.8284271247461903f, s10 = 3.1622776601683795f;
+  const float x2 = x * x, y2 = y * y, r2 = x2 + y2, xy = x * y;
+  // j=2,3: tilt
+  z.v[0] = 2.f * x;            z.dx[0] = 2.f;               z.dy[0] = 0.f;
+  z.v[1] = 2.f * y;            z.dx[1] = 0.f;               z.dy[1] = 2.f;
+  // j=4: defocus
+  z.v[2] = s3 * (2.f * r2 - 1.f); z.dx[2] = 4.f * s3 * x;  z.dy[2] = 4.f * s3 * y;
+  // j=5,6: astigmatism
+  z.v[3] = 2.f * s6 * xy;      z.dx[3] = 2.f * s6 * y;      z.dy[3] = 2.f * s6 * x;
+  z.v[4] = s6 * (x2 - y2);     z.dx[4] = 2.f * s6 * x;      z.dy[4] = -2.f * s6 * y;
+  // j=7,8: coma
+  z.v[5] = s8 * (3.f * r2 - 2.f) * y;  z.dx[5] = s8 * 6.f * xy;  z.dy[5] = s8 * (3.f * x2 + 9.f * y2 - 2.f);
+  z.v[6] = s8 * (3.f * r2 - 2.f) * x;  z.dx[6] = s8 * (9.f * x2 + 3.f * y2 - 2.f);  z.dy[6] = s8 * 6.f * xy;
+  // j=9,10: trefoil
+  z.v[7] = s8 * (3.f * x2 * y - y2 * y);  z.dx[7] = s8 * 6.f * xy;  z.dy[7] = s8 * 3.f * (x2 - y2);
+  z.v[8] = s8 * (x2 * x - 3.f * x * y2);  z.dx[8] = s8 * 3.f * (x2 - y2);  z.dy[8] = -s8 * 6.f * xy;
+  // j=11: spherical
+  z.v[9] = s5 * (6.f * r2 * r2 - 6.f * r2 + 1.f);
+  z.dx[9] = s5 * 12.f * x * (2.f * r2 - 1.f);
+  z.dy[9] = s5 * 12.f * y * (2.f * r2 - 1.f);
+  // j=12,13: secondary astigmatism, (4 r^2 - 3) * {x^2 - y^2, 2xy}
+  const float a = 4.f * r2 - 3.f, u = x2 - y2, w = 2.f * xy;
+  z.v[10] = s10 * a * u;  z.dx[10] = s10 * (8.f * x * u + 2.f * a * x);  z.dy[10] = s10 * (8.f * y * u - 2.f * a * y);
+  z.v[11] = s10 * a * w;  z.dx[11] = s10 * (8.f * x * w + 2.f * a * y);  z.dy[11] = s10 * (8.f * y * w + 2.f * a * x);
+  // j=14,15: tetrafoil, Re/Im (x + i y)^4
+  z.v[12] = s10 * (x2 * x2 - 6.f * x2 * y2 + y2 * y2);
+  z.dx[12] = s10 * (4.f * x2 * x - 12.f * x * y2);
+  z.dy[12] = s10 * (4.f * y2 * y - 12.f * x2 * y);
+  z.v[13] = s10 * (4.f * x2 * xy - 4.f * xy * y2);
+  z.dx[13] = s10 * (12.f * x2 * y - 4.f * y2 * y);
+  z.dy[13] = s10 * (4.f * x2 * x - 12.f * x * y2);
+}
+
+// Per-launch pupil constants.
+struct PupilConst {
+  float R, Rinv, inv_lambda, dk2;
+  int hard_edge;
+};
+
+// Pupil value at q = p - delta (spectral px): M = A exp(i chi),
+// chi = sum_j c_j Z_j(q/R) + z kappa(q),
+// kappa = 2 pi (sqrt(lambda^-2 - |q|^2 dk^2) - 1/lambda), evaluated in the
+// cancellation-free form -2 pi k^2 / (sqrt(lambda^-2 - k^2) + 1/lambda).
+FPM_HD float pupil_amp(float qy, float qx, const PupilConst& P) {
+  const float r2 = qx * qx + qy * qy;
+  if (P.hard_edge) return r2 <= P.R * P.R ? 1.f : 0.f;
+  const float r = sqrtf(r2);
+  return fminf(fmaxf(P.R + 0.5f - r, 0.f), 1.f);
+}
+
+FPM_HD float defocus_kappa(float r2, const PupilConst& P, float* root_out) {
+  const float k2 = r2 * P.dk2;
+  const float root = sqrtf(P.inv_lambda * P.inv_lambda - k2);
+  *root_out = root;
+  return -6.283185307179586f * k2 / (root + P.inv_lambda);
+}
+
+FPM_HD float2 pupil_value(float qy, float qx, const PupilConst& P,
+                                              const float* __restrict__ zc, float z) {
+  const float A = pupil_amp(qy, qx, P);
+  if (A == 0.f) return make_float2(0.f, 0.f);
+  Zern Z;
+  zernike_eval(qx * P.Rinv, qy * P.Rinv, Z);
+  float th = 0.f;
+#pragma unroll
+  for (int j = 0; j < 14; ++j) th = fmaf(zc[j], Z.v[j], th);
+  float root;
+  const float kap = defocus_kappa(qx * qx + qy * qy, P, &root);
+  float sn, cs;
+  sincosf(fmaf(z, kap, th), &sn, &cs);
+  return make_float2(A * cs, A * sn);
+}
+
+// ---------------------------------------------------------------------------
+// FFT: Stockham autosort over a shared-memory buffer of M points, run by a
+// group of G = M/8 consecutive threads of one warp (so M <= 256). Each pass
+// reads 8 (radix 8), 2x4 (radix-4 tail) or 4x2 (radix-2 tail) points per
+// thread into registers, applies twiddles W_{R Ns}^{r k} (k = butterfly mod
+// Ns), a radix-R DFT, and writes them to (b - k) R + k + r Ns. All threads of
+// the warp call it together; the warp synchronises between the read and write
+// halves of each pass. tw[t] = exp(-2 pi i t / M). DIR = -1: forward
+// (exp(-)), +1: inverse (exp(+)); both unnormalised. The load/store halves
+// are host-callable so the index arithmetic can be emulated on a CPU.
+// ---------------------------------------------------------------------------
+template <int DIR>
+FPM_HD float2 tw_dir(float2 w) { return DIR < 0 ? w : make_float2(w.x, -w.y); }
+
+// multiply by DIR * i = exp(DIR * i pi / 2)
+template <int DIR>
+FPM_HD float2 mul_i(float2 a) {
+  return DIR < 0 ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+}
+
+template <int DIR>
+FPM_HD void dft2(float2& a0, float2& a1) {
+  const float2 t = a0;
+  a0 = cadd(t, a1);
+  a1 = csub(t, a1);
+}
+
+template <int DIR>
+FPM_HD void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2);
+  const float2 t2 = cadd(a1, a3), t3 = mul_i<DIR>(csub(a1, a3));
+  a0 = cadd(t0, t2);
+  a2 = csub(t0, t2);
+  a1 = cadd(t1, t3);
+  a3 = csub(t1, t3);
+}
+
+template <int DIR>
+FPM_HD void dft8(float2 (&v)[8]) {
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<DIR>(e0, e1, e2, e3);
+  dft4<DIR>(o0, o1, o2, o3);
+  const float h = 0.70710678118654752f;
+  const float d = (float)DIR;
+  // o_k * W8^k with W8 = exp(DIR * i pi / 4)
+  const float2 w1 = make_float2((o1.x - d * o1.y) * h, (o1.y + d * o1.x) * h);
+  const float2 w2 = mul_i<DIR>(o2);
+  const float2 w3 = make_float2((-o3.x - d * o3.y) * h, (-o3.y + d * o3.x) * h);
+  v[0] = cadd(e0, o0); v[4] = csub(e0, o0);
+  v[1] = cadd(e1, w1); v[5] = csub(e1, w1);
+  v[2] = cadd(e2, w2); v[6] = csub(e2, w2);
+  v[3] = cadd(e3, w3); v[7] = csub(e3, w3);
+}
+
+template <int M>
+struct FftShape {
+  static_assert(M >= 16 && M <= 256 && (M & (M - 1)) == 0, "group FFT size");
+  static constexpr int G = M / 8;                 // threads per transform
+  static constexpr int LOG = (M == 16) ? 4 : (M == 32) ? 5 : (M == 64) ? 6 : (M == 128) ? 7 : 8;
+  static constexpr int N8 = LOG / 3;              // radix-8 passes
+  static constexpr int TAIL = LOG % 3;            // 0: none, 1: radix 2, 2: radix 4
+};
+
+// One radix-8 pass, read half: 8 points of butterfly j, twiddled, transformed.
+template <int M, int DIR>
+FPM_HD void r8_load(const float2* buf, const float2* tw, int j, int Ns, float2 (&v)[8]) {
+  constexpr int G = M / 8;
+  const int k = j & (Ns - 1);
+  for (int r = 0; r < 8; ++r) v[r] = buf[j + r * G];
+  if (Ns > 1) {
+    const int step = M / (8 * Ns);
+    for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], tw_dir<DIR>(tw[r * k * step]));
+  }
+  dft8<DIR>(v);
+}
+template <int M>
+FPM_HD void r8_store(float2* buf, int j, int Ns, const float2 (&v)[8]) {
+  const int k = j & (Ns - 1);
+  const int base = (j - k) * 8 + k;
+  for (int r = 0; r < 8; ++r) buf[base + r * Ns] = v[r];
+}
+// radix-4 tail: butterflies j and j + G
+template <int M, int DIR>
+FPM_HD void r4_load(const float2* buf, const float2* tw, int j, int Ns, float2 (&v)[8]) {
+  constexpr int G = M / 8;
+  for (int b = 0; b < 2; ++b) {
+    const int jj = j + b * G;
+    const int k = jj & (Ns - 1);
+    const int step = M / (4 * Ns);
+    float2* w = v + 4 * b;
+    for (int r = 0; r < 4; ++r) w[r] = buf[jj + r * (M / 4)];
+    for (int r = 1; r < 4; ++r) w[r] = cmul(w[r], tw_dir<DIR>(tw[r * k * step]));
+    dft4<DIR>(w[0], w[1], w[2], w[3]);
+  }
+}
+template <int M>
+FPM_HD void r4_store(float2* buf, int j, int Ns, const float2 (&v)[8]) {
+  constexpr int G = M / 8;
+  for (int b = 0; b < 2; ++b) {
+    const int jj = j + b * G;
+    const int k = jj & (Ns - 1);
+    const int base = (jj - k) * 4 + k;
+    for (int r = 0; r < 4; ++r) buf[base + r * Ns] = v[4 * b + r];
+  }
+}
+// radix-2 tail: butterflies j + b G, b = 0..3
+template <int M, int DIR>
+FPM_HD void r2_load(const float2* buf, const float2* tw, int j, int Ns, float2 (&v)[8]) {
+  constexpr int G = M / 8;
+  for (int b = 0; b < 4; ++b) {
+    const int jj = j + b * G;
+    const int k = jj & (Ns - 1);
+    const int step = M / (2 * Ns);
+    v[2 * b] = buf[jj];
+    v[2 * b + 1] = cmul(buf[jj + M / 2], tw_dir<DIR>(tw[k * step]));
+    dft2<DIR>(v[2 * b], v[2 * b + 1]);
+  }
+}
+template <int M>
+FPM_HD void r2_store(float2* buf, int j, int Ns, const float2 (&v)[8]) {
+  constexpr int G = M / 8;
+  for (int b = 0; b < 4; ++b) {
+    const int jj = j + b * G;
+    const int k = jj & (Ns - 1);
+    const int base = (jj - k) * 2 + k;
+    buf[base] = v[2 * b];
+    buf[base + Ns] = v[2 * b + 1];
+  }
+}
+
+#if defined(__CUDACC__)
+template <int M, int DIR>
+__device__ __forceinline__ void fft_group(float2* __restrict__ buf, const float2* __restrict__ tw, int j) {
+  using S = FftShape<M>;
+  int Ns = 1;
+#pragma unroll
+  for (int pass = 0; pass < S::N8; ++pass) {
+    float2 v[8];
+    r8_load<M, DIR>(buf, tw, j, Ns, v);
+    __syncwarp();
+    r8_store<M>(buf, j, Ns, v);
+    __syncwarp();
+    Ns *= 8;
+  }
+  if (S::TAIL == 2) {
+    float2 v[8];
+    r4_load<M, DIR>(buf, tw, j, Ns, v);
+    __syncwarp();
+    r4_store<M>(buf, j, Ns, v);
+    __syncwarp();
+  } else if (S::TAIL == 1) {
+    float2 v[8];
+    r2_load<M, DIR>(buf, tw, j, Ns, v);
+    __syncwarp();
+    r2_store<M>(buf, j, Ns, v);
+    __syncwarp();
+  }
+}
+#endif
+
+// Host emulation of fft_group (all threads' read halves, then all write
+// halves, pass by pass) for checking the index arithmetic on a CPU.
+template <int M, int DIR>
+inline void fft_group_emulate(float2* buf, const float2* tw) {
+  using S = FftShape<M>;
+  constexpr int G = M / 8;
+  float2 V[G][8];
+  int Ns = 1;
+  for (int pass = 0; pass < S::N8; ++pass) {
+    for (int j = 0; j < G; ++j) r8_load<M, DIR>(buf, tw, j, Ns, V[j]);
+    for (int j = 0; j < G; ++j) r8_store<M>(buf, j, Ns, V[j]);
+    Ns *= 8;
+  }
+  if (S::TAIL == 2) {
+    for (int j = 0; j < G; ++j) r4_load<M, DIR>(buf, tw, j, Ns, V[j]);
+    for (int j = 0; j < G; ++j) r4_store<M>(buf, j, Ns, V[j]);
+  } else if (S::TAIL == 1) {
+    for (int j = 0; j < G; ++j) r2_load<M, DIR>(buf, tw, j, Ns, V[j]);
+    for (int j = 0; j < G; ++j) r2_store<M>(buf, j, Ns, V[j]);
+  }
+}
+
+}  // namespace fpmk

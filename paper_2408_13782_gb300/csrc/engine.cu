@@ -1,0 +1,838 @@
+// Host side of the Batch-FPM engine: the C ABI declared in include/fpm.h.
+//
+// All device work of a handle runs on an internal non-blocking stream that is
+// joined to the caller's stream at entry and exit of every call (event
+// record/wait), so work stays ordered with the caller's stream while the
+// engine can capture CUDA graphs even when the caller uses the legacy default
+// stream. Multi-step runs are captured once per (n_steps, B) as a graph whose
+// first nodes copy the batch schedule and the Adam step count from pinned
+// staging buffers, followed by two kernels per step (fused per-LED forward
+// and adjoint, then the batch-ordered gather with Adam).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/fpm.h"
+#include "internal.h"
+
+using namespace fpmk;
+
+namespace {
+thread_local std::string g_create_error;
+}
+
+struct fpm_handle {
+  int N = 0, m = 0, n = 0, s = 0, h = 0, W = 0, C = 0;
+  float R = 0.f, lambda = 0.f, dk = 0.f;
+  int edge = 0;
+  int centre = 0;
+  std::vector<float> nominal;
+  std::vector<int2> nint_h;
+  std::vector<float> sp0;  // initial scalar parameters
+  int x_lo = 0, n_cols = 0;
+  cudaStream_t user = nullptr, st = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_stage = nullptr;
+  fpm_hparams hp{};
+  // device state
+  float2 *Ot = nullptr, *mO = nullptr, *vO = nullptr, *tmp = nullptr, *tmp2 = nullptr;
+  float2 *tw_m = nullptr, *tw_N = nullptr;
+  float *meas = nullptr, *sp = nullptr, *msp = nullptr, *vsp = nullptr, *gsc = nullptr, *fbuf = nullptr;
+  int2 *nint = nullptr, *span = nullptr;
+  float2* gbox = nullptr;
+  double* part = nullptr;
+  int capB = 0;
+  int* sched = nullptr;
+  int cap_sched = 0;
+  double* losses = nullptr;
+  int cap_losses = 0;
+  size_t cap_fbuf = 0;
+  double* epoch = nullptr;
+  long long* tbase = nullptr;
+  int* err = nullptr;
+  // pinned staging
+  int* h_sched = nullptr;
+  int cap_h_sched = 0;
+  long long* h_t = nullptr;
+  int* h_err = nullptr;
+  long long t_host = 0;
+  bool loaded = false;
+  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+  std::string msg;
+};
+
+namespace {
+
+int fail(fpm_handle* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (h) h->msg = buf;
+  else g_create_error = buf;
+  return code;
+}
+
+#define CK(h, call)                                                                          \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail((h), e_ == cudaErrorMemoryAllocation ? FPM_ERR_OOM : FPM_ERR_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                        \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool is_pageable_host(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return at.type == cudaMemoryTypeUnregistered;
+}
+
+void free_all(fpm_handle* h) {
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  void* dev[] = {h->Ot, h->mO, h->vO, h->tmp, h->tmp2, h->tw_m, h->tw_N, h->meas, h->sp, h->msp, h->vsp,
+                 h->gsc, h->fbuf, h->nint, h->span, h->gbox, h->part, h->sched, h->losses, h->epoch,
+                 h->tbase, h->err};
+  for (void* p : dev)
+    if (p) cudaFree(p);
+  if (h->h_sched) cudaFreeHost(h->h_sched);
+  if (h->h_t) cudaFreeHost(h->h_t);
+  if (h->h_err) cudaFreeHost(h->h_err);
+  if (h->ev_in) cudaEventDestroy(h->ev_in);
+  if (h->ev_out) cudaEventDestroy(h->ev_out);
+  if (h->ev_stage) cudaEventDestroy(h->ev_stage);
+  if (h->st) cudaStreamDestroy(h->st);
+}
+
+// Order the internal stream after the caller's stream.
+int enter(fpm_handle* h) {
+  CK(h, cudaEventRecord(h->ev_in, h->user));
+  CK(h, cudaStreamWaitEvent(h->st, h->ev_in, 0));
+  return FPM_OK;
+}
+// Order the caller's stream after the internal stream.
+int leave(fpm_handle* h) {
+  CK(h, cudaEventRecord(h->ev_out, h->st));
+  CK(h, cudaStreamWaitEvent(h->user, h->ev_out, 0));
+  return FPM_OK;
+}
+
+// Read and clear the device error flag (synchronises the internal stream).
+int check_device_error(fpm_handle* h) {
+  CK(h, cudaMemcpyAsync(h->h_err, h->err, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  const int e = *h->h_err;
+  if (e) {
+    CK(h, cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
+    if (e & DERR_NONFINITE) return fail(h, FPM_ERR_NONFINITE, "a batch loss was not finite");
+    return fail(h, FPM_ERR_RANGE, "a kernel saw an LED index out of range");
+  }
+  return FPM_OK;
+}
+
+std::vector<float2> twiddles(int n) {
+  std::vector<float2> t(n);
+  for (int i = 0; i < n; ++i) {
+    const double a = -2.0 * M_PI * (double)i / (double)n;
+    t[i] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  return t;
+}
+
+int validate_batches(fpm_handle* h, const int32_t* idx, int n_steps, int B) {
+  if (!idx) return fail(h, FPM_ERR_ARG, "null batch index pointer");
+  if (B < 1 || B > h->n || B > MAX_BATCH) return fail(h, FPM_ERR_SHAPE, "batch size %d outside [1, %d]", B, h->n);
+  std::vector<int> seen(h->n, -1);
+  for (int s = 0; s < n_steps; ++s)
+    for (int b = 0; b < B; ++b) {
+      const int i = idx[(size_t)s * B + b];
+      if (i < 0 || i >= h->n) return fail(h, FPM_ERR_RANGE, "LED index %d outside [0, %d)", i, h->n);
+      if (seen[i] == s) return fail(h, FPM_ERR_RANGE, "LED index %d repeated in batch %d", i, s);
+      seen[i] = s;
+    }
+  return FPM_OK;
+}
+
+template <class T>
+int grow(fpm_handle* h, T** p, int* cap, int need) {
+  if (*cap >= need) return FPM_OK;
+  if (*p) CK(h, cudaFree(*p));
+  *p = nullptr;
+  *cap = 0;
+  CK(h, cudaMalloc((void**)p, sizeof(T) * (size_t)need));
+  *cap = need;
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);  // graphs hold the old address
+  h->graphs.clear();
+  return FPM_OK;
+}
+
+int ensure_batch(fpm_handle* h, int B) {
+  if (h->capB >= B) return FPM_OK;
+  if (h->gbox) CK(h, cudaFree(h->gbox));
+  if (h->part) CK(h, cudaFree(h->part));
+  h->gbox = nullptr;
+  h->part = nullptr;
+  h->capB = 0;
+  CK(h, cudaMalloc(&h->gbox, sizeof(float2) * (size_t)B * h->W * h->W));
+  CK(h, cudaMalloc(&h->part, sizeof(double) * (size_t)B * h->C * NPART));
+  h->capB = B;
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  return FPM_OK;
+}
+
+int ensure_fbuf(fpm_handle* h, size_t floats) {
+  if (h->cap_fbuf >= floats) return FPM_OK;
+  if (h->fbuf) CK(h, cudaFree(h->fbuf));
+  h->fbuf = nullptr;
+  h->cap_fbuf = 0;
+  CK(h, cudaMalloc(&h->fbuf, sizeof(float) * floats));
+  h->cap_fbuf = floats;
+  return FPM_OK;
+}
+
+LedArgs led_args(fpm_handle* h, const int* idx_dev, int B, int mode) {
+  LedArgs a{};
+  a.Ot = h->Ot;
+  a.meas = h->meas;
+  a.sp = h->sp;
+  a.n_int = h->nint;
+  a.idx = idx_dev;
+  a.gbox = h->gbox;
+  a.part = h->part;
+  a.tw = h->tw_m;
+  a.N = h->N;
+  a.n_leds = h->n;
+  a.B = B;
+  a.h = h->h;
+  a.W = h->W;
+  a.R = h->R;
+  a.Rinv = 1.f / h->R;
+  a.inv_lambda = 1.f / h->lambda;
+  a.dk2 = h->dk * h->dk;
+  a.hard_edge = h->edge == FPM_EDGE_HARD;
+  a.loss = h->hp.loss;
+  a.mode = mode;
+  a.err = h->err;
+  return a;
+}
+
+UpdArgs upd_args(fpm_handle* h, const int* idx_dev, int B, int step_off, double* loss_slot, int assemble) {
+  UpdArgs u{};
+  u.Ot = h->Ot;
+  u.mO = h->mO;
+  u.vO = h->vO;
+  u.sp = h->sp;
+  u.msp = h->msp;
+  u.vsp = h->vsp;
+  u.gbox = h->gbox;
+  u.part = h->part;
+  u.idx = idx_dev;
+  u.n_int = h->nint;
+  u.span = h->span;
+  u.x_lo = h->x_lo;
+  u.n_cols = h->n_cols;
+  u.N = h->N;
+  u.n_leds = h->n;
+  u.B = B;
+  u.C = h->C;
+  u.h = h->h;
+  u.W = h->W;
+  u.lr_obj = h->hp.lr_object;
+  u.lr_zern = h->hp.lr_zernike;
+  u.lr_def = h->hp.lr_defocus;
+  u.lr_gam = h->hp.lr_gamma;
+  u.lr_off = h->hp.lr_offset;
+  u.b1 = h->hp.beta1;
+  u.b2 = h->hp.beta2;
+  u.eps = h->hp.eps;
+  u.offset_bound = FPM_OFFSET_BOUND_PX;
+  u.t_base = h->tbase;
+  u.step_off = step_off;
+  u.learn = h->hp.learn_mask;
+  u.loss_slot = loss_slot;
+  u.epoch_loss = h->epoch;
+  u.err = h->err;
+  u.assemble = assemble;
+  u.g_obj = h->tmp;
+  u.g_sc = h->gsc;
+  return u;
+}
+
+int reset_state(fpm_handle* h) {
+  const size_t NN = (size_t)h->N * h->N;
+  CK(h, cudaMemsetAsync(h->mO, 0, sizeof(float2) * NN, h->st));
+  CK(h, cudaMemsetAsync(h->vO, 0, sizeof(float2) * NN, h->st));
+  const int P = sp_size(h->n);
+  CK(h, cudaMemcpyAsync(h->sp, h->sp0.data(), sizeof(float) * P, cudaMemcpyHostToDevice, h->st));
+  CK(h, cudaMemsetAsync(h->msp, 0, sizeof(float) * P, h->st));
+  CK(h, cudaMemsetAsync(h->vsp, 0, sizeof(float) * P, h->st));
+  CK(h, cudaMemsetAsync(h->epoch, 0, sizeof(double), h->st));
+  h->t_host = 0;
+  return FPM_OK;
+}
+
+// real-space object (row-major, in tmp) -> centred spectrum in Ot
+int object_from_field(fpm_handle* h) {
+  CK(h, launch_fft_rows(h->tmp, h->N, h->tw_N, -1, h->st));
+  CK(h, launch_fft_cols_centre(h->tmp, h->Ot, h->N, h->tw_N, 1.f / (float)(h->s * h->s), h->st));
+  return FPM_OK;
+}
+
+int copy_out(fpm_handle* h, void* dst, const void* src, size_t bytes, bool* host_dst) {
+  if (!dst) return FPM_OK;
+  if (!is_device_ptr(dst)) *host_dst = true;
+  CK(h, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, h->st));
+  return FPM_OK;
+}
+
+int build_graph(fpm_handle* h, int n_steps, int B, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  CK(h, cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaMemcpyAsync(h->sched, h->h_sched, sizeof(int) * (size_t)n_steps * B,
+                                  cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h->tbase, h->h_t, sizeof(long long), cudaMemcpyHostToDevice, h->st);
+  for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
+    const int* idx = h->sched + (size_t)s * B;
+    e = launch_led(h->m, led_args(h, idx, B, MODE_LOSS), h->st);
+    if (e == cudaSuccess) e = launch_update(upd_args(h, idx, B, s, h->losses + s, 0), h->st);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(h->st, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return fail(h, FPM_ERR_CUDA, "graph capture failed: %s",
+                cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return fail(h, FPM_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+  return FPM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fpm_create(const fpm_geometry* g, float R, int32_t upsample, void* cuda_stream, fpm_handle** out) {
+  g_create_error.clear();
+  if (!g || !out || !g->led_offset) return fail(nullptr, FPM_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (led_cluster_size(g->m) == 0) return fail(nullptr, FPM_ERR_SHAPE, "m=%d not in {32, 64, 128, 256}", g->m);
+  if (upsample < 1 || (long long)g->m * upsample > 8192 || (upsample & (upsample - 1)))
+    return fail(nullptr, FPM_ERR_SHAPE, "upsample=%d must be a power of two with m*upsample <= 8192", upsample);
+  if (g->n_leds < 1 || g->n_leds > 1024) return fail(nullptr, FPM_ERR_SHAPE, "n_leds=%d outside [1, 1024]", g->n_leds);
+  if (!(R > 0.f) || !(g->lambda_um > 0.f) || !(g->dk_per_um > 0.f))
+    return fail(nullptr, FPM_ERR_ARG, "radius, wavelength and spectral bin must be positive");
+  if (g->pupil_edge != FPM_EDGE_AA && g->pupil_edge != FPM_EDGE_HARD)
+    return fail(nullptr, FPM_ERR_ARG, "unknown pupil edge %d", g->pupil_edge);
+  fpm_handle* h = new fpm_handle();
+  h->m = g->m;
+  h->s = upsample;
+  h->N = g->m * upsample;
+  h->n = g->n_leds;
+  h->R = R;
+  h->lambda = g->lambda_um;
+  h->dk = g->dk_per_um;
+  h->edge = g->pupil_edge;
+  h->user = (cudaStream_t)cuda_stream;
+  h->C = led_cluster_size(h->m);
+  h->h = (int)std::floor((double)R + 0.5 + std::sqrt(2.0) * FPM_OFFSET_BOUND_PX) + 1;
+  h->W = 2 * h->h + 1;
+  auto bad = [&](int code, const char* why) {
+    g_create_error = why;
+    delete h;
+    return code;
+  };
+  if (2 * h->h >= h->m) return bad(FPM_ERR_SHAPE, "pupil box does not fit the low-res window (2h >= m)");
+  if ((double)(R + 2.f) * g->dk_per_um * g->lambda_um >= 1.0)
+    return bad(FPM_ERR_SHAPE, "pupil reaches evanescent frequencies (radius * dk * lambda >= 1)");
+  h->nominal.assign(g->led_offset, g->led_offset + 2 * (size_t)h->n);
+  h->nint_h.resize(h->n);
+  h->sp0.assign(sp_size(h->n), 0.f);
+  double best = 1e300;
+  int lo_x = h->N, hi_x = -1;
+  std::vector<int2> span(h->N, make_int2(h->N, 0));
+  for (int i = 0; i < h->n; ++i) {
+    const double r = h->nominal[2 * i], c = h->nominal[2 * i + 1];
+    if (!std::isfinite(r) || !std::isfinite(c)) return bad(FPM_ERR_ARG, "non-finite LED offset");
+    const int ri = (int)std::nearbyint(r), ci = (int)std::nearbyint(c);
+    h->nint_h[i] = make_int2(ri, ci);
+    h->sp0[sp_offset(h->n) + 2 * i] = (float)(r - ri);
+    h->sp0[sp_offset(h->n) + 2 * i + 1] = (float)(c - ci);
+    const int r0 = h->N / 2 + ri - h->h, c0 = h->N / 2 + ci - h->h;
+    if (r0 < 0 || c0 < 0 || r0 + h->W > h->N || c0 + h->W > h->N)
+      return bad(FPM_ERR_SHAPE, "an LED crop box leaves the high-res spectrum");
+    for (int x = c0; x < c0 + h->W; ++x) {
+      span[x].x = std::min(span[x].x, r0);
+      span[x].y = std::max(span[x].y, r0 + h->W);
+    }
+    lo_x = std::min(lo_x, c0);
+    hi_x = std::max(hi_x, c0 + h->W);
+    const double d = std::hypot(r, c);
+    if (d < best) {
+      best = d;
+      h->centre = i;
+    }
+  }
+  for (int i = 0; i < h->n; ++i) h->sp0[SP_GAMMA + i] = 1.f;
+  h->x_lo = lo_x;
+  h->n_cols = hi_x - lo_x;
+  h->hp.lr_object = 0.1f;
+  h->hp.lr_zernike = 0.01f;
+  h->hp.lr_defocus = 0.1f;
+  h->hp.lr_gamma = 0.01f;
+  h->hp.lr_offset = 0.01f;
+  h->hp.beta1 = 0.9f;
+  h->hp.beta2 = 0.999f;
+  h->hp.eps = 1e-8f;
+  h->hp.loss = FPM_LOSS_AMPLITUDE;
+  h->hp.learn_mask = FPM_LEARN_OBJECT;
+  h->hp.precision = FPM_PRECISION_FP32_FFT;
+
+  auto ck = [&](cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return true;
+    g_create_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return false;
+  };
+  const size_t NN = (size_t)h->N * h->N;
+  const int P = sp_size(h->n);
+  bool ok = ck(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking), "stream") &&
+            ck(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming), "event") &&
+            ck(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming), "event") &&
+            ck(cudaEventCreateWithFlags(&h->ev_stage, cudaEventDisableTiming), "event") &&
+            ck(cudaMalloc(&h->Ot, sizeof(float2) * NN), "alloc O") &&
+            ck(cudaMalloc(&h->mO, sizeof(float2) * NN), "alloc m") &&
+            ck(cudaMalloc(&h->vO, sizeof(float2) * NN), "alloc v") &&
+            ck(cudaMalloc(&h->tmp, sizeof(float2) * NN), "alloc tmp") &&
+            ck(cudaMalloc(&h->tmp2, sizeof(float2) * NN), "alloc tmp2") &&
+            ck(cudaMalloc(&h->tw_m, sizeof(float2) * h->m), "alloc tw") &&
+            ck(cudaMalloc(&h->tw_N, sizeof(float2) * h->N), "alloc tw") &&
+            ck(cudaMalloc(&h->meas, sizeof(float) * (size_t)h->n * h->m * h->m), "alloc stack") &&
+            ck(cudaMalloc(&h->sp, sizeof(float) * P), "alloc params") &&
+            ck(cudaMalloc(&h->msp, sizeof(float) * P), "alloc params") &&
+            ck(cudaMalloc(&h->vsp, sizeof(float) * P), "alloc params") &&
+            ck(cudaMalloc(&h->gsc, sizeof(float) * P), "alloc params") &&
+            ck(cudaMalloc(&h->nint, sizeof(int2) * h->n), "alloc leds") &&
+            ck(cudaMalloc(&h->span, sizeof(int2) * h->N), "alloc span") &&
+            ck(cudaMalloc(&h->epoch, sizeof(double)), "alloc") &&
+            ck(cudaMalloc(&h->tbase, sizeof(long long)), "alloc") &&
+            ck(cudaMalloc(&h->err, sizeof(int)), "alloc") &&
+            ck(cudaMallocHost(&h->h_t, sizeof(long long)), "pinned") &&
+            ck(cudaMallocHost(&h->h_err, sizeof(int)), "pinned") &&
+            ck(led_prepare(h->m, h->W), "kernel attributes");
+  if (ok) {
+    const auto twm = twiddles(h->m), twN = twiddles(h->N);
+    ok = ck(cudaMemcpy(h->tw_m, twm.data(), sizeof(float2) * h->m, cudaMemcpyHostToDevice), "copy") &&
+         ck(cudaMemcpy(h->tw_N, twN.data(), sizeof(float2) * h->N, cudaMemcpyHostToDevice), "copy") &&
+         ck(cudaMemcpy(h->nint, h->nint_h.data(), sizeof(int2) * h->n, cudaMemcpyHostToDevice), "copy") &&
+         ck(cudaMemcpy(h->span, span.data(), sizeof(int2) * h->N, cudaMemcpyHostToDevice), "copy") &&
+         ck(cudaMemset(h->Ot, 0, sizeof(float2) * NN), "memset") &&
+         ck(cudaMemset(h->err, 0, sizeof(int)), "memset") &&
+         ck(cudaMemset(h->tbase, 0, sizeof(long long)), "memset");
+  }
+  if (ok) ok = reset_state(h) == FPM_OK && ck(cudaStreamSynchronize(h->st), "sync");
+  if (!ok) {
+    if (g_create_error.empty()) g_create_error = h->msg;
+    free_all(h);
+    delete h;
+    return FPM_ERR_CUDA;
+  }
+  *out = h;
+  return FPM_OK;
+}
+
+void fpm_destroy(fpm_handle* h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  free_all(h);
+  delete h;
+}
+
+const char* fpm_last_error(const fpm_handle* h) { return h ? h->msg.c_str() : g_create_error.c_str(); }
+
+int fpm_set_hparams(fpm_handle* h, const fpm_hparams* hp) {
+  if (!h || !hp) return fail(h, FPM_ERR_ARG, "null argument");
+  if (hp->loss != FPM_LOSS_AMPLITUDE && hp->loss != FPM_LOSS_INTENSITY) return fail(h, FPM_ERR_ARG, "unknown loss");
+  if (hp->learn_mask & ~FPM_LEARN_ALL) return fail(h, FPM_ERR_ARG, "unknown learn bits");
+  if (hp->precision != FPM_PRECISION_FP32_FFT) return fail(h, FPM_ERR_ARG, "unsupported precision mode");
+  if (!(hp->beta1 >= 0.f && hp->beta1 < 1.f && hp->beta2 >= 0.f && hp->beta2 < 1.f && hp->eps > 0.f))
+    return fail(h, FPM_ERR_ARG, "betas must lie in [0, 1) and eps be positive");
+  const bool lr_ok = std::isfinite(hp->lr_object) && std::isfinite(hp->lr_zernike) &&
+                     std::isfinite(hp->lr_defocus) && std::isfinite(hp->lr_gamma) && std::isfinite(hp->lr_offset);
+  if (!lr_ok) return fail(h, FPM_ERR_ARG, "non-finite learning rate");
+  const bool graph_relevant = hp->loss != h->hp.loss || std::memcmp(hp, &h->hp, sizeof *hp) != 0;
+  h->hp = *hp;
+  if (graph_relevant) {  // the captured kernels hold the hyper-parameters by value
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+  }
+  return FPM_OK;
+}
+
+int fpm_get_hparams(const fpm_handle* h, fpm_hparams* hp) {
+  if (!h || !hp) return FPM_ERR_ARG;
+  *hp = h->hp;
+  return FPM_OK;
+}
+
+int fpm_dims(const fpm_handle* h, int32_t* N, int32_t* m, int32_t* n_leds, int32_t* box) {
+  if (!h) return FPM_ERR_ARG;
+  if (N) *N = h->N;
+  if (m) *m = h->m;
+  if (n_leds) *n_leds = h->n;
+  if (box) *box = h->W;
+  return FPM_OK;
+}
+
+int fpm_load(fpm_handle* h, const float* stack, int32_t flags) {
+  if (!h || !stack) return fail(h, FPM_ERR_ARG, "null argument");
+  if (flags & ~FPM_LOAD_INIT) return fail(h, FPM_ERR_ARG, "unknown load flags");
+  int rc = enter(h);
+  if (rc) return rc;
+  CK(h, cudaMemcpyAsync(h->meas, stack, sizeof(float) * (size_t)h->n * h->m * h->m, cudaMemcpyDefault, h->st));
+  if (flags & FPM_LOAD_INIT) {
+    CK(h, launch_upsample_centre(h->meas + (size_t)h->centre * h->m * h->m, h->m, h->s, h->tmp, h->st));
+    if ((rc = object_from_field(h))) return rc;
+    if ((rc = reset_state(h))) return rc;
+  }
+  h->loaded = true;
+  return leave(h);
+}
+
+int fpm_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int32_t B, double* losses_out) {
+  if (!h) return FPM_ERR_ARG;
+  if (!h->loaded) return fail(h, FPM_ERR_STATE, "no stack loaded");
+  if (n_steps < 1) return fail(h, FPM_ERR_SHAPE, "n_steps must be >= 1");
+  int rc = validate_batches(h, schedule, n_steps, B);
+  if (rc) return rc;
+  if ((rc = ensure_batch(h, B))) return rc;
+  if ((rc = grow(h, &h->sched, &h->cap_sched, n_steps * B))) return rc;
+  if ((rc = grow(h, &h->losses, &h->cap_losses, n_steps))) return rc;
+  // the previous run's graph may still be reading the staging buffers
+  CK(h, cudaEventSynchronize(h->ev_stage));
+  if (h->cap_h_sched < n_steps * B) {
+    if (h->h_sched) CK(h, cudaFreeHost(h->h_sched));
+    h->h_sched = nullptr;
+    h->cap_h_sched = 0;
+    CK(h, cudaMallocHost(&h->h_sched, sizeof(int) * (size_t)n_steps * B));
+    h->cap_h_sched = n_steps * B;
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+  }
+  std::memcpy(h->h_sched, schedule, sizeof(int) * (size_t)n_steps * B);
+  *h->h_t = h->t_host;
+  auto key = std::make_pair(n_steps, B);
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    cudaGraphExec_t ex;
+    if ((rc = build_graph(h, n_steps, B, &ex))) return rc;
+    it = h->graphs.emplace(key, ex).first;
+  }
+  if ((rc = enter(h))) return rc;
+  CK(h, cudaGraphLaunch(it->second, h->st));
+  CK(h, cudaEventRecord(h->ev_stage, h->st));
+  h->t_host += n_steps;
+  if (losses_out) {
+    bool host = false;
+    if ((rc = copy_out(h, losses_out, h->losses, sizeof(double) * n_steps, &host))) return rc;
+    if (host) {
+      if ((rc = check_device_error(h))) return rc;
+    }
+  }
+  return leave(h);
+}
+
+int fpm_profile_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int32_t B, void* flush,
+                    int64_t flush_bytes, float* led_ms, float* update_ms, float* step_ms) {
+  if (!h) return FPM_ERR_ARG;
+  if (!h->loaded) return fail(h, FPM_ERR_STATE, "no stack loaded");
+  if (n_steps < 1) return fail(h, FPM_ERR_SHAPE, "n_steps must be >= 1");
+  if (flush && flush_bytes <= 0) return fail(h, FPM_ERR_ARG, "flush buffer without a size");
+  if (flush && !is_device_ptr(flush)) return fail(h, FPM_ERR_ARG, "flush buffer must be device memory");
+  int rc = validate_batches(h, schedule, n_steps, B);
+  if (rc) return rc;
+  if ((rc = ensure_batch(h, B))) return rc;
+  if ((rc = grow(h, &h->sched, &h->cap_sched, n_steps * B))) return rc;
+  if ((rc = grow(h, &h->losses, &h->cap_losses, n_steps))) return rc;
+  if ((rc = enter(h))) return rc;
+  CK(h, cudaMemcpyAsync(h->sched, schedule, sizeof(int) * (size_t)n_steps * B, cudaMemcpyHostToDevice, h->st));
+  const long long t0 = h->t_host;
+  CK(h, cudaMemcpyAsync(h->tbase, &t0, sizeof(long long), cudaMemcpyHostToDevice, h->st));
+  std::vector<cudaEvent_t> ev((size_t)3 * n_steps, nullptr);
+  auto destroy = [&]() {
+    for (auto e : ev)
+      if (e) cudaEventDestroy(e);
+  };
+  for (auto& e : ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      destroy();
+      return fail(h, FPM_ERR_CUDA, "event creation failed");
+    }
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ex = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal);
+  for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
+    const int* idx = h->sched + (size_t)s * B;
+    if (flush) e = cudaMemsetAsync(flush, s & 0xff, (size_t)flush_bytes, h->st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s], h->st);
+    if (e == cudaSuccess) e = launch_led(h->m, led_args(h, idx, B, MODE_LOSS), h->st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 1], h->st);
+    if (e == cudaSuccess) e = launch_update(upd_args(h, idx, B, s, h->losses + s, 0), h->st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 2], h->st);
+  }
+  cudaError_t e2 = cudaStreamEndCapture(h->st, &g);
+  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ex, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  if (ex) cudaGraphExecDestroy(ex);
+  if (e != cudaSuccess) {
+    destroy();
+    return fail(h, FPM_ERR_CUDA, "profiled run failed: %s", cudaGetErrorString(e));
+  }
+  h->t_host += n_steps;
+  for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
+    float a = 0.f, b = 0.f;
+    e = cudaEventElapsedTime(&a, ev[3 * s], ev[3 * s + 1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[3 * s + 1], ev[3 * s + 2]);
+    if (led_ms) led_ms[s] = a;
+    if (update_ms) update_ms[s] = b;
+    if (step_ms) step_ms[s] = a + b;
+  }
+  destroy();
+  if (e != cudaSuccess) return fail(h, FPM_ERR_CUDA, "event timing failed: %s", cudaGetErrorString(e));
+  if ((rc = check_device_error(h))) return rc;
+  return leave(h);
+}
+
+int fpm_step(fpm_handle* h, const int32_t* batch_idx, int32_t B, double* loss_out) {
+  return fpm_run(h, batch_idx, 1, B, loss_out);
+}
+
+int fpm_epoch_loss(fpm_handle* h, double* out, int32_t reset) {
+  if (!h) return FPM_ERR_ARG;
+  int rc = enter(h);
+  if (rc) return rc;
+  if (out) {
+    bool host = false;
+    if ((rc = copy_out(h, out, h->epoch, sizeof(double), &host))) return rc;
+  }
+  if (reset) CK(h, cudaMemsetAsync(h->epoch, 0, sizeof(double), h->st));
+  if ((rc = check_device_error(h))) return rc;
+  return leave(h);
+}
+
+int fpm_forward(fpm_handle* h, const int32_t* idx, int32_t B, float* I_out) {
+  if (!h || !I_out) return fail(h, FPM_ERR_ARG, "null argument");
+  int rc = validate_batches(h, idx, 1, B);
+  if (rc) return rc;
+  if ((rc = ensure_batch(h, B))) return rc;
+  if ((rc = grow(h, &h->sched, &h->cap_sched, B))) return rc;
+  const size_t img = (size_t)B * h->m * h->m;
+  const bool dev_out = is_device_ptr(I_out);
+  if (!dev_out && (rc = ensure_fbuf(h, img))) return rc;
+  if ((rc = enter(h))) return rc;
+  CK(h, cudaMemcpyAsync(h->sched, idx, sizeof(int) * B, cudaMemcpyHostToDevice, h->st));
+  LedArgs a = led_args(h, h->sched, B, MODE_FORWARD);
+  a.I_out = dev_out ? I_out : h->fbuf;
+  CK(h, launch_led(h->m, a, h->st));
+  if (!dev_out) {
+    CK(h, cudaMemcpyAsync(I_out, h->fbuf, sizeof(float) * img, cudaMemcpyDeviceToHost, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+  }
+  return leave(h);
+}
+
+int fpm_backward(fpm_handle* h, const int32_t* idx, int32_t B, const float* dL_dI, float* g_object,
+                 float* g_zernike, float* g_defocus, float* g_gamma, float* g_offset, double* loss_out) {
+  if (!h) return FPM_ERR_ARG;
+  if (!dL_dI && !h->loaded) return fail(h, FPM_ERR_STATE, "no stack loaded");
+  int rc = validate_batches(h, idx, 1, B);
+  if (rc) return rc;
+  if ((rc = ensure_batch(h, B))) return rc;
+  if ((rc = grow(h, &h->sched, &h->cap_sched, B))) return rc;
+  if ((rc = grow(h, &h->losses, &h->cap_losses, 1))) return rc;
+  const size_t img = (size_t)B * h->m * h->m;
+  const bool dev_in = dL_dI && is_device_ptr(dL_dI);
+  if (dL_dI && !dev_in && (rc = ensure_fbuf(h, img))) return rc;
+  if ((rc = enter(h))) return rc;
+  CK(h, cudaMemcpyAsync(h->sched, idx, sizeof(int) * B, cudaMemcpyHostToDevice, h->st));
+  LedArgs a = led_args(h, h->sched, B, dL_dI ? MODE_UPSTREAM : MODE_LOSS);
+  if (dL_dI) {
+    if (!dev_in) CK(h, cudaMemcpyAsync(h->fbuf, dL_dI, sizeof(float) * img, cudaMemcpyHostToDevice, h->st));
+    a.dLdI = dev_in ? dL_dI : h->fbuf;
+  }
+  CK(h, launch_led(h->m, a, h->st));
+  const size_t NN = (size_t)h->N * h->N;
+  CK(h, cudaMemsetAsync(h->tmp, 0, sizeof(float2) * NN, h->st));
+  CK(h, launch_update(upd_args(h, h->sched, B, 0, h->losses, 1), h->st));
+  bool host = false;
+  if (g_object) {
+    CK(h, launch_transpose(h->tmp, h->tmp2, h->N, h->st));
+    if ((rc = copy_out(h, g_object, h->tmp2, sizeof(float2) * NN, &host))) return rc;
+  }
+  const int off = sp_offset(h->n);
+  if ((rc = copy_out(h, g_zernike, h->gsc + SP_ZERN, sizeof(float) * 14, &host))) return rc;
+  if ((rc = copy_out(h, g_defocus, h->gsc + SP_DEFOCUS, sizeof(float), &host))) return rc;
+  if ((rc = copy_out(h, g_gamma, h->gsc + SP_GAMMA, sizeof(float) * h->n, &host))) return rc;
+  if ((rc = copy_out(h, g_offset, h->gsc + off, sizeof(float) * 2 * h->n, &host))) return rc;
+  if (loss_out) {
+    if (dL_dI) *loss_out = 0.0;
+    else if ((rc = copy_out(h, loss_out, h->losses, sizeof(double), &host))) return rc;
+  }
+  if (host) CK(h, cudaStreamSynchronize(h->st));
+  return leave(h);
+}
+
+int fpm_get(fpm_handle* h, float* O, float* zernike, float* defocus, float* gamma, float* offset) {
+  if (!h) return FPM_ERR_ARG;
+  int rc = enter(h);
+  if (rc) return rc;
+  bool host = false;
+  if (O) {
+    CK(h, launch_transpose(h->Ot, h->tmp2, h->N, h->st));
+    if ((rc = copy_out(h, O, h->tmp2, sizeof(float2) * (size_t)h->N * h->N, &host))) return rc;
+  }
+  if ((rc = copy_out(h, zernike, h->sp + SP_ZERN, sizeof(float) * 14, &host))) return rc;
+  if ((rc = copy_out(h, defocus, h->sp + SP_DEFOCUS, sizeof(float), &host))) return rc;
+  if ((rc = copy_out(h, gamma, h->sp + SP_GAMMA, sizeof(float) * h->n, &host))) return rc;
+  if ((rc = copy_out(h, offset, h->sp + sp_offset(h->n), sizeof(float) * 2 * h->n, &host))) return rc;
+  if (host) CK(h, cudaStreamSynchronize(h->st));
+  return leave(h);
+}
+
+int fpm_set(fpm_handle* h, const float* O, const float* zernike, const float* defocus, const float* gamma,
+            const float* offset) {
+  if (!h) return FPM_ERR_ARG;
+  if (offset) {
+    const bool host = !is_device_ptr(offset);
+    if (host)
+      for (int i = 0; i < 2 * h->n; ++i)
+        if (!(std::fabs(offset[i]) <= FPM_OFFSET_BOUND_PX))
+          return fail(h, FPM_ERR_RANGE, "offset %d outside +-%.2f px", i, (double)FPM_OFFSET_BOUND_PX);
+  }
+  int rc = enter(h);
+  if (rc) return rc;
+  if (O) {
+    CK(h, cudaMemcpyAsync(h->tmp2, O, sizeof(float2) * (size_t)h->N * h->N, cudaMemcpyDefault, h->st));
+    CK(h, launch_transpose(h->tmp2, h->Ot, h->N, h->st));
+  }
+  if (zernike) CK(h, cudaMemcpyAsync(h->sp + SP_ZERN, zernike, sizeof(float) * 14, cudaMemcpyDefault, h->st));
+  if (defocus) CK(h, cudaMemcpyAsync(h->sp + SP_DEFOCUS, defocus, sizeof(float), cudaMemcpyDefault, h->st));
+  if (gamma) CK(h, cudaMemcpyAsync(h->sp + SP_GAMMA, gamma, sizeof(float) * h->n, cudaMemcpyDefault, h->st));
+  if (offset)
+    CK(h, cudaMemcpyAsync(h->sp + sp_offset(h->n), offset, sizeof(float) * 2 * h->n, cudaMemcpyDefault, h->st));
+  const bool any_host = (O && is_pageable_host(O)) || (zernike && is_pageable_host(zernike)) ||
+                        (defocus && is_pageable_host(defocus)) || (gamma && is_pageable_host(gamma)) ||
+                        (offset && is_pageable_host(offset));
+  if (any_host) CK(h, cudaStreamSynchronize(h->st));
+  return leave(h);
+}
+
+int fpm_set_object_field(fpm_handle* h, const float* o) {
+  if (!h || !o) return fail(h, FPM_ERR_ARG, "null argument");
+  int rc = enter(h);
+  if (rc) return rc;
+  CK(h, cudaMemcpyAsync(h->tmp, o, sizeof(float2) * (size_t)h->N * h->N, cudaMemcpyDefault, h->st));
+  if ((rc = object_from_field(h))) return rc;
+  if (is_pageable_host(o)) CK(h, cudaStreamSynchronize(h->st));
+  return leave(h);
+}
+
+int64_t fpm_state_size(const fpm_handle* h) {
+  if (!h) return FPM_ERR_ARG;
+  return (int64_t)6 * h->N * h->N + 3LL * sp_size(h->n) + 4;
+}
+
+int fpm_get_state(fpm_handle* h, float* state) {
+  if (!h || !state) return fail(h, FPM_ERR_ARG, "null argument");
+  int rc = enter(h);
+  if (rc) return rc;
+  const size_t NN = (size_t)h->N * h->N;
+  const int P = sp_size(h->n);
+  bool host = false;
+  float2* src[3] = {h->Ot, h->mO, h->vO};
+  for (int q = 0; q < 3; ++q) {
+    CK(h, launch_transpose(src[q], h->tmp2, h->N, h->st));
+    if ((rc = copy_out(h, state + 2 * NN * q, h->tmp2, sizeof(float2) * NN, &host))) return rc;
+    CK(h, cudaStreamSynchronize(h->st));  // tmp2 is reused by the next transpose
+  }
+  float* sps[3] = {h->sp, h->msp, h->vsp};
+  for (int q = 0; q < 3; ++q)
+    if ((rc = copy_out(h, state + 6 * NN + (size_t)P * q, sps[q], sizeof(float) * P, &host))) return rc;
+  double tail[2];
+  CK(h, cudaMemcpyAsync(&tail[1], h->epoch, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  tail[0] = (double)h->t_host;
+  CK(h, cudaMemcpyAsync(state + 6 * NN + 3 * (size_t)P, tail, sizeof tail, cudaMemcpyDefault, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  return leave(h);
+}
+
+int fpm_set_state(fpm_handle* h, const float* state) {
+  if (!h || !state) return fail(h, FPM_ERR_ARG, "null argument");
+  int rc = enter(h);
+  if (rc) return rc;
+  const size_t NN = (size_t)h->N * h->N;
+  const int P = sp_size(h->n);
+  float2* dst[3] = {h->Ot, h->mO, h->vO};
+  for (int q = 0; q < 3; ++q) {
+    CK(h, cudaMemcpyAsync(h->tmp2, state + 2 * NN * q, sizeof(float2) * NN, cudaMemcpyDefault, h->st));
+    CK(h, launch_transpose(h->tmp2, dst[q], h->N, h->st));
+    CK(h, cudaStreamSynchronize(h->st));
+  }
+  float* sps[3] = {h->sp, h->msp, h->vsp};
+  for (int q = 0; q < 3; ++q)
+    CK(h, cudaMemcpyAsync(sps[q], state + 6 * NN + (size_t)P * q, sizeof(float) * P, cudaMemcpyDefault, h->st));
+  double tail[2];
+  CK(h, cudaMemcpyAsync(tail, state + 6 * NN + 3 * (size_t)P, sizeof tail, cudaMemcpyDefault, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  if (!(tail[0] >= 0.0) || !std::isfinite(tail[1])) return fail(h, FPM_ERR_ARG, "corrupt state tail");
+  h->t_host = (long long)tail[0];
+  CK(h, cudaMemcpyAsync(h->epoch, &tail[1], sizeof(double), cudaMemcpyHostToDevice, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  h->loaded = true;
+  return leave(h);
+}
+
+int fpm_epoch_permutation(int32_t n, uint64_t seed, int32_t epoch, int32_t* out) {
+  if (n < 1 || !out || epoch < 0) return FPM_ERR_ARG;
+  uint64_t s = seed ^ ((uint64_t)(epoch + 1) * 0xA0761D6478BD642FULL);
+  auto next = [&s]() {
+    s += 0x9E3779B97F4A7C15ULL;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+  };
+  for (int i = 0; i < n; ++i) out[i] = i;
+  for (int i = n - 1; i > 0; --i) {
+    const int j = (int)(next() % (uint64_t)(i + 1));
+    const int t = out[i];
+    out[i] = out[j];
+    out[j] = t;
+  }
+  return FPM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,83 @@
+// Launch arguments shared by the host engine and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace fpmk {
+
+// Per-CTA partial sums written by the LED kernel (FP64).
+constexpr int NPART = 19;
+enum : int { P_LOSS = 0, P_GAMMA = 1, P_ZERN = 2, P_DEFOCUS = 16, P_DY = 17, P_DX = 18 };
+
+// Scalar parameter vector layout: [zernike 14][defocus 1][gamma n][delta n x (dy, dx)].
+constexpr int SP_ZERN = 0, SP_DEFOCUS = 14, SP_GAMMA = 15;
+__host__ __device__ inline int sp_offset(int n_leds) { return SP_GAMMA + n_leds; }
+__host__ __device__ inline int sp_size(int n_leds) { return SP_GAMMA + 3 * n_leds; }
+
+enum LedMode : int { MODE_LOSS = 0, MODE_FORWARD = 1, MODE_UPSTREAM = 2 };
+
+// Device error flags (bit set, OR-accumulated).
+enum : int { DERR_INDEX = 1, DERR_NONFINITE = 2 };
+
+constexpr int MAX_BATCH = 1024;
+
+struct LedArgs {
+  const float2* Ot;     // [N][N] spectrum, column-major: element (row y, col x) at Ot[x * N + y]
+  const float* meas;    // [n_leds][m][m] measured intensities (MODE_LOSS)
+  const float* dLdI;    // [B][m][m] upstream gradient of the intensities (MODE_UPSTREAM)
+  float* I_out;         // [B][m][m] predicted intensities (MODE_FORWARD)
+  const float* sp;      // scalar parameters, layout above
+  const int2* n_int;    // [n_leds] integer crop offsets (x = row, y = col)
+  const int* idx;       // [B] LED of each batch slot
+  float2* gbox;         // [B][W][W] per-LED object-gradient boxes, [slot][col][row]
+  double* part;         // [B][cluster][NPART]
+  const float2* tw;     // [m] exp(-2 pi i t / m)
+  int N, n_leds, B, h, W;
+  float R, Rinv, inv_lambda, dk2;
+  int hard_edge, loss, mode;
+  int* err;
+};
+
+struct UpdArgs {
+  float2* Ot;           // [N][N] column-major
+  float2* mO;           // Adam first moment of (Re, Im)
+  float2* vO;           // Adam second moment of (Re, Im)
+  float* sp;            // scalar parameters
+  float* msp;
+  float* vsp;
+  const float2* gbox;   // from the LED kernel
+  const double* part;
+  const int* idx;
+  const int2* n_int;
+  const int2* span;     // [N] per column: [row_lo, row_hi) of the update region
+  int x_lo, n_cols;     // update-region columns [x_lo, x_lo + n_cols)
+  int N, n_leds, B, C, h, W;
+  float lr_obj, lr_zern, lr_def, lr_gam, lr_off, b1, b2, eps;
+  float offset_bound;
+  const long long* t_base;  // Adam steps taken before this launch sequence
+  int step_off;             // this step's position in the sequence
+  unsigned learn;
+  double* loss_slot;        // batch loss of this step
+  double* epoch_loss;       // running FP64 sum
+  int* err;
+  int assemble;             // 1: write gradients (g_obj, g_sc) instead of updating
+  float2* g_obj;            // [N][N] column-major, zeroed by the caller
+  float* g_sc;              // [15 + 3 n_leds]
+};
+
+// Cluster size used for low-res side m (CTAs cooperating on one LED image).
+int led_cluster_size(int m);
+size_t led_smem_bytes(int m, int W);
+cudaError_t led_prepare(int m, int W);
+cudaError_t launch_led(int m, const LedArgs& a, cudaStream_t s);
+cudaError_t launch_update(const UpdArgs& a, cudaStream_t s);
+
+// Field kernels (initialisation, object transforms, layout changes).
+cudaError_t launch_upsample_centre(const float* I, int m, int s, float2* out_rowmajor, cudaStream_t st);
+cudaError_t launch_fft_rows(float2* data, int N, const float2* twN, int dir, cudaStream_t st);
+cudaError_t launch_fft_cols_centre(const float2* rows, float2* Ot, int N, const float2* twN, float scale,
+                                   cudaStream_t st);
+cudaError_t launch_transpose(const float2* in, float2* out, int N, cudaStream_t st);
+
+}  // namespace fpmk

@@ -1,0 +1,274 @@
+"""ctypes binding of the GB300 Batch-FPM engine (include/fpm.h).
+
+Argument marshalling only: every computation runs in the CUDA library. Arrays
+may be numpy arrays (host) or torch tensors (host or CUDA); the library infers
+the copy direction from unified addressing. Importing works without a GPU;
+creating an engine needs the built library and a CUDA device, and fails with
+FpmError otherwise (there is no fallback path).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libfpm_gb300.so")
+
+FPM_OK = 0
+ERRORS = {-1: "FPM_ERR_ARG", -2: "FPM_ERR_SHAPE", -3: "FPM_ERR_RANGE", -4: "FPM_ERR_OOM",
+          -5: "FPM_ERR_NONFINITE", -6: "FPM_ERR_TIMEOUT", -7: "FPM_ERR_CUDA", -8: "FPM_ERR_STATE"}
+EDGE = {"aa": 0, "hard": 1}
+LOSS = {"amplitude": 0, "intensity": 1}
+LEARN = {"object": 1, "zernike": 2, "defocus": 4, "gamma": 8, "offset": 16}
+LOAD_INIT = 1
+
+# every symbol include/fpm.h declares
+EXPORTS = ("fpm_create", "fpm_set_hparams", "fpm_get_hparams", "fpm_load", "fpm_step", "fpm_run",
+           "fpm_epoch_loss", "fpm_profile_run", "fpm_forward", "fpm_backward", "fpm_get", "fpm_set", "fpm_set_object_field",
+           "fpm_state_size", "fpm_get_state", "fpm_set_state", "fpm_dims", "fpm_epoch_permutation",
+           "fpm_destroy", "fpm_last_error")
+
+
+class FpmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_int32), ("n_leds", ctypes.c_int32), ("led_offset", ctypes.c_void_p),
+                ("lambda_um", ctypes.c_float), ("dk_per_um", ctypes.c_float), ("pupil_edge", ctypes.c_int32)]
+
+
+class Hparams(ctypes.Structure):
+    _fields_ = [("lr_object", ctypes.c_float), ("lr_zernike", ctypes.c_float), ("lr_defocus", ctypes.c_float),
+                ("lr_gamma", ctypes.c_float), ("lr_offset", ctypes.c_float), ("beta1", ctypes.c_float),
+                ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("loss", ctypes.c_int32),
+                ("learn_mask", ctypes.c_uint32), ("precision", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the engine library (raises FpmError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise FpmError(-7, f"engine library missing at {LIB_PATH}; build it with "
+                           "paper_2408_13782_gb300.build.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, f32p, dp = ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p
+    sig = {
+        "fpm_create": ([ctypes.POINTER(Geometry), ctypes.c_float, i32, vp, ctypes.POINTER(vp)], i32),
+        "fpm_set_hparams": ([vp, ctypes.POINTER(Hparams)], i32),
+        "fpm_get_hparams": ([vp, ctypes.POINTER(Hparams)], i32),
+        "fpm_load": ([vp, f32p, i32], i32),
+        "fpm_step": ([vp, vp, i32, dp], i32),
+        "fpm_run": ([vp, vp, i32, i32, dp], i32),
+        "fpm_epoch_loss": ([vp, dp, i32], i32),
+        "fpm_profile_run": ([vp, vp, i32, i32, vp, ctypes.c_int64, vp, vp, vp], i32),
+        "fpm_forward": ([vp, vp, i32, f32p], i32),
+        "fpm_backward": ([vp, vp, i32, f32p, f32p, f32p, f32p, f32p, f32p, dp], i32),
+        "fpm_get": ([vp, f32p, f32p, f32p, f32p, f32p], i32),
+        "fpm_set": ([vp, f32p, f32p, f32p, f32p, f32p], i32),
+        "fpm_set_object_field": ([vp, f32p], i32),
+        "fpm_state_size": ([vp], ctypes.c_int64),
+        "fpm_get_state": ([vp, f32p], i32),
+        "fpm_set_state": ([vp, f32p], i32),
+        "fpm_dims": ([vp, vp, vp, vp, vp], i32),
+        "fpm_epoch_permutation": ([i32, ctypes.c_uint64, i32, vp], i32),
+        "fpm_destroy": ([vp], None),
+        "fpm_last_error": ([vp], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def _ptr(x):
+    """Address of a contiguous numpy array or torch tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous, "array must be C-contiguous"
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous(), "tensor must be contiguous"
+        return x.data_ptr()
+    raise TypeError(type(x))
+
+
+def epoch_permutation(n: int, seed: int, epoch: int) -> np.ndarray:
+    out = np.empty(n, np.int32)
+    rc = lib().fpm_epoch_permutation(n, seed & ((1 << 64) - 1), epoch, out.ctypes.data)
+    if rc:
+        raise FpmError(rc, "bad arguments")
+    return out
+
+
+class Engine:
+    """One reconstruction job (object, pupil, defocus, LED parameters, Adam state) on the GPU."""
+
+    def __init__(self, m: int, upsample: int, led_offset, pupil_radius: float, lambda_um: float,
+                 dk_per_um: float, edge: str = "aa", stream=None):
+        L = lib()
+        self._off = np.ascontiguousarray(np.asarray(led_offset, np.float32).reshape(-1, 2))
+        g = Geometry(m, self._off.shape[0], self._off.ctypes.data, lambda_um, dk_per_um, EDGE[edge])
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else 0
+        h = ctypes.c_void_p()
+        rc = L.fpm_create(ctypes.byref(g), pupil_radius, upsample, ctypes.c_void_p(stream), ctypes.byref(h))
+        if rc:
+            raise FpmError(rc, L.fpm_last_error(None).decode())
+        self._h = h
+        self.m, self.s, self.N, self.n_leds = m, upsample, m * upsample, self._off.shape[0]
+        dims = [ctypes.c_int32() for _ in range(4)]
+        L.fpm_dims(h, *(ctypes.byref(d) for d in dims))
+        self.box = dims[3].value
+
+    # -- plumbing --------------------------------------------------------
+    def _check(self, rc):
+        if rc:
+            raise FpmError(rc, lib().fpm_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().fpm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- API ---------------------------------------------------------------
+    def set_hparams(self, lr=None, betas=(0.9, 0.999), eps=1e-8, loss="amplitude", learn=("object",)):
+        lr = dict(object=0.1, zernike=0.01, defocus=0.1, gamma=0.01, offset=0.01, **(lr or {}))
+        mask = 0
+        for k in learn:
+            mask |= LEARN[k]
+        hp = Hparams(lr["object"], lr["zernike"], lr["defocus"], lr["gamma"], lr["offset"],
+                     betas[0], betas[1], eps, LOSS[loss], mask, 0)
+        self._check(lib().fpm_set_hparams(self._h, ctypes.byref(hp)))
+
+    def load(self, stack, init: bool = True):
+        stack = _f32(stack)
+        self._check(lib().fpm_load(self._h, _ptr(stack), LOAD_INIT if init else 0))
+
+    def step(self, batch, loss: bool = True) -> float | None:
+        b = np.ascontiguousarray(np.asarray(batch, np.int32))
+        out = ctypes.c_double() if loss else None
+        self._check(lib().fpm_step(self._h, b.ctypes.data, b.size, ctypes.byref(out) if loss else None))
+        return out.value if loss else None
+
+    def run(self, schedule, losses=True):
+        """schedule: [n_steps, B] int32 (host). losses: True -> numpy array,
+        a CUDA tensor [n_steps] float64 -> filled asynchronously, False -> none."""
+        s = np.ascontiguousarray(np.asarray(schedule, np.int32))
+        assert s.ndim == 2
+        if losses is True:
+            out = np.empty(s.shape[0], np.float64)
+            self._check(lib().fpm_run(self._h, s.ctypes.data, s.shape[0], s.shape[1], out.ctypes.data))
+            return out
+        dst = _ptr(losses) if losses is not False and losses is not None else None
+        self._check(lib().fpm_run(self._h, s.ctypes.data, s.shape[0], s.shape[1], dst))
+        return losses if dst else None
+
+    def profile_run(self, schedule, flush=None):
+        """Timed steps (see fpm_profile_run). flush: a CUDA tensor cleared before every
+        step, or None. Returns per-step ms of (per-LED kernel, update kernel, step)."""
+        s = np.ascontiguousarray(np.asarray(schedule, np.int32))
+        n = s.shape[0]
+        led, upd, stp = (np.empty(n, np.float32) for _ in range(3))
+        fb = flush.numel() * flush.element_size() if flush is not None else 0
+        self._check(lib().fpm_profile_run(self._h, s.ctypes.data, n, s.shape[1], _ptr(flush), fb,
+                                          led.ctypes.data, upd.ctypes.data, stp.ctypes.data))
+        return led, upd, stp
+
+    def epoch_loss(self, reset=False) -> float:
+        out = ctypes.c_double()
+        self._check(lib().fpm_epoch_loss(self._h, ctypes.byref(out), int(reset)))
+        return out.value
+
+    def forward(self, idx, out=None):
+        b = np.ascontiguousarray(np.asarray(idx, np.int32))
+        if out is None:
+            out = np.empty((b.size, self.m, self.m), np.float32)
+        self._check(lib().fpm_forward(self._h, b.ctypes.data, b.size, _ptr(out)))
+        return out
+
+    def backward(self, idx, dL_dI=None, want_object=True):
+        b = np.ascontiguousarray(np.asarray(idx, np.int32))
+        gO = np.empty((self.N, self.N, 2), np.float32) if want_object else None
+        gz = np.empty(14, np.float32)
+        gd = np.empty(1, np.float32)
+        gg = np.empty(self.n_leds, np.float32)
+        go = np.empty((self.n_leds, 2), np.float32)
+        loss = ctypes.c_double()
+        up = _f32(dL_dI) if dL_dI is not None and isinstance(dL_dI, np.ndarray) else dL_dI
+        self._check(lib().fpm_backward(self._h, b.ctypes.data, b.size, _ptr(up), _ptr(gO), _ptr(gz),
+                                       _ptr(gd), _ptr(gg), _ptr(go), ctypes.byref(loss)))
+        return dict(object=None if gO is None else gO[..., 0] + 1j * gO[..., 1].astype(np.float64),
+                    zernike=gz, defocus=float(gd[0]), gamma=gg, offset=go, loss=loss.value)
+
+    def get(self, object=True):
+        O = np.empty((self.N, self.N, 2), np.float32) if object else None
+        z = np.empty(14, np.float32)
+        d = np.empty(1, np.float32)
+        g = np.empty(self.n_leds, np.float32)
+        o = np.empty((self.n_leds, 2), np.float32)
+        self._check(lib().fpm_get(self._h, _ptr(O), _ptr(z), _ptr(d), _ptr(g), _ptr(o)))
+        return dict(object=None if O is None else O[..., 0] + 1j * O[..., 1].astype(np.float64),
+                    zernike=z, defocus=float(d[0]), gamma=g, offset=o)
+
+    def get_object_into(self, tensor):
+        """Copy O into a CUDA tensor [N, N, 2] float32 without a host round trip."""
+        self._check(lib().fpm_get(self._h, _ptr(tensor), None, None, None, None))
+
+    def set(self, object=None, zernike=None, defocus=None, gamma=None, offset=None):
+        O = None
+        if object is not None:
+            O = _f32(np.stack([np.real(object), np.imag(object)], -1)) if np.iscomplexobj(object) else _f32(object)
+        z = None if zernike is None else _f32(zernike)
+        d = None if defocus is None else _f32(np.array([defocus]))
+        g = None if gamma is None else _f32(gamma)
+        o = None if offset is None else _f32(offset)
+        self._check(lib().fpm_set(self._h, _ptr(O), _ptr(z), _ptr(d), _ptr(g), _ptr(o)))
+
+    def set_object_field(self, o):
+        arr = _f32(np.stack([np.real(o), np.imag(o)], -1))
+        self._check(lib().fpm_set_object_field(self._h, _ptr(arr)))
+
+    def state_size(self) -> int:
+        return int(lib().fpm_state_size(self._h))
+
+    def get_state(self) -> np.ndarray:
+        st = np.empty(self.state_size(), np.float32)
+        self._check(lib().fpm_get_state(self._h, st.ctypes.data))
+        return st
+
+    def set_state(self, st):
+        st = _f32(st)
+        self._check(lib().fpm_set_state(self._h, st.ctypes.data))
+
+
+def _f32(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.contiguous()
+    return np.ascontiguousarray(np.asarray(x, np.float32))

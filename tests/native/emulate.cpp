@@ -1,0 +1,57 @@
+// CPU emulation of the engine's device helpers (FFT passes, Zernike
+// polynomials, pupil). Built and run by tests/test_device_helpers_cpu.py,
+// which compares the printed values against numpy and the FP64 oracle.
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
+#include "device.cuh"
+
+using namespace fpmk;
+
+template <int M>
+static void run_fft() {
+  std::vector<float2> tw(M), buf(M);
+  for (int t = 0; t < M; ++t) {
+    const double a = -2.0 * M_PI * t / M;
+    tw[t] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  for (int dir = -1; dir <= 1; dir += 2) {
+    for (int t = 0; t < M; ++t)
+      buf[t] = make_float2((float)std::sin(0.37 * t + 0.1 * M), (float)std::cos(0.91 * t) - 0.25f);
+    if (dir < 0) fft_group_emulate<M, -1>(buf.data(), tw.data());
+    else fft_group_emulate<M, +1>(buf.data(), tw.data());
+    std::printf("fft %d %d", M, dir);
+    for (int t = 0; t < M; ++t) std::printf(" %.9g %.9g", buf[t].x, buf[t].y);
+    std::printf("\n");
+  }
+}
+
+int main() {
+  run_fft<16>();
+  run_fft<32>();
+  run_fft<64>();
+  run_fft<128>();
+  run_fft<256>();
+  for (int i = 0; i < 40; ++i) {
+    const float x = (float)std::sin(1.3 * i) * 1.05f, y = (float)std::cos(0.7 * i + 0.2) * 0.9f;
+    Zern z;
+    zernike_eval(x, y, z);
+    std::printf("zern %.9g %.9g", x, y);
+    for (int j = 0; j < 14; ++j) std::printf(" %.9g %.9g %.9g", z.v[j], z.dx[j], z.dy[j]);
+    std::printf("\n");
+  }
+  // pupil value on a few q for fixed coefficients
+  float zc[14];
+  for (int j = 0; j < 14; ++j) zc[j] = 0.3f * (float)std::sin(2.1 * j + 0.3);
+  const float R = 10.f, lambda = 0.532f, dk = 1.f / (32 * 0.6f), zz = 2.5f;
+  for (int edge = 0; edge < 2; ++edge) {
+    PupilConst P{R, 1.f / R, 1.f / lambda, dk * dk, edge};
+    for (int i = 0; i < 60; ++i) {
+      const float qy = (float)(std::sin(0.9 * i) * 11.0), qx = (float)(std::cos(1.7 * i) * 11.0);
+      const float2 Mv = pupil_value(qy, qx, P, zc, zz);
+      std::printf("pupil %d %.9g %.9g %.9g %.9g\n", edge, qy, qx, Mv.x, Mv.y);
+    }
+  }
+  return 0;
+}

@@ -1,0 +1,72 @@
+"""CPU checks of the engine's device helpers, emulated on the host.
+
+The FFT pass code, the Cartesian Zernike table and the pupil function of
+the CUDA engine are host-callable; a small C++ program runs them on the CPU
+and the values are compared with numpy's FFT and the FP64 oracle.
+"""
+
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle as orc
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+CSRC = os.path.join(ROOT, "paper_2408_13782_gb300", "csrc")
+
+
+@pytest.fixture(scope="module")
+def emulated(tmp_path_factory):
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("no host C++ compiler")
+    exe = str(tmp_path_factory.mktemp("emu") / "emulate")
+    cuda_inc = os.environ.get("CUDA_HOME", "/usr/local/cuda") + "/include"
+    subprocess.run([gxx, "-O1", "-std=c++17", "-I", CSRC, "-I", cuda_inc,
+                    os.path.join(ROOT, "tests", "native", "emulate.cpp"), "-o", exe, "-lm"],
+                   check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    rows = {}
+    for line in out.splitlines():
+        tag, *vals = line.split()
+        rows.setdefault(tag, []).append(vals)
+    return rows
+
+
+def test_fft_passes_match_numpy(emulated):
+    for vals in emulated["fft"]:
+        M, d = int(vals[0]), int(vals[1])
+        got = np.array(vals[2:], float).view(complex)
+        t = np.arange(M)
+        x = np.sin(0.37 * t + 0.1 * M).astype(np.float32) + 1j * (np.cos(0.91 * t).astype(np.float32) - 0.25)
+        ref = np.fft.fft(x) if d < 0 else np.fft.ifft(x) * M
+        err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+        assert err < 2e-6, (M, d, err)
+
+
+def test_zernike_table_matches_oracle(emulated):
+    for vals in emulated["zern"]:
+        v = np.array(vals, float)
+        x, y = v[0], v[1]
+        tab = v[2:].reshape(14, 3)
+        for j in range(2, 16):
+            gx, gy = orc.zernike_grad(j, x, y)
+            np.testing.assert_allclose(tab[j - 2], [orc.zernike(j, x, y), gx, gy], rtol=2e-6, atol=2e-6,
+                                       err_msg=f"Z{j}")
+
+
+def test_pupil_matches_oracle(emulated):
+    zc = 0.3 * np.sin(2.1 * np.arange(14) + 0.3)
+    R, lam, dk, z = 10.0, 0.532, 1.0 / (32 * 0.6), 2.5
+    for vals in emulated["pupil"]:
+        edge = int(vals[0])
+        qy, qx, re, im = (float(v) for v in vals[1:])
+        # evaluate the oracle's pupil on a 1x1 grid: p = 0, delta = -q
+        g = orc.Geometry(2, 2, np.zeros((1, 2)), R, "hard" if edge else "aa", lam, dk)
+        g.m = 1
+        P = orc.pupil(g, zc, z, [-qy, -qx])
+        ref = P["M"][0, 0]
+        assert abs(complex(re, im) - ref) < 2e-5, (edge, qy, qx, complex(re, im), ref)

@@ -1,0 +1,319 @@
+"""GPU engine vs FP64 oracle, through the C ABI, on the same seeded inputs.
+
+Tolerances: relative L2 <= 1e-5 on forward intensities, <= 1e-4 on every
+gradient, <= 1e-3 on the object after a fixed number of epochs (FP32 path).
+Each measured error is recorded for the parity report.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as orc
+from paper_2408_13782_gb300 import FpmError
+from synth import recipes as S
+from tests.gpu_common import (engine_for, hparams_to_engine, multiparam_problem, push, record, rel_l2,
+                              simulate)
+
+pytestmark = pytest.mark.gpu
+
+TOL_I, TOL_G, TOL_O = 1e-5, 1e-4, 1e-3
+
+
+def _grad_errors(tag, eng_g, ref_g, idx, n_leds):
+    errs = {}
+    errs["object"] = rel_l2(eng_g["object"], ref_g["object"])
+    errs["zernike"] = rel_l2(eng_g["zernike"], ref_g["zernike"])
+    errs["defocus"] = rel_l2([eng_g["defocus"]], [ref_g["defocus"]])
+    errs["gamma"] = rel_l2(eng_g["gamma"], ref_g["gamma"])
+    errs["offset"] = rel_l2(eng_g["offset"], ref_g["offset"])
+    for k, v in errs.items():
+        record(f"{tag}.grad.{k}", v)
+    return errs
+
+
+# --------------------------------------------------------------------------
+# forward model
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m,edge", [(32, "aa"), (64, "hard"), (64, "aa"), (128, "aa"), (256, "aa")])
+def test_forward_multiparam(m, edge):
+    c, I, g, prm, O = multiparam_problem(m=m, edge=edge, grid=5 if m < 256 else 3)
+    eng = engine_for(g)
+    push(eng, O, prm)
+    idx = np.arange(g.n_leds)
+    got = eng.forward(idx)
+    ref = orc.forward(O, prm, g, idx)
+    err = rel_l2(got, ref)
+    record(f"forward.m{m}.{edge}", err)
+    assert err <= TOL_I
+    for i in idx:   # per image, dark field included
+        assert rel_l2(got[i], ref[i]) <= 10 * TOL_I
+
+
+def test_forward_config1_literal():
+    c = S.config("c1")
+    I, o, g_n, g_t, prm_t = simulate(c)
+    eng = engine_for(g_t)
+    eng.set_object_field(o)
+    got = eng.forward(np.arange(g_t.n_leds))
+    err = rel_l2(got, I)
+    record("forward.c1", err)
+    assert err <= TOL_I
+
+
+# --------------------------------------------------------------------------
+# gradients (built-in loss and upstream dL/dI)
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m,loss", [(64, "amplitude"), (64, "intensity"), (128, "amplitude"), (32, "amplitude")])
+def test_gradients_builtin_loss(m, loss):
+    c, I, g, prm, O = multiparam_problem(m=m)
+    eng = engine_for(g)
+    eng.set_hparams(loss=loss)
+    eng.load(I, init=False)
+    push(eng, O, prm)
+    idx = [3, 0, 11, 7][: min(4, g.n_leds)]
+    got = eng.backward(idx)
+    L, ref, _ = orc.loss_and_grad(O, prm, g, idx, I.astype(np.float64), loss)
+    record(f"grad.m{m}.{loss}.loss", abs(got["loss"] - L) / L)
+    assert abs(got["loss"] - L) <= TOL_I * L
+    errs = _grad_errors(f"m{m}.{loss}", got, ref, idx, g.n_leds)
+    for k, v in errs.items():
+        assert v <= TOL_G, (k, v)
+
+
+def test_gradients_upstream():
+    c, I, g, prm, O = multiparam_problem(m=64, seed=9)
+    eng = engine_for(g)
+    push(eng, O, prm)
+    idx = [1, 6, 2]
+    rng = np.random.default_rng(3)
+    w = rng.normal(size=(len(idx), g.m, g.m)).astype(np.float32)
+    got = eng.backward(idx, dL_dI=w)
+    Iw = np.zeros((g.n_leds, g.m, g.m))
+    Iw[idx] = w
+    _, ref, _ = orc.loss_and_grad(O, prm, g, idx, Iw, "linear")
+    errs = _grad_errors("upstream", got, ref, idx, g.n_leds)
+    for k, v in errs.items():
+        assert v <= TOL_G, (k, v)
+
+
+# --------------------------------------------------------------------------
+# initialisation and object transforms
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("m,s", [(64, 4), (256, 4), (128, 8)])
+def test_init_object(m, s):
+    rng = np.random.default_rng(m + s)
+    nominal = np.array([[0.0, 0.0], [0.0, 8.0 * m / 64]])
+    g = orc.Geometry(m * s, m, nominal, 14.0 * m / 64, "aa", 0.532, 1 / (m * 0.6))
+    stack = (rng.random((2, m, m)) * 2 - 0.1).astype(np.float32)   # a few negatives: clamped
+    eng = engine_for(g)
+    eng.load(stack, init=True)
+    got = eng.get()
+    ref = orc.init_object(stack[g.centre_led].astype(np.float64), s)
+    err = rel_l2(got["object"], ref)
+    record(f"init.m{m}.s{s}", err)
+    assert err <= TOL_I
+    assert np.all(got["gamma"] == 1) and np.all(got["zernike"] == 0) and got["defocus"] == 0
+
+
+def test_object_field_and_roundtrip():
+    rng = np.random.default_rng(2)
+    m, s = 64, 8
+    g = orc.Geometry(m * s, m, np.zeros((1, 2)), 10.0, "aa", 0.532, 1 / (m * 0.6))
+    o = S.make_object(m * s, 4)
+    eng = engine_for(g)
+    eng.set_object_field(o)
+    got = eng.get()["object"]
+    err = rel_l2(got, orc.object_spectrum(o, s))
+    record("object_field.n512", err)
+    assert err <= TOL_I
+    X = (rng.normal(size=(m * s, m * s)) + 1j * rng.normal(size=(m * s, m * s))).astype(np.complex64)
+    eng.set(object=X)
+    assert np.array_equal(eng.get()["object"].astype(np.complex64), X)
+
+
+# --------------------------------------------------------------------------
+# update steps and trajectories
+# --------------------------------------------------------------------------
+
+def _oracle_and_engine(c, I, g, hp):
+    rec = orc.Reconstruction(g, I, hp)
+    eng = engine_for(g)
+    hparams_to_engine(eng, hp)
+    eng.load(I, init=True)
+    return rec, eng
+
+
+def test_steps_multiparam_all_learnable():
+    c, I, g_t, prm, O = multiparam_problem(m=64, seed=21)
+    g = orc.Geometry(c.N, c.m, S.led_grid(c.grid, c.pitch, c.jitter, c.seed)[0], c.R, c.edge,
+                     c.lambda_um, c.dk_per_um)
+    hp = orc.Hparams(lr=dict(object=0.5, zernike=0.01, defocus=0.1, gamma=0.01, offset=0.01),
+                     learn=("object", "zernike", "defocus", "gamma", "offset"))
+    rec, eng = _oracle_and_engine(c, I, g, hp)
+    err0 = rel_l2(eng.get()["object"], rec.O)
+    record("steps.init", err0)
+    assert err0 <= TOL_I
+    sched = S.schedule(g.n_leds, 4, 2, seed=3)
+    for k, b in enumerate(sched[:6]):
+        L_ref = rec.step(b)
+        L_got = eng.step(b)
+        assert abs(L_got - L_ref) <= 1e-5 * L_ref + 1e-12, (k, L_got, L_ref)
+        st = eng.get()
+        eo = rel_l2(st["object"], rec.O)
+        record(f"steps.k{k}.object", eo)
+        assert eo <= 1e-4, (k, eo)
+        for name, ref in (("zernike", rec.prm.zernike), ("gamma", rec.prm.gamma), ("offset", rec.prm.offset)):
+            assert rel_l2(st[name], ref) <= 1e-4, (k, name)
+        assert abs(st["defocus"] - rec.prm.defocus) <= 1e-4 * max(1.0, abs(rec.prm.defocus))
+
+
+def test_trajectory_config1_30_epochs():
+    c = S.config("c1")
+    I, o, g_n, g_t, prm_t = simulate(c)
+    hp = orc.Hparams(lr=dict(c.lr), learn=c.learn)
+    rec, eng = _oracle_and_engine(c, I, g_n, hp)
+    sched = S.schedule(g_n.n_leds, c.B, c.epochs, c.seed)
+    nb = -(-g_n.n_leds // c.B)
+    losses_ref = rec.run(sched)
+    # the engine runs each epoch's full batches as one graph and the short last batch on its own
+    losses_got = []
+    for e in range(c.epochs):
+        ep = sched[e * nb:(e + 1) * nb]
+        full = np.stack([b for b in ep if len(b) == c.B])
+        losses_got.extend(eng.run(full).tolist())
+        for b in ep:
+            if len(b) != c.B:
+                losses_got.append(eng.step(b))
+    eo = rel_l2(eng.get()["object"], rec.O)
+    el = rel_l2(losses_got, losses_ref)
+    record("trajectory.c1.object", eo)
+    record("trajectory.c1.losses", el)
+    assert eo <= TOL_O
+    assert el <= TOL_O
+    e_loss = eng.epoch_loss()
+    assert abs(e_loss - rec.epoch_loss) <= 1e-3 * rec.epoch_loss
+
+
+def test_run_equals_steps_bitwise_and_deterministic():
+    c, I, g_t, prm, O = multiparam_problem(m=64, seed=31)
+    hp = orc.Hparams(lr=dict(object=0.5), learn=("object", "zernike", "defocus", "gamma", "offset"))
+    sched = np.stack(S.schedule(g_t.n_leds, 5, 1, seed=4)[:5])
+    outs = []
+    for mode in ("run", "run", "steps"):
+        eng = engine_for(g_t)
+        hparams_to_engine(eng, hp)
+        eng.load(I, init=True)
+        if mode == "run":
+            eng.run(sched)
+        else:
+            for b in sched:
+                eng.step(b, loss=False)
+        outs.append(eng.get_state())
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
+
+
+def test_checkpoint_resume_bitwise():
+    c, I, g_t, prm, O = multiparam_problem(m=64, seed=41)
+    hp = orc.Hparams(lr=dict(object=0.5), learn=("object", "zernike", "defocus", "gamma", "offset"))
+    sched = np.stack(S.schedule(g_t.n_leds, 5, 2, seed=5)[:8])
+    a = engine_for(g_t); hparams_to_engine(a, hp); a.load(I)
+    a.run(sched)
+    ref = a.get_state()
+    b = engine_for(g_t); hparams_to_engine(b, hp); b.load(I)
+    b.run(sched[:3])
+    st = b.get_state()
+    c2 = engine_for(g_t); hparams_to_engine(c2, hp); c2.load(I, init=False)
+    c2.set_state(st)
+    c2.run(sched[3:])
+    assert np.array_equal(c2.get_state(), ref)
+
+
+def test_global_and_sequential_modes():
+    # Eq. (6): one batch of every LED; Eq. (7): batches of one in fixed order.
+    c, I, g_t, prm, O = multiparam_problem(m=32, grid=3, seed=51)
+    hp = orc.Hparams(lr=dict(object=0.3), learn=("object",))
+    for B in (g_t.n_leds, 1):
+        sched = S.schedule(g_t.n_leds, B, 2, seed=0, shuffle=False)
+        rec, eng = _oracle_and_engine(c, I, g_t, hp)
+        ref = rec.run(sched)
+        got = eng.run(np.stack(sched))
+        assert rel_l2(got, ref) <= 1e-5
+        assert rel_l2(eng.get()["object"], rec.O) <= 1e-4
+
+
+# --------------------------------------------------------------------------
+# full-size paper-scale workload (1024^2 object, 256^2 images, 225 LEDs, B=16)
+# --------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def c2_problem():
+    c = S.config("c2")
+    I, o, g_n, g_t, prm_t = simulate(c)
+    return c, I, o, g_n, g_t, prm_t
+
+
+def test_c2_forward_sampled(c2_problem):
+    c, I, o, g_n, g_t, prm_t = c2_problem
+    eng = engine_for(g_t)
+    eng.set_object_field(o)
+    push(eng, orc.object_spectrum(o, c.s), prm_t)
+    idx = [0, 1, 9, 30, 100, 150, 200, 224]
+    got = eng.forward(idx)
+    ref = orc.forward(orc.object_spectrum(o, c.s), prm_t, g_t, idx)
+    err = rel_l2(got, ref)
+    record("c2.forward", err)
+    assert err <= TOL_I
+
+
+def test_c2_batch_gradients_and_steps(c2_problem):
+    c, I, o, g_n, g_t, prm_t = c2_problem
+    hp = orc.Hparams(lr=dict(c.lr), learn=c.learn)
+    rec, eng = _oracle_and_engine(c, I, g_n, hp)
+    sched = S.schedule(g_n.n_leds, c.B, 1, c.seed)
+    b0 = sched[0]
+    got = eng.backward(b0)
+    L, ref, _ = orc.loss_and_grad(rec.O, rec.prm, g_n, b0, I.astype(np.float64))
+    record("c2.loss", abs(got["loss"] - L) / L)
+    assert abs(got["loss"] - L) <= TOL_I * L
+    errs = _grad_errors("c2", got, ref, b0, g_n.n_leds)
+    for k, v in errs.items():
+        assert v <= TOL_G, (k, v)
+    for k in range(3):
+        rec.step(sched[k])
+    eng.run(np.stack(sched[:3]))
+    eo = rel_l2(eng.get()["object"], rec.O)
+    record("c2.steps3.object", eo)
+    assert eo <= 1e-4
+
+
+# --------------------------------------------------------------------------
+# edge cases and errors
+# --------------------------------------------------------------------------
+
+def test_errors_and_edge_cases():
+    c, I, g, prm, O = multiparam_problem(m=32, grid=3, seed=61)
+    eng = engine_for(g)
+    with pytest.raises(FpmError) as e:
+        eng.step([0, 1])                       # before load
+    assert e.value.code == -8
+    eng.load(I)
+    for bad, code in (([0, 0], -3), ([9], -3), ([-1], -3), ([], -2)):
+        with pytest.raises(FpmError) as e:
+            eng.step(bad)
+        assert e.value.code == code, bad
+    with pytest.raises(FpmError):
+        eng.set(offset=np.full((g.n_leds, 2), 3.0))
+    # ragged batch sizes back to back, B = 1 and B = n_leds
+    for b in ([4], [0, 1, 2, 3, 4, 5, 6, 7, 8], [8, 2]):
+        assert np.isfinite(eng.step(b))
+    # a non-finite measurement surfaces as FPM_ERR_NONFINITE
+    bad = I.copy()
+    bad[0, 3, 3] = np.inf
+    eng.load(bad, init=False)
+    with pytest.raises(FpmError) as e:
+        eng.step([0])
+    assert e.value.code == -5

@@ -40,7 +40,7 @@ def _check(num, ana, what, rtol=1e-6, scale=1.0):
     assert abs(num - ana) <= rtol * max(abs(ana), scale), f"{what}: fd {num} vs analytic {ana}"
 
 
-@pytest.mark.parametrize("loss", ["amplitude", "intensity"])
+@pytest.mark.parametrize("loss", ["amplitude", "intensity", "linear"])
 def test_gradients_match_central_differences(loss):
     g, prm, O, I, idx, loss = _problem(loss=loss)
     L0, gr, _ = orc.loss_and_grad(O, prm, g, idx, I, loss)
