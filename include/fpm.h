@@ -140,8 +140,8 @@ int fpm_step(fpm_handle* h, const int32_t* batch_idx, int32_t B, double* loss_ou
  * the call waits for the run to finish. */
 int fpm_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int32_t B, double* losses_out);
 
-/* Timing variant of fpm_run for profiling: the same steps, captured as one graph,
- * with, before every step, a clear of flush_bytes of the device buffer `flush`
+/* Timing variant of fpm_run for profiling: the same steps, launched directly on the
+ * engine's stream (not as a graph), with, before every step, a clear of flush_bytes of the device buffer `flush`
  * (nullable: no clear; a buffer larger than the L2 cache evicts the working set so
  * each step starts cold), and CUDA events on the engine's stream around each step
  * and each of its two kernels. Outputs (host, [n_steps] each, nullable): elapsed

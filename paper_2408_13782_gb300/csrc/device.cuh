@@ -69,6 +69,71 @@ FPM_HD void zernike_eval(float x, float y, Zern& z) {
   z.dy[13] = s10 * (4.f * x2 * x - 12.f * x * y2);
 }
 
+// The same polynomials as combinations of the 15 monomials x^a y^b with
+// a + b <= 4, ordered by degree d = a + b and then by b: monomial index
+// d(d+1)/2 + b, i.e. 1, x, y, x2, xy, y2, x3, x2y, xy2, y3, x4, x3y, x2y2,
+// xy3, y4. Row j-2 holds the coefficients of Z_j.
+#define FPM_S3 1.7320508075688772f
+#define FPM_S5 2.2360679774997896f
+#define FPM_S6 2.449489742783178f
+#define FPM_S8 2.8284271247461903f
+#define FPM_S10 3.1622776601683795f
+#define FPM_ZERN_MONO_TABLE                                                                          \
+  {                                                                                                  \
+    /* Z2  */ {0, 2, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0},                                         \
+    /* Z3  */ {0, 0, 2, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0},                                         \
+    /* Z4  */ {-FPM_S3, 0, 0, 2 * FPM_S3, 0, 2 * FPM_S3, 0, 0, 0, 0, 0, 0, 0, 0, 0},                 \
+    /* Z5  */ {0, 0, 0, 0, 2 * FPM_S6, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0},                                \
+    /* Z6  */ {0, 0, 0, FPM_S6, 0, -FPM_S6, 0, 0, 0, 0, 0, 0, 0, 0, 0},                             \
+    /* Z7  */ {0, 0, -2 * FPM_S8, 0, 0, 0, 0, 3 * FPM_S8, 0, 3 * FPM_S8, 0, 0, 0, 0, 0},             \
+    /* Z8  */ {0, -2 * FPM_S8, 0, 0, 0, 0, 3 * FPM_S8, 0, 3 * FPM_S8, 0, 0, 0, 0, 0, 0},             \
+    /* Z9  */ {0, 0, 0, 0, 0, 0, 0, 3 * FPM_S8, 0, -FPM_S8, 0, 0, 0, 0, 0},                          \
+    /* Z10 */ {0, 0, 0, 0, 0, 0, FPM_S8, 0, -3 * FPM_S8, 0, 0, 0, 0, 0, 0},                          \
+    /* Z11 */ {FPM_S5, 0, 0, -6 * FPM_S5, 0, -6 * FPM_S5, 0, 0, 0, 0, 6 * FPM_S5, 0, 12 * FPM_S5, 0, 6 * FPM_S5}, \
+    /* Z12 */ {0, 0, 0, -3 * FPM_S10, 0, 3 * FPM_S10, 0, 0, 0, 0, 4 * FPM_S10, 0, 0, 0, -4 * FPM_S10},  \
+    /* Z13 */ {0, 0, 0, 0, -6 * FPM_S10, 0, 0, 0, 0, 0, 0, 8 * FPM_S10, 0, 8 * FPM_S10, 0},         \
+    /* Z14 */ {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, FPM_S10, 0, -6 * FPM_S10, 0, FPM_S10},                  \
+    /* Z15 */ {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 4 * FPM_S10, 0, -4 * FPM_S10, 0},                    \
+  }
+#if defined(__CUDACC__)
+static __constant__ float kZernMonoDev[14][15] = FPM_ZERN_MONO_TABLE;
+#endif
+static const float kZernMonoHost[14][15] = FPM_ZERN_MONO_TABLE;
+
+// Coefficient of monomial m in Z_{j+2}.
+FPM_HD float zern_mono(int j, int m) {
+#if defined(__CUDA_ARCH__)
+  return kZernMonoDev[j][m];
+#else
+  return kZernMonoHost[j][m];
+#endif
+}
+
+FPM_HD void monomials(float x, float y, float (&mo)[15]) {
+  const float x2 = x * x, y2 = y * y, xy = x * y;
+  mo[0] = 1.f; mo[1] = x; mo[2] = y;
+  mo[3] = x2; mo[4] = xy; mo[5] = y2;
+  mo[6] = x2 * x; mo[7] = x2 * y; mo[8] = x * y2; mo[9] = y2 * y;
+  mo[10] = x2 * x2; mo[11] = x2 * xy; mo[12] = x2 * y2; mo[13] = xy * y2; mo[14] = y2 * y2;
+}
+
+// For aberration coefficients c[14] (Noll 2..15): theta = sum_m K[m] mo[m],
+// d theta/dx = sum_{m<10} Dx[m] mo[m], d theta/dy = sum_{m<10} Dy[m] mo[m].
+FPM_HD void theta_poly(const float* c, float (&K)[15], float (&Dx)[10], float (&Dy)[10]) {
+  for (int m = 0; m < 15; ++m) {
+    float s = 0.f;
+    for (int j = 0; j < 14; ++j) s = fmaf(c[j], zern_mono(j, m), s);
+    K[m] = s;
+  }
+  for (int m = 0; m < 10; ++m) Dx[m] = Dy[m] = 0.f;
+  for (int d = 1; d <= 4; ++d)
+    for (int b = 0; b <= d; ++b) {
+      const int a = d - b, m = d * (d + 1) / 2 + b;
+      if (a > 0) Dx[(d - 1) * d / 2 + b] += (float)a * K[m];        // x^(a-1) y^b
+      if (b > 0) Dy[(d - 1) * d / 2 + (b - 1)] += (float)b * K[m];  // x^a y^(b-1)
+    }
+}
+
 // Per-launch pupil constants.
 struct PupilConst {
   float R, Rinv, inv_lambda, dk2;
@@ -109,16 +174,34 @@ FPM_HD float2 pupil_value(float qy, float qx, const PupilConst& P,
   return make_float2(A * cs, A * sn);
 }
 
+// The same pupil value with the aberration phase taken from its monomial
+// coefficients K = poly[0..14] (see theta_poly).
+FPM_HD float2 pupil_value_poly(float qy, float qx, const PupilConst& P, const float* __restrict__ poly,
+                               float z) {
+  const float A = pupil_amp(qy, qx, P);
+  if (A == 0.f) return make_float2(0.f, 0.f);
+  float mo[15];
+  monomials(qx * P.Rinv, qy * P.Rinv, mo);
+  float th = 0.f;
+  for (int q = 0; q < 15; ++q) th = fmaf(poly[q], mo[q], th);
+  float root;
+  const float kap = defocus_kappa(qx * qx + qy * qy, P, &root);
+  float sn, cs;
+  sincosf(fmaf(z, kap, th), &sn, &cs);
+  return make_float2(A * cs, A * sn);
+}
+
 // ---------------------------------------------------------------------------
-// FFT: Stockham autosort over a shared-memory buffer of M points, run by a
-// group of G = M/8 consecutive threads of one warp (so M <= 256). Each pass
-// reads 8 (radix 8), 2x4 (radix-4 tail) or 4x2 (radix-2 tail) points per
-// thread into registers, applies twiddles W_{R Ns}^{r k} (k = butterfly mod
-// Ns), a radix-R DFT, and writes them to (b - k) R + k + r Ns. All threads of
-// the warp call it together; the warp synchronises between the read and write
-// halves of each pass. tw[t] = exp(-2 pi i t / M). DIR = -1: forward
-// (exp(-)), +1: inverse (exp(+)); both unnormalised. The load/store halves
-// are host-callable so the index arithmetic can be emulated on a CPU.
+// FFT: Stockham autosort over a (padded) shared-memory buffer of M points,
+// run by a group of G = M/8 consecutive threads of one warp (so M <= 256).
+// Each pass reads 8 (radix 8), 2x4 (radix-4 tail) or 4x2 (radix-2 tail)
+// points per thread into registers, applies twiddles W_{R Ns}^{r k} (k =
+// butterfly mod Ns), a radix-R DFT, and writes them to (b - k) R + k + r Ns.
+// All threads of the warp call it together; the warp synchronises between the
+// read and write halves of each pass. Twiddle table tw[t] = exp(-2 pi i t/M).
+// DIR = -1: forward (exp(-)), +1: inverse (exp(+)); both unnormalised. The
+// load/store halves are host-callable so the index arithmetic can be emulated
+// on a CPU.
 // ---------------------------------------------------------------------------
 template <int DIR>
 FPM_HD float2 tw_dir(float2 w) { return DIR < 0 ? w : make_float2(w.x, -w.y); }
@@ -173,35 +256,80 @@ struct FftShape {
   static constexpr int TAIL = LOG % 3;            // 0: none, 1: radix 2, 2: radix 4
 };
 
+// Buffers are padded with one point after every 8 (index i stored at
+// i + i/8): with the Stockham read/write strides below every pass is free of
+// shared-memory bank conflicts (to within one doubled bank in the contiguous
+// reads).
+FPM_HD int pidx(int i) { return i + (i >> 3); }
+// 256-point transforms use two radix-16 passes (16 threads x 16 points); for
+// their access pattern one pad point every 16 makes every pass conflict-free.
+FPM_HD int pidx16(int i) { return i + (i >> 4); }
+template <int M>
+FPM_HD int bidx(int i) { return M == 256 ? pidx16(i) : pidx(i); }
+template <int M>
+struct FftBuf {
+  static constexpr int SIZE = M == 256 ? M + M / 16 : M + M / 8;   // padded length of one buffer
+  static constexpr int G = M == 256 ? 16 : M / 8;                   // threads per transform
+};
+
+// Per-thread twiddles: thread j of a group only ever needs W_{R Ns}^{r k}
+// with k = (butterfly index) mod Ns fixed by j, so they are loaded once.
+template <int M>
+struct FftTw {
+  using S = FftShape<M>;
+  static constexpr int N8T = (S::N8 > 1 ? (S::N8 - 1) * 7 : 0);
+  static constexpr int TT = S::TAIL == 2 ? 6 : (S::TAIL == 1 ? 4 : 0);
+  float2 w[(N8T + TT) > 0 ? (N8T + TT) : 1];
+};
+
+// Fill the twiddles of thread j from the table tw[t] = exp(-2 pi i t / M).
+template <int M>
+FPM_HD void fft_twiddles(const float2* tw, int j, FftTw<M>& T) {
+  using S = FftShape<M>;
+  constexpr int G = M / 8;
+  int q = 0, Ns = 8;
+  for (int pass = 1; pass < S::N8; ++pass, Ns *= 8) {
+    const int k = j & (Ns - 1), step = M / (8 * Ns);
+    for (int r = 1; r < 8; ++r) T.w[q++] = tw[r * k * step];
+  }
+  if (S::TAIL == 2) {
+    for (int b = 0; b < 2; ++b) {
+      const int jj = j + b * G, k = jj & (Ns - 1), step = M / (4 * Ns);
+      for (int r = 1; r < 4; ++r) T.w[q++] = tw[r * k * step];
+    }
+  } else if (S::TAIL == 1) {
+    for (int b = 0; b < 4; ++b) {
+      const int jj = j + b * G, k = jj & (Ns - 1), step = M / (2 * Ns);
+      T.w[q++] = tw[k * step];
+    }
+  }
+}
+
 // One radix-8 pass, read half: 8 points of butterfly j, twiddled, transformed.
+// tw points at this pass's 7 twiddles (unused when Ns == 1).
 template <int M, int DIR>
 FPM_HD void r8_load(const float2* buf, const float2* tw, int j, int Ns, float2 (&v)[8]) {
   constexpr int G = M / 8;
-  const int k = j & (Ns - 1);
-  for (int r = 0; r < 8; ++r) v[r] = buf[j + r * G];
-  if (Ns > 1) {
-    const int step = M / (8 * Ns);
-    for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], tw_dir<DIR>(tw[r * k * step]));
-  }
+  for (int r = 0; r < 8; ++r) v[r] = buf[pidx(j + r * G)];
+  if (Ns > 1)
+    for (int r = 1; r < 8; ++r) v[r] = cmul(v[r], tw_dir<DIR>(tw[r - 1]));
   dft8<DIR>(v);
 }
 template <int M>
 FPM_HD void r8_store(float2* buf, int j, int Ns, const float2 (&v)[8]) {
   const int k = j & (Ns - 1);
   const int base = (j - k) * 8 + k;
-  for (int r = 0; r < 8; ++r) buf[base + r * Ns] = v[r];
+  for (int r = 0; r < 8; ++r) buf[pidx(base + r * Ns)] = v[r];
 }
-// radix-4 tail: butterflies j and j + G
+// radix-4 tail: butterflies j and j + G; tw points at 2 x 3 twiddles
 template <int M, int DIR>
 FPM_HD void r4_load(const float2* buf, const float2* tw, int j, int Ns, float2 (&v)[8]) {
   constexpr int G = M / 8;
   for (int b = 0; b < 2; ++b) {
     const int jj = j + b * G;
-    const int k = jj & (Ns - 1);
-    const int step = M / (4 * Ns);
     float2* w = v + 4 * b;
-    for (int r = 0; r < 4; ++r) w[r] = buf[jj + r * (M / 4)];
-    for (int r = 1; r < 4; ++r) w[r] = cmul(w[r], tw_dir<DIR>(tw[r * k * step]));
+    for (int r = 0; r < 4; ++r) w[r] = buf[pidx(jj + r * (M / 4))];
+    for (int r = 1; r < 4; ++r) w[r] = cmul(w[r], tw_dir<DIR>(tw[3 * b + r - 1]));
     dft4<DIR>(w[0], w[1], w[2], w[3]);
   }
 }
@@ -212,19 +340,17 @@ FPM_HD void r4_store(float2* buf, int j, int Ns, const float2 (&v)[8]) {
     const int jj = j + b * G;
     const int k = jj & (Ns - 1);
     const int base = (jj - k) * 4 + k;
-    for (int r = 0; r < 4; ++r) buf[base + r * Ns] = v[4 * b + r];
+    for (int r = 0; r < 4; ++r) buf[pidx(base + r * Ns)] = v[4 * b + r];
   }
 }
-// radix-2 tail: butterflies j + b G, b = 0..3
+// radix-2 tail: butterflies j + b G, b = 0..3; tw points at 4 twiddles
 template <int M, int DIR>
 FPM_HD void r2_load(const float2* buf, const float2* tw, int j, int Ns, float2 (&v)[8]) {
   constexpr int G = M / 8;
   for (int b = 0; b < 4; ++b) {
     const int jj = j + b * G;
-    const int k = jj & (Ns - 1);
-    const int step = M / (2 * Ns);
-    v[2 * b] = buf[jj];
-    v[2 * b + 1] = cmul(buf[jj + M / 2], tw_dir<DIR>(tw[k * step]));
+    v[2 * b] = buf[pidx(jj)];
+    v[2 * b + 1] = cmul(buf[pidx(jj + M / 2)], tw_dir<DIR>(tw[b]));
     dft2<DIR>(v[2 * b], v[2 * b + 1]);
   }
 }
@@ -235,20 +361,91 @@ FPM_HD void r2_store(float2* buf, int j, int Ns, const float2 (&v)[8]) {
     const int jj = j + b * G;
     const int k = jj & (Ns - 1);
     const int base = (jj - k) * 2 + k;
-    buf[base] = v[2 * b];
-    buf[base + Ns] = v[2 * b + 1];
+    buf[pidx(base)] = v[2 * b];
+    buf[pidx(base + Ns)] = v[2 * b + 1];
+  }
+}
+
+// ---- radix 16 (M = 256: two passes, 16 threads per transform) ----
+// 16-point DFT in registers: n = n1 + 4 n2, k = k2 + 4 k1; DFT4 over n2,
+// twiddles W16^(n1 k2), DFT4 over n1.
+template <int DIR>
+FPM_HD void dft16(float2 (&v)[16]) {
+  const float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, h = 0.70710678118654752f;
+  const float d = (float)DIR;
+  float2 y[4][4];
+  for (int n1 = 0; n1 < 4; ++n1) {
+    float2 a0 = v[n1], a1 = v[n1 + 4], a2 = v[n1 + 8], a3 = v[n1 + 12];
+    dft4<DIR>(a0, a1, a2, a3);
+    y[n1][0] = a0; y[n1][1] = a1; y[n1][2] = a2; y[n1][3] = a3;
+  }
+  const float2 w1 = make_float2(c1, d * s1), w2 = make_float2(h, d * h), w3 = make_float2(s1, d * c1);
+  const float2 w6 = make_float2(-h, d * h), w9 = make_float2(-c1, -d * s1);
+  y[1][1] = cmul(y[1][1], w1); y[1][2] = cmul(y[1][2], w2); y[1][3] = cmul(y[1][3], w3);
+  y[2][1] = cmul(y[2][1], w2); y[2][2] = mul_i<DIR>(y[2][2]); y[2][3] = cmul(y[2][3], w6);
+  y[3][1] = cmul(y[3][1], w3); y[3][2] = cmul(y[3][2], w6); y[3][3] = cmul(y[3][3], w9);
+  for (int k2 = 0; k2 < 4; ++k2) {
+    float2 a0 = y[0][k2], a1 = y[1][k2], a2 = y[2][k2], a3 = y[3][k2];
+    dft4<DIR>(a0, a1, a2, a3);
+    v[k2] = a0; v[k2 + 4] = a1; v[k2 + 8] = a2; v[k2 + 12] = a3;
+  }
+}
+
+// Second-pass twiddles of thread j (256 points): tw2[(r-1) * 16 + j] = W256^(r j).
+FPM_HD void fft256_twiddles(const float2* tw, float2* tw2, int j) {
+  for (int r = 1; r < 16; ++r) tw2[(r - 1) * 16 + j] = tw[r * j];
+}
+
+template <int DIR>
+FPM_HD void r16_load(const float2* buf, const float2* tw2, int j, int pass, float2 (&v)[16]) {
+  for (int r = 0; r < 16; ++r) v[r] = buf[pidx16(j + 16 * r)];
+  if (pass == 1)
+    for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw_dir<DIR>(tw2[(r - 1) * 16 + j]));
+  dft16<DIR>(v);
+}
+FPM_HD void r16_store(float2* buf, int j, int pass, const float2 (&v)[16]) {
+  if (pass == 0)
+    for (int r = 0; r < 16; ++r) buf[pidx16(16 * j + r)] = v[r];
+  else
+    for (int r = 0; r < 16; ++r) buf[pidx16(j + 16 * r)] = v[r];
+}
+
+#if defined(__CUDACC__)
+// 256-point transform by 16 threads (half a warp); tw2 in shared memory.
+template <int DIR>
+__device__ __forceinline__ void fft256_group(float2* __restrict__ buf, const float2* __restrict__ tw2, int j) {
+  float2 v[16];
+#pragma unroll
+  for (int pass = 0; pass < 2; ++pass) {
+    r16_load<DIR>(buf, tw2, j, pass, v);
+    __syncwarp();
+    r16_store(buf, j, pass, v);
+    __syncwarp();
+  }
+}
+#endif
+
+template <int DIR>
+inline void fft256_emulate(float2* buf, const float2* tw) {
+  float2 tw2[15 * 16];
+  for (int j = 0; j < 16; ++j) fft256_twiddles(tw, tw2, j);
+  float2 V[16][16];
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int j = 0; j < 16; ++j) r16_load<DIR>(buf, tw2, j, pass, V[j]);
+    for (int j = 0; j < 16; ++j) r16_store(buf, j, pass, V[j]);
   }
 }
 
 #if defined(__CUDACC__)
+// In-place transform of the padded buffer buf by the G threads of a group.
 template <int M, int DIR>
-__device__ __forceinline__ void fft_group(float2* __restrict__ buf, const float2* __restrict__ tw, int j) {
+__device__ __forceinline__ void fft_group(float2* __restrict__ buf, const FftTw<M>& T, int j) {
   using S = FftShape<M>;
   int Ns = 1;
 #pragma unroll
   for (int pass = 0; pass < S::N8; ++pass) {
     float2 v[8];
-    r8_load<M, DIR>(buf, tw, j, Ns, v);
+    r8_load<M, DIR>(buf, pass > 0 ? T.w + (pass - 1) * 7 : T.w, j, Ns, v);
     __syncwarp();
     r8_store<M>(buf, j, Ns, v);
     __syncwarp();
@@ -256,13 +453,13 @@ __device__ __forceinline__ void fft_group(float2* __restrict__ buf, const float2
   }
   if (S::TAIL == 2) {
     float2 v[8];
-    r4_load<M, DIR>(buf, tw, j, Ns, v);
+    r4_load<M, DIR>(buf, T.w + FftTw<M>::N8T, j, Ns, v);
     __syncwarp();
     r4_store<M>(buf, j, Ns, v);
     __syncwarp();
   } else if (S::TAIL == 1) {
     float2 v[8];
-    r2_load<M, DIR>(buf, tw, j, Ns, v);
+    r2_load<M, DIR>(buf, T.w + FftTw<M>::N8T, j, Ns, v);
     __syncwarp();
     r2_store<M>(buf, j, Ns, v);
     __syncwarp();
@@ -277,17 +474,19 @@ inline void fft_group_emulate(float2* buf, const float2* tw) {
   using S = FftShape<M>;
   constexpr int G = M / 8;
   float2 V[G][8];
+  FftTw<M> T[G];
+  for (int j = 0; j < G; ++j) fft_twiddles<M>(tw, j, T[j]);
   int Ns = 1;
   for (int pass = 0; pass < S::N8; ++pass) {
-    for (int j = 0; j < G; ++j) r8_load<M, DIR>(buf, tw, j, Ns, V[j]);
+    for (int j = 0; j < G; ++j) r8_load<M, DIR>(buf, pass > 0 ? T[j].w + (pass - 1) * 7 : T[j].w, j, Ns, V[j]);
     for (int j = 0; j < G; ++j) r8_store<M>(buf, j, Ns, V[j]);
     Ns *= 8;
   }
   if (S::TAIL == 2) {
-    for (int j = 0; j < G; ++j) r4_load<M, DIR>(buf, tw, j, Ns, V[j]);
+    for (int j = 0; j < G; ++j) r4_load<M, DIR>(buf, T[j].w + FftTw<M>::N8T, j, Ns, V[j]);
     for (int j = 0; j < G; ++j) r4_store<M>(buf, j, Ns, V[j]);
   } else if (S::TAIL == 1) {
-    for (int j = 0; j < G; ++j) r2_load<M, DIR>(buf, tw, j, Ns, V[j]);
+    for (int j = 0; j < G; ++j) r2_load<M, DIR>(buf, T[j].w + FftTw<M>::N8T, j, Ns, V[j]);
     for (int j = 0; j < G; ++j) r2_store<M>(buf, j, Ns, V[j]);
   }
 }

@@ -54,12 +54,14 @@ struct fpm_handle {
   int cap_losses = 0;
   size_t cap_fbuf = 0;
   double* epoch = nullptr;
-  long long* tbase = nullptr;
+  float2* coef = nullptr;  // per-step Adam bias corrections of the current run
+  int cap_coef = 0;
   int* err = nullptr;
   // pinned staging
   int* h_sched = nullptr;
   int cap_h_sched = 0;
-  long long* h_t = nullptr;
+  float2* h_coef = nullptr;
+  int cap_h_coef = 0;
   int* h_err = nullptr;
   long long t_host = 0;
   bool loaded = false;
@@ -111,11 +113,11 @@ void free_all(fpm_handle* h) {
   h->graphs.clear();
   void* dev[] = {h->Ot, h->mO, h->vO, h->tmp, h->tmp2, h->tw_m, h->tw_N, h->meas, h->sp, h->msp, h->vsp,
                  h->gsc, h->fbuf, h->nint, h->span, h->gbox, h->part, h->sched, h->losses, h->epoch,
-                 h->tbase, h->err};
+                 h->coef, h->err};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (h->h_sched) cudaFreeHost(h->h_sched);
-  if (h->h_t) cudaFreeHost(h->h_t);
+  if (h->h_coef) cudaFreeHost(h->h_coef);
   if (h->h_err) cudaFreeHost(h->h_err);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
@@ -185,6 +187,16 @@ int grow(fpm_handle* h, T** p, int* cap, int need) {
   return FPM_OK;
 }
 
+// Adam bias corrections (1/(1 - b1^t), 1/sqrt(1 - b2^t)) for steps
+// t = t_host + 1 .. t_host + n_steps, in FP64, into dst (host).
+void fill_coef(const fpm_handle* h, int n_steps, float2* dst) {
+  const double b1 = h->hp.beta1, b2 = h->hp.beta2;
+  for (int s = 0; s < n_steps; ++s) {
+    const double t = (double)(h->t_host + s + 1);
+    dst[s] = make_float2((float)(1.0 / (1.0 - std::pow(b1, t))), (float)(1.0 / std::sqrt(1.0 - std::pow(b2, t))));
+  }
+}
+
 int ensure_batch(fpm_handle* h, int B) {
   if (h->capB >= B) return FPM_OK;
   if (h->gbox) CK(h, cudaFree(h->gbox));
@@ -193,7 +205,7 @@ int ensure_batch(fpm_handle* h, int B) {
   h->part = nullptr;
   h->capB = 0;
   CK(h, cudaMalloc(&h->gbox, sizeof(float2) * (size_t)B * h->W * h->W));
-  CK(h, cudaMalloc(&h->part, sizeof(double) * (size_t)B * h->C * NPART));
+  CK(h, cudaMalloc(&h->part, sizeof(double) * (size_t)B * NPART));
   h->capB = B;
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();
@@ -266,7 +278,7 @@ UpdArgs upd_args(fpm_handle* h, const int* idx_dev, int B, int step_off, double*
   u.b2 = h->hp.beta2;
   u.eps = h->hp.eps;
   u.offset_bound = FPM_OFFSET_BOUND_PX;
-  u.t_base = h->tbase;
+  u.coef = assemble ? nullptr : h->coef;
   u.step_off = step_off;
   u.learn = h->hp.learn_mask;
   u.loss_slot = loss_slot;
@@ -310,11 +322,14 @@ int build_graph(fpm_handle* h, int n_steps, int B, cudaGraphExec_t* out) {
   CK(h, cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaMemcpyAsync(h->sched, h->h_sched, sizeof(int) * (size_t)n_steps * B,
                                   cudaMemcpyHostToDevice, h->st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(h->tbase, h->h_t, sizeof(long long), cudaMemcpyHostToDevice, h->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h->coef, h->h_coef, sizeof(float2) * n_steps, cudaMemcpyHostToDevice, h->st);
+  // kernels after the first may start early (programmatic dependent launch)
+  // and wait in-kernel for their predecessor's results
   for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
     const int* idx = h->sched + (size_t)s * B;
-    e = launch_led(h->m, led_args(h, idx, B, MODE_LOSS), h->st);
-    if (e == cudaSuccess) e = launch_update(upd_args(h, idx, B, s, h->losses + s, 0), h->st);
+    e = launch_led(h->m, h->C, led_args(h, idx, B, MODE_LOSS), h->st, s > 0);
+    if (e == cudaSuccess) e = launch_update(upd_args(h, idx, B, s, h->losses + s, 0), h->st, true);
   }
   cudaError_t e2 = cudaStreamEndCapture(h->st, &g);
   if (e != cudaSuccess || e2 != cudaSuccess) {
@@ -354,7 +369,7 @@ int fpm_create(const fpm_geometry* g, float R, int32_t upsample, void* cuda_stre
   h->dk = g->dk_per_um;
   h->edge = g->pupil_edge;
   h->user = (cudaStream_t)cuda_stream;
-  h->C = led_cluster_size(h->m);
+  h->C = led_cluster_size(h->m);  // refined once a device is available
   h->h = (int)std::floor((double)R + 0.5 + std::sqrt(2.0) * FPM_OFFSET_BOUND_PX) + 1;
   h->W = 2 * h->h + 1;
   auto bad = [&](int code, const char* why) {
@@ -434,11 +449,9 @@ int fpm_create(const fpm_geometry* g, float R, int32_t upsample, void* cuda_stre
             ck(cudaMalloc(&h->nint, sizeof(int2) * h->n), "alloc leds") &&
             ck(cudaMalloc(&h->span, sizeof(int2) * h->N), "alloc span") &&
             ck(cudaMalloc(&h->epoch, sizeof(double)), "alloc") &&
-            ck(cudaMalloc(&h->tbase, sizeof(long long)), "alloc") &&
             ck(cudaMalloc(&h->err, sizeof(int)), "alloc") &&
-            ck(cudaMallocHost(&h->h_t, sizeof(long long)), "pinned") &&
             ck(cudaMallocHost(&h->h_err, sizeof(int)), "pinned") &&
-            ck(led_prepare(h->m, h->W), "kernel attributes");
+            ck(led_prepare(h->m, (h->C = led_choose_cluster(h->m, h->W)), h->W), "kernel attributes");
   if (ok) {
     const auto twm = twiddles(h->m), twN = twiddles(h->N);
     ok = ck(cudaMemcpy(h->tw_m, twm.data(), sizeof(float2) * h->m, cudaMemcpyHostToDevice), "copy") &&
@@ -446,8 +459,7 @@ int fpm_create(const fpm_geometry* g, float R, int32_t upsample, void* cuda_stre
          ck(cudaMemcpy(h->nint, h->nint_h.data(), sizeof(int2) * h->n, cudaMemcpyHostToDevice), "copy") &&
          ck(cudaMemcpy(h->span, span.data(), sizeof(int2) * h->N, cudaMemcpyHostToDevice), "copy") &&
          ck(cudaMemset(h->Ot, 0, sizeof(float2) * NN), "memset") &&
-         ck(cudaMemset(h->err, 0, sizeof(int)), "memset") &&
-         ck(cudaMemset(h->tbase, 0, sizeof(long long)), "memset");
+         ck(cudaMemset(h->err, 0, sizeof(int)), "memset");
   }
   if (ok) ok = reset_state(h) == FPM_OK && ck(cudaStreamSynchronize(h->st), "sync");
   if (!ok) {
@@ -527,8 +539,18 @@ int fpm_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int32_t B, 
   if ((rc = ensure_batch(h, B))) return rc;
   if ((rc = grow(h, &h->sched, &h->cap_sched, n_steps * B))) return rc;
   if ((rc = grow(h, &h->losses, &h->cap_losses, n_steps))) return rc;
+  if ((rc = grow(h, &h->coef, &h->cap_coef, n_steps))) return rc;
   // the previous run's graph may still be reading the staging buffers
   CK(h, cudaEventSynchronize(h->ev_stage));
+  if (h->cap_h_coef < n_steps) {
+    if (h->h_coef) CK(h, cudaFreeHost(h->h_coef));
+    h->h_coef = nullptr;
+    h->cap_h_coef = 0;
+    CK(h, cudaMallocHost(&h->h_coef, sizeof(float2) * (size_t)n_steps));
+    h->cap_h_coef = n_steps;
+    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+    h->graphs.clear();
+  }
   if (h->cap_h_sched < n_steps * B) {
     if (h->h_sched) CK(h, cudaFreeHost(h->h_sched));
     h->h_sched = nullptr;
@@ -539,7 +561,7 @@ int fpm_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int32_t B, 
     h->graphs.clear();
   }
   std::memcpy(h->h_sched, schedule, sizeof(int) * (size_t)n_steps * B);
-  *h->h_t = h->t_host;
+  fill_coef(h, n_steps, h->h_coef);
   auto key = std::make_pair(n_steps, B);
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
@@ -574,9 +596,11 @@ int fpm_profile_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int
   if ((rc = grow(h, &h->sched, &h->cap_sched, n_steps * B))) return rc;
   if ((rc = grow(h, &h->losses, &h->cap_losses, n_steps))) return rc;
   if ((rc = enter(h))) return rc;
+  if ((rc = grow(h, &h->coef, &h->cap_coef, n_steps))) return rc;
   CK(h, cudaMemcpyAsync(h->sched, schedule, sizeof(int) * (size_t)n_steps * B, cudaMemcpyHostToDevice, h->st));
-  const long long t0 = h->t_host;
-  CK(h, cudaMemcpyAsync(h->tbase, &t0, sizeof(long long), cudaMemcpyHostToDevice, h->st));
+  std::vector<float2> coef(n_steps);
+  fill_coef(h, n_steps, coef.data());
+  CK(h, cudaMemcpyAsync(h->coef, coef.data(), sizeof(float2) * n_steps, cudaMemcpyHostToDevice, h->st));
   std::vector<cudaEvent_t> ev((size_t)3 * n_steps, nullptr);
   auto destroy = [&]() {
     for (auto e : ev)
@@ -587,25 +611,20 @@ int fpm_profile_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int
       destroy();
       return fail(h, FPM_ERR_CUDA, "event creation failed");
     }
-  cudaGraph_t g = nullptr;
-  cudaGraphExec_t ex = nullptr;
-  cudaError_t e = cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal);
+  // Direct launches (events recorded inside captured graphs cannot be timed);
+  // with a flush before every step the host stays ahead of the device, so
+  // each timed window holds only device work.
+  cudaError_t e = cudaSuccess;
   for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
     const int* idx = h->sched + (size_t)s * B;
     if (flush) e = cudaMemsetAsync(flush, s & 0xff, (size_t)flush_bytes, h->st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s], h->st);
-    if (e == cudaSuccess) e = launch_led(h->m, led_args(h, idx, B, MODE_LOSS), h->st);
+    if (e == cudaSuccess) e = launch_led(h->m, h->C, led_args(h, idx, B, MODE_LOSS), h->st, false);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 1], h->st);
-    if (e == cudaSuccess) e = launch_update(upd_args(h, idx, B, s, h->losses + s, 0), h->st);
+    if (e == cudaSuccess) e = launch_update(upd_args(h, idx, B, s, h->losses + s, 0), h->st, false);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 2], h->st);
   }
-  cudaError_t e2 = cudaStreamEndCapture(h->st, &g);
-  if (e == cudaSuccess) e = e2;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
-  if (g) cudaGraphDestroy(g);
-  if (e == cudaSuccess) e = cudaGraphLaunch(ex, h->st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
-  if (ex) cudaGraphExecDestroy(ex);
   if (e != cudaSuccess) {
     destroy();
     return fail(h, FPM_ERR_CUDA, "profiled run failed: %s", cudaGetErrorString(e));
@@ -655,7 +674,7 @@ int fpm_forward(fpm_handle* h, const int32_t* idx, int32_t B, float* I_out) {
   CK(h, cudaMemcpyAsync(h->sched, idx, sizeof(int) * B, cudaMemcpyHostToDevice, h->st));
   LedArgs a = led_args(h, h->sched, B, MODE_FORWARD);
   a.I_out = dev_out ? I_out : h->fbuf;
-  CK(h, launch_led(h->m, a, h->st));
+  CK(h, launch_led(h->m, h->C, a, h->st, false));
   if (!dev_out) {
     CK(h, cudaMemcpyAsync(I_out, h->fbuf, sizeof(float) * img, cudaMemcpyDeviceToHost, h->st));
     CK(h, cudaStreamSynchronize(h->st));
@@ -674,6 +693,7 @@ int fpm_backward(fpm_handle* h, const int32_t* idx, int32_t B, const float* dL_d
   if ((rc = grow(h, &h->losses, &h->cap_losses, 1))) return rc;
   const size_t img = (size_t)B * h->m * h->m;
   const bool dev_in = dL_dI && is_device_ptr(dL_dI);
+  if (dev_in && ((uintptr_t)dL_dI & 15)) return fail(h, FPM_ERR_ARG, "device dL_dI must be 16-byte aligned");
   if (dL_dI && !dev_in && (rc = ensure_fbuf(h, img))) return rc;
   if ((rc = enter(h))) return rc;
   CK(h, cudaMemcpyAsync(h->sched, idx, sizeof(int) * B, cudaMemcpyHostToDevice, h->st));
@@ -682,10 +702,10 @@ int fpm_backward(fpm_handle* h, const int32_t* idx, int32_t B, const float* dL_d
     if (!dev_in) CK(h, cudaMemcpyAsync(h->fbuf, dL_dI, sizeof(float) * img, cudaMemcpyHostToDevice, h->st));
     a.dLdI = dev_in ? dL_dI : h->fbuf;
   }
-  CK(h, launch_led(h->m, a, h->st));
+  CK(h, launch_led(h->m, h->C, a, h->st, false));
   const size_t NN = (size_t)h->N * h->N;
   CK(h, cudaMemsetAsync(h->tmp, 0, sizeof(float2) * NN, h->st));
-  CK(h, launch_update(upd_args(h, h->sched, B, 0, h->losses, 1), h->st));
+  CK(h, launch_update(upd_args(h, h->sched, B, 0, h->losses, 1), h->st, false));
   bool host = false;
   if (g_object) {
     CK(h, launch_transpose(h->tmp, h->tmp2, h->N, h->st));

@@ -31,7 +31,7 @@ struct LedArgs {
   const int2* n_int;    // [n_leds] integer crop offsets (x = row, y = col)
   const int* idx;       // [B] LED of each batch slot
   float2* gbox;         // [B][W][W] per-LED object-gradient boxes, [slot][col][row]
-  double* part;         // [B][cluster][NPART]
+  double* part;         // [B][NPART], summed over the LED's cluster
   const float2* tw;     // [m] exp(-2 pi i t / m)
   int N, n_leds, B, h, W;
   float R, Rinv, inv_lambda, dk2;
@@ -55,7 +55,7 @@ struct UpdArgs {
   int N, n_leds, B, C, h, W;
   float lr_obj, lr_zern, lr_def, lr_gam, lr_off, b1, b2, eps;
   float offset_bound;
-  const long long* t_base;  // Adam steps taken before this launch sequence
+  const float2* coef;       // per step of the sequence: (1/(1-b1^t), 1/sqrt(1-b2^t)); nullable
   int step_off;             // this step's position in the sequence
   unsigned learn;
   double* loss_slot;        // batch loss of this step
@@ -66,12 +66,14 @@ struct UpdArgs {
   float* g_sc;              // [15 + 3 n_leds]
 };
 
-// Cluster size used for low-res side m (CTAs cooperating on one LED image).
+// Cluster size C (CTAs cooperating on one LED image) for low-res side m.
 int led_cluster_size(int m);
-size_t led_smem_bytes(int m, int W);
-cudaError_t led_prepare(int m, int W);
-cudaError_t launch_led(int m, const LedArgs& a, cudaStream_t s);
-cudaError_t launch_update(const UpdArgs& a, cudaStream_t s);
+int led_choose_cluster(int m, int W);
+size_t led_smem_bytes(int m, int C, int W);
+cudaError_t led_prepare(int m, int C, int W);
+// pdl: allow programmatic dependent launch after the previous kernel in the stream.
+cudaError_t launch_led(int m, int C, const LedArgs& a, cudaStream_t s, bool pdl);
+cudaError_t launch_update(const UpdArgs& a, cudaStream_t s, bool pdl);
 
 // Field kernels (initialisation, object transforms, layout changes).
 cudaError_t launch_upsample_centre(const float* I, int m, int s, float2* out_rowmajor, cudaStream_t st);

@@ -11,6 +11,9 @@
 // CTA r of the cluster owns a slice of box columns (phases A and C) and a
 // slice of image rows (phase B). T / U live in the owners' shared memory and
 // are gathered / scattered through distributed shared memory in phase B.
+// The CTA's slice of O (support pixels only) and its rows of the measured
+// image are copied into shared memory with cp.async at the start, so each
+// kernel exposes global-memory latency about once.
 #include <cooperative_groups.h>
 
 #include "device.cuh"
@@ -20,93 +23,172 @@ namespace cg = cooperative_groups;
 
 namespace fpmk {
 
+// Threads per CTA for each low-res size; the cluster size C (CTAs per LED
+// image) is a second template parameter (led_choose_cluster picks it).
 template <int M> struct LedCfg;
-template <> struct LedCfg<32> { static constexpr int C = 2, NT = 64; };
-template <> struct LedCfg<64> { static constexpr int C = 4, NT = 128; };
-template <> struct LedCfg<128> { static constexpr int C = 8, NT = 256; };
-template <> struct LedCfg<256> { static constexpr int C = 8, NT = 256; };
+template <> struct LedCfg<32> { static constexpr int NT = 64; };
+template <> struct LedCfg<64> { static constexpr int NT = 128; };
+template <> struct LedCfg<128> { static constexpr int NT = 256; };
+template <> struct LedCfg<256> { static constexpr int NT = 256; };
 
-template <int M>
+// per-thread accumulators: loss, gamma, 15 monomial moments, defocus, delta_y, delta_x
+constexpr int NACC = 20;
+enum : int { A_LOSS = 0, A_GAMMA = 1, A_MONO = 2, A_DEF = 17, A_DY = 18, A_DX = 19 };
+
+template <int M, int C>
 struct LedLayout {
-  static constexpr int C = LedCfg<M>::C, NT = LedCfg<M>::NT;
-  static constexpr int G = M / 8;                  // threads per transform
+  static constexpr int NT = LedCfg<M>::NT;
+  static constexpr int G = FftBuf<M>::G;           // threads per transform
   static constexpr int NG = NT / G;                // transform groups per CTA
   static constexpr int ROWS = M / C;               // image rows per CTA
   static constexpr int TS = M + 1;                 // T row stride (odd: conflict-free gathers)
-  static constexpr int FS = M + (G < 16 ? G : 0);  // per-group FFT buffer stride
+  static constexpr int FS = FftBuf<M>::SIZE;       // padded per-group buffer (stride = 8 mod 16 when G = 8)
+  static constexpr int NW = NT / 32;
+  static constexpr int NPOLY = 40;                 // K[15], Dx[10], Dy[10], pad
+  static constexpr int NTW2 = M == 256 ? 15 * 16 : 0;  // per-thread second-pass twiddles (M = 256)
   static size_t bytes(int W) {
     const int chunk = (W + C - 1) / C;
-    return sizeof(float2) * ((size_t)chunk * TS + (size_t)NG * FS + M) + 16 * sizeof(float) +
-           sizeof(double) * (NT / 32) * NPART;
+    return sizeof(float) * (size_t)ROWS * M +
+           sizeof(float2) * ((size_t)chunk * TS + (size_t)NG * FS + M + NTW2 + (size_t)chunk * W) +
+           sizeof(float) * (NPOLY + (size_t)NW * NACC) + sizeof(double) * (16 + NPART + 1);
   }
 };
 
-__device__ __forceinline__ double warp_sum(double v) {
+__device__ __forceinline__ float warp_sum_f(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
 
-template <int M>
-__global__ void __launch_bounds__(LedCfg<M>::NT) led_kernel(const LedArgs a) {
-  using L = LedLayout<M>;
-  constexpr int C = L::C, NT = L::NT, G = L::G, NG = L::NG, ROWS = L::ROWS, TS = L::TS, FS = L::FS;
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Programmatic dependent launch: let the next kernel in the stream be
+// scheduled early / wait here until the previous kernel's writes are visible.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
+// In-place transform of one padded buffer by its thread group.
+template <int M, int DIR>
+__device__ __forceinline__ void transform(float2* buf, const FftTw<M == 256 ? 128 : M>& TW, const float2* tw2,
+                                          int j) {
+  if constexpr (M == 256) fft256_group<DIR>(buf, tw2, j);
+  else fft_group<M, DIR>(buf, TW, j);
+}
+
+template <int M, int C>
+__global__ void __launch_bounds__(LedCfg<M>::NT, 2) led_kernel(const LedArgs a) {
+  using L = LedLayout<M, C>;
+  constexpr int NT = L::NT, G = L::G, NG = L::NG, ROWS = L::ROWS, TS = L::TS, FS = L::FS;
+  constexpr int NW = L::NW;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
   const int k = blockIdx.x / C;
   const int W = a.W, h = a.h, N = a.N;
   const int chunk = (W + C - 1) / C;
   const int c0 = rank * chunk, c1 = min(W, c0 + chunk);
+  const int y0 = rank * ROWS;
 
+  // layout: image rows first (16-byte aligned for cp.async), then the float2 arrays
   extern __shared__ __align__(16) unsigned char smem[];
-  float2* T = reinterpret_cast<float2*>(smem);
-  float2* fb = T + (size_t)chunk * TS;
-  float2* tws = fb + NG * FS;
-  float* zc = reinterpret_cast<float*>(tws + M);
-  double* red = reinterpret_cast<double*>(zc + 16);
+  float* ms = reinterpret_cast<float*>(smem);             // [ROWS][M] measured image / dL/dI rows
+  float2* T = reinterpret_cast<float2*>(ms + ROWS * M);   // [chunk][TS] T, then U, by box column
+  float2* fb = T + (size_t)chunk * TS;                    // [NG][FS] transform buffers
+  float2* tws = fb + NG * FS;                             // [M] twiddle table
+  float2* tw2 = tws + M;                                  // [15][16] second-pass twiddles (M = 256)
+  float2* Ob = tw2 + L::NTW2;                             // [chunk][W] O on this CTA's box columns
+  float* poly = reinterpret_cast<float*>(Ob + (size_t)chunk * W);  // K[15] Dx[10] Dy[10]
+  float* red = poly + L::NPOLY;                           // [NW][NACC]
+  double* dsum = reinterpret_cast<double*>(red + NW * NACC);  // [16 + NPART] (8-byte aligned: float counts are even)
 
   const int tid = threadIdx.x;
   const int led = a.idx[k];
-  if (led < 0 || led >= a.n_leds) {  // same value for every CTA of the cluster: uniform exit
+  if (led < 0 || led >= a.n_leds) {  // the same for every CTA of the cluster: uniform exit
     if (tid == 0 && rank == 0) atomicOr(a.err, DERR_INDEX);
     return;
   }
+  // inputs that no earlier kernel writes: image rows, twiddles
+  const float* rows_src = a.mode == MODE_LOSS ? a.meas + ((size_t)led * M + y0) * M
+                        : a.mode == MODE_UPSTREAM ? a.dLdI + ((size_t)k * M + y0) * M : nullptr;
+  if (rows_src)
+    for (int q = tid; q < ROWS * M / 4; q += NT) cp_async16(ms + 4 * q, rows_src + 4 * q);
+  cp_async_commit();
   for (int t = tid; t < M; t += NT) tws[t] = a.tw[t];
-  if (tid < 14) zc[tid] = a.sp[SP_ZERN + tid];
+  pdl_launch_dependents();
+  pdl_wait();  // O and the scalar parameters come from the previous update
+
+  if (tid == 0) {  // aberration phase as a polynomial in the monomials of q/R
+    float c[14], K[15], Dx[10], Dy[10];
+    for (int q = 0; q < 14; ++q) c[q] = a.sp[SP_ZERN + q];
+    theta_poly(c, K, Dx, Dy);
+    for (int q = 0; q < 15; ++q) poly[q] = K[q];
+    for (int q = 0; q < 10; ++q) {
+      poly[15 + q] = Dx[q];
+      poly[25 + q] = Dy[q];
+    }
+  }
   const float zdef = a.sp[SP_DEFOCUS];
   const float gam = a.sp[SP_GAMMA + led];
   const float dly = a.sp[sp_offset(a.n_leds) + 2 * led];
   const float dlx = a.sp[sp_offset(a.n_leds) + 2 * led + 1];
   const int2 nn = a.n_int[led];
   const PupilConst P{a.R, a.Rinv, a.inv_lambda, a.dk2, a.hard_edge};
-  __syncthreads();
-
-  const int grp = tid / G, j = tid % G;
-  float2* buf = fb + grp * FS;
-  // column-major spectrum: box column c holds spectrum column N/2 + n.y - h + c,
+  // column-major spectrum: box column c is spectrum column N/2 + n.y - h + c,
   // and row ky of it sits at offset N/2 + n.x + ky
   const size_t col0 = (size_t)(N / 2 + nn.y - h);
   const int row0 = N / 2 + nn.x;
+  {
+    // radius with a margin: a superset of every pixel where A > 0
+    const float rs = (P.hard_edge ? P.R : P.R + 0.5f) + 1e-3f;
+    const int ncol = c1 > c0 ? c1 - c0 : 0;
+    for (int q = tid; q < ncol * W; q += NT) {
+      const int cl = q / W, r = q - cl * W;
+      const float qx = (float)(c0 + cl - h) - dlx, qy = (float)(r - h) - dly;
+      if (qx * qx + qy * qy <= rs * rs)  // support pixels only (superset of A > 0)
+        cp_async8(Ob + q, a.Ot + (col0 + c0 + cl) * N + (row0 - h + r));
+    }
+  }
+  cp_async_commit();
+  const int grp = tid / G, j = tid % G;
+  float2* buf = fb + grp * FS;
+  FftTw<M == 256 ? 128 : M> TW;  // radix-8 path: per-thread twiddles in registers
+  __syncthreads();                // twiddle table
+  if constexpr (M == 256) {
+    if (tid < 16) fft256_twiddles(tws, tw2, tid);
+  } else {
+    fft_twiddles<M>(tws, j, TW);
+  }
+  cp_async_wait<0>();
+  __syncthreads();  // O slice and image rows in shared memory
 
   // ---------------- phase A: column inverse transforms over ky -------------
   for (int cb = c0; cb < c1; cb += NG) {
     const int c = cb + grp;
     const bool act = c < c1;
-    const float2* Ocol = a.Ot + (col0 + (act ? c : c0)) * N + row0;
+    const float2* Oc = Ob + (size_t)(act ? c - c0 : 0) * W + h;   // index by ky
     const float qx = (float)(c - h) - dlx;
     for (int t = j; t < M; t += G) {
       const int ky = t < M / 2 ? t : t - M;
       float2 v = make_float2(0.f, 0.f);
       if (act && ky >= -h && ky <= h) {
-        const float2 Mv = pupil_value((float)ky - dly, qx, P, zc, zdef);
-        if (Mv.x != 0.f || Mv.y != 0.f) v = cmul(Ocol[ky], Mv);
+        const float2 Mv = pupil_value_poly((float)ky - dly, qx, P, poly, zdef);
+        if (Mv.x != 0.f || Mv.y != 0.f) v = cmul(Oc[ky], Mv);
       }
-      buf[t] = v;
+      buf[bidx<M>(t)] = v;
     }
     __syncwarp();
-    fft_group<M, +1>(buf, tws, j);
+    transform<M, +1>(buf, TW, tw2, j);
     if (act)
-      for (int t = j; t < M; t += G) T[(c - c0) * TS + t] = buf[t];
+      for (int t = j; t < M; t += G) T[(c - c0) * TS + t] = buf[bidx<M>(t)];
     __syncwarp();
   }
   cluster.sync();
@@ -118,7 +200,7 @@ __global__ void __launch_bounds__(LedCfg<M>::NT) led_kernel(const LedArgs a) {
   for (int rb = 0; rb < ROWS; rb += NG) {
     const int rr = rb + grp;
     const bool act = rr < ROWS;
-    const int y = rank * ROWS + (act ? rr : 0);
+    const int yl = act ? rr : 0, y = y0 + yl;
     for (int t = j; t < M; t += G) {
       const int kx = t < M / 2 ? t : t - M;
       float2 v = make_float2(0.f, 0.f);
@@ -127,26 +209,26 @@ __global__ void __launch_bounds__(LedCfg<M>::NT) led_kernel(const LedArgs a) {
         const float2* Tr = cluster.map_shared_rank(T, own);
         v = Tr[lc * TS + y];
       }
-      buf[t] = v;
+      buf[bidx<M>(t)] = v;
     }
     __syncwarp();
-    fft_group<M, +1>(buf, tws, j);
+    transform<M, +1>(buf, TW, tw2, j);
     for (int t = j; t < M; t += G) {
-      const float2 psi = cscale(buf[t], inv_m2);
+      const float2 psi = cscale(buf[bidx<M>(t)], inv_m2);
       const float mag2 = psi.x * psi.x + psi.y * psi.y;
       float2 gp = make_float2(0.f, 0.f);
       if (act) {
-        const size_t pix = (size_t)y * M + t;
         if (a.mode == MODE_FORWARD) {
-          a.I_out[(size_t)k * M * M + pix] = gam * mag2;
+          a.I_out[((size_t)k * M + y) * M + t] = gam * mag2;
         } else if (a.mode == MODE_LOSS) {
-          const float meas = a.meas[(size_t)led * M * M + pix];
+          const float meas = ms[yl * M + t];
           if (a.loss == 0) {
-            const float mag = sqrtf(mag2);
+            const float rinv = mag2 > 0.f ? rsqrtf(mag2) : 0.f;
+            const float mag = mag2 * rinv;
             const float res = sg * mag - sqrtf(fmaxf(meas, 0.f));
             acc_loss = fmaf(res, res, acc_loss);
             acc_g = fmaf(res, mag, acc_g);
-            if (mag > 0.f) gp = cscale(psi, 2.f * res * sg / mag);
+            gp = cscale(psi, 2.f * res * sg * rinv);   // 0 where psi = 0
           } else {
             const float res = gam * mag2 - meas;
             acc_loss = fmaf(res, res, acc_loss);
@@ -154,21 +236,21 @@ __global__ void __launch_bounds__(LedCfg<M>::NT) led_kernel(const LedArgs a) {
             gp = cscale(psi, 4.f * gam * res);
           }
         } else {
-          const float d = a.dLdI[(size_t)k * M * M + pix];
+          const float d = ms[yl * M + t];
           acc_g = fmaf(d, mag2, acc_g);
           gp = cscale(psi, 2.f * gam * d);
         }
       }
-      buf[t] = gp;
+      buf[bidx<M>(t)] = gp;
     }
     __syncwarp();
     if (a.mode != MODE_FORWARD) {
-      fft_group<M, -1>(buf, tws, j);
+      transform<M, -1>(buf, TW, tw2, j);
       if (act)
         for (int c = j; c < W; c += G) {
           const int kx = c - h, own = c / chunk, lc = c - own * chunk;
           float2* Tr = cluster.map_shared_rank(T, own);
-          Tr[lc * TS + y] = buf[kx & (M - 1)];
+          Tr[lc * TS + y] = buf[bidx<M>(kx & (M - 1))];
         }
       __syncwarp();
     }
@@ -177,19 +259,19 @@ __global__ void __launch_bounds__(LedCfg<M>::NT) led_kernel(const LedArgs a) {
   if (a.mode == MODE_FORWARD) return;
 
   // ---------------- phase C: column transforms over y, box gradients -------
-  float acc_z[14];
+  float acc_m[15];
 #pragma unroll
-  for (int q = 0; q < 14; ++q) acc_z[q] = 0.f;
+  for (int q = 0; q < 15; ++q) acc_m[q] = 0.f;
   float acc_def = 0.f, acc_dy = 0.f, acc_dx = 0.f;
   float2* gb = a.gbox + (size_t)k * W * W;
   for (int cb = c0; cb < c1; cb += NG) {
     const int c = cb + grp;
     const bool act = c < c1;
-    for (int t = j; t < M; t += G) buf[t] = act ? T[(c - c0) * TS + t] : make_float2(0.f, 0.f);
+    for (int t = j; t < M; t += G) buf[bidx<M>(t)] = act ? T[(c - c0) * TS + t] : make_float2(0.f, 0.f);
     __syncwarp();
-    fft_group<M, -1>(buf, tws, j);
+    transform<M, -1>(buf, TW, tw2, j);
     if (act) {
-      const float2* Ocol = a.Ot + (col0 + c) * N + row0;
+      const float2* Oc = Ob + (size_t)(c - c0) * W + h;
       const float qx = (float)(c - h) - dlx;
       for (int r = j; r < W; r += G) {
         const int ky = r - h;
@@ -197,15 +279,16 @@ __global__ void __launch_bounds__(LedCfg<M>::NT) led_kernel(const LedArgs a) {
         float2 out = make_float2(0.f, 0.f);
         const float A = pupil_amp(qy, qx, P);
         if (A > 0.f) {
-          const float2 gphi = cscale(buf[ky & (M - 1)], inv_m2);
-          Zern Z;
-          zernike_eval(qx * P.Rinv, qy * P.Rinv, Z);
+          const float2 gphi = cscale(buf[bidx<M>(ky & (M - 1))], inv_m2);
+          float mo[15];
+          monomials(qx * P.Rinv, qy * P.Rinv, mo);
           float th = 0.f, dthx = 0.f, dthy = 0.f;
 #pragma unroll
-          for (int q = 0; q < 14; ++q) {
-            th = fmaf(zc[q], Z.v[q], th);
-            dthx = fmaf(zc[q], Z.dx[q], dthx);
-            dthy = fmaf(zc[q], Z.dy[q], dthy);
+          for (int q = 0; q < 15; ++q) th = fmaf(poly[q], mo[q], th);
+#pragma unroll
+          for (int q = 0; q < 10; ++q) {
+            dthx = fmaf(poly[15 + q], mo[q], dthx);
+            dthy = fmaf(poly[25 + q], mo[q], dthy);
           }
           const float r2 = qx * qx + qy * qy;
           float root;
@@ -214,12 +297,12 @@ __global__ void __launch_bounds__(LedCfg<M>::NT) led_kernel(const LedArgs a) {
           sincosf(fmaf(zdef, kap, th), &sn, &cs);
           const float2 e = make_float2(cs, sn);
           const float2 Mv = cscale(e, A);
-          out = cmulc(Mv, gphi);                 // conj(M) gPhi
-          const float2 gM = cmulc(Ocol[ky], gphi);  // conj(O) gPhi
-          const float tt = -cmulc(gM, Mv).y;     // dL/dchi = Re(conj(gM) i M)
-          const float ee = cmulc(gM, e).x;       // dL/dA   = Re(conj(gM) e^{i chi})
+          out = cmulc(Mv, gphi);                   // conj(M) gPhi
+          const float2 gM = cmulc(Oc[ky], gphi);   // conj(O) gPhi
+          const float tt = -cmulc(gM, Mv).y;       // dL/dchi = Re(conj(gM) i M)
+          const float ee = cmulc(gM, e).x;         // dL/dA   = Re(conj(gM) e^{i chi})
 #pragma unroll
-          for (int q = 0; q < 14; ++q) acc_z[q] = fmaf(tt, Z.v[q], acc_z[q]);
+          for (int q = 0; q < 15; ++q) acc_m[q] = fmaf(tt, mo[q], acc_m[q]);
           acc_def = fmaf(tt, kap, acc_def);
           const float dk = -6.283185307179586f * P.dk2 / root;  // d kappa / d q = dk * q
           const float dchiy = fmaf(dthy, P.Rinv, zdef * dk * qy);
@@ -242,97 +325,151 @@ __global__ void __launch_bounds__(LedCfg<M>::NT) led_kernel(const LedArgs a) {
   }
 
   // ---------------- reduction of the scalar partials -----------------------
+  // FP32 within a thread (a few dozen terms) and across a warp, FP64 across
+  // warps; the monomial moments become Zernike gradients in FP64 at the end.
   const int warp = tid >> 5, lane = tid & 31;
-  float vals[NPART];
-  vals[P_LOSS] = acc_loss;
-  vals[P_GAMMA] = acc_g;
+  float vals[NACC];
+  vals[A_LOSS] = acc_loss;
+  vals[A_GAMMA] = acc_g;
 #pragma unroll
-  for (int q = 0; q < 14; ++q) vals[P_ZERN + q] = acc_z[q];
-  vals[P_DEFOCUS] = acc_def;
-  vals[P_DY] = acc_dy;
-  vals[P_DX] = acc_dx;
+  for (int q = 0; q < 15; ++q) vals[A_MONO + q] = acc_m[q];
+  vals[A_DEF] = acc_def;
+  vals[A_DY] = acc_dy;
+  vals[A_DX] = acc_dx;
 #pragma unroll
-  for (int q = 0; q < NPART; ++q) {
-    const double s = warp_sum((double)vals[q]);
-    if (lane == 0) red[warp * NPART + q] = s;
+  for (int q = 0; q < NACC; ++q) {
+    const float s = warp_sum_f(vals[q]);
+    if (lane == 0) red[warp * NACC + q] = s;
   }
   __syncthreads();
-  if (tid < NPART) {
-    double s = 0.0;
-    for (int w = 0; w < NT / 32; ++w) s += red[w * NPART + tid];
-    if (tid == P_GAMMA && a.mode == MODE_LOSS && a.loss == 0) s /= (double)sg;
-    a.part[((size_t)k * C + rank) * NPART + tid] = s;
+  double tot = 0.0;
+  if (tid < NACC)
+    for (int w = 0; w < NW; ++w) tot += (double)red[w * NACC + tid];
+  if (tid >= A_MONO && tid < A_MONO + 15) dsum[tid - A_MONO] = tot;
+  __syncthreads();
+  // this CTA's partials in Zernike form, then summed over the cluster in rank order
+  if (tid == A_LOSS) dsum[16 + P_LOSS] = tot;
+  if (tid == A_GAMMA) dsum[16 + P_GAMMA] = (a.mode == MODE_LOSS && a.loss == 0) ? tot / (double)sg : tot;
+  if (tid == A_DEF) dsum[16 + P_DEFOCUS] = tot;
+  if (tid == A_DY) dsum[16 + P_DY] = tot;
+  if (tid == A_DX) dsum[16 + P_DX] = tot;
+  if (tid < 14) {  // dL/dc_j = sum_m (Z_j)_m * (sum_p t(p) mo_m(p))
+    double z = 0.0;
+    for (int m = 0; m < 15; ++m) z += (double)zern_mono(tid, m) * dsum[m];
+    dsum[16 + P_ZERN + tid] = z;
   }
+  cluster.sync();
+  if (rank == 0 && tid < NPART) {
+    double s = 0.0;
+    for (int r = 0; r < C; ++r) s += cluster.map_shared_rank(dsum, r)[16 + tid];
+    a.part[(size_t)k * NPART + tid] = s;
+  }
+  cluster.sync();  // keep every CTA's shared memory alive until rank 0 has read it
 }
 
 int led_cluster_size(int m) {
   switch (m) {
-    case 32: return LedCfg<32>::C;
-    case 64: return LedCfg<64>::C;
-    case 128: return LedCfg<128>::C;
-    case 256: return LedCfg<256>::C;
+    case 32: return 2;
+    case 64: return 4;
+    case 128: return 8;
+    case 256: return 16;
   }
   return 0;
 }
 
-size_t led_smem_bytes(int m, int W) {
-  switch (m) {
-    case 32: return LedLayout<32>::bytes(W);
-    case 64: return LedLayout<64>::bytes(W);
-    case 128: return LedLayout<128>::bytes(W);
-    case 256: return LedLayout<256>::bytes(W);
+template <int M, int C>
+static const void* kernel_ptr() { return (const void*)led_kernel<M, C>; }
+
+template <int M, int C>
+static cudaError_t prepare_t(int W);
+
+// A 16-CTA cluster (a non-portable size) is used for m = 256 only when the
+// device can hold 16 of them at once (a whole 16-LED batch in one wave);
+// otherwise 8.
+int led_choose_cluster(int m, int W) {
+  if (m != 256) return led_cluster_size(m);
+  const void* k16 = kernel_ptr<256, 16>();
+  if (prepare_t<256, 16>(W) != cudaSuccess) {  // non-portable size + shared-memory limit
+    cudaGetLastError();
+    return 8;
   }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(16, 1, 1);
+  cfg.blockDim = dim3(LedCfg<256>::NT, 1, 1);
+  cfg.dynamicSmemBytes = LedLayout<256, 16>::bytes(W);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 16;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k16, &cfg) != cudaSuccess || n < 16) {
+    cudaGetLastError();
+    return 8;  // a 16-LED batch of 16-CTA clusters would need a second wave
+  }
+  return 16;
+}
+
+size_t led_smem_bytes(int m, int C, int W) {
+  if (m == 32) return LedLayout<32, 2>::bytes(W);
+  if (m == 64) return LedLayout<64, 4>::bytes(W);
+  if (m == 128) return LedLayout<128, 8>::bytes(W);
+  if (m == 256) return C == 16 ? LedLayout<256, 16>::bytes(W) : LedLayout<256, 8>::bytes(W);
   return 0;
 }
 
 // The dynamic shared-memory limit is a per-function attribute shared by all
 // handles, so it is raised once to the device's opt-in maximum; each launch
 // then asks for what its box width needs.
-template <int M>
+template <int M, int C>
 static cudaError_t prepare_t(int W) {
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
-  if (LedLayout<M>::bytes(W) > (size_t)optin) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(led_kernel<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (LedLayout<M, C>::bytes(W) > (size_t)optin) return cudaErrorInvalidValue;
+  if (C > 8) {
+    e = cudaFuncSetAttribute(led_kernel<M, C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaFuncSetAttribute(led_kernel<M, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
 
-cudaError_t led_prepare(int m, int W) {
-  switch (m) {
-    case 32: return prepare_t<32>(W);
-    case 64: return prepare_t<64>(W);
-    case 128: return prepare_t<128>(W);
-    case 256: return prepare_t<256>(W);
-  }
+cudaError_t led_prepare(int m, int C, int W) {
+  if (m == 32) return prepare_t<32, 2>(W);
+  if (m == 64) return prepare_t<64, 4>(W);
+  if (m == 128) return prepare_t<128, 8>(W);
+  if (m == 256) return C == 16 ? prepare_t<256, 16>(W) : prepare_t<256, 8>(W);
   return cudaErrorInvalidValue;
 }
 
-template <int M>
-static cudaError_t launch_t(const LedArgs& a, cudaStream_t s) {
-  using L = LedLayout<M>;
+template <int M, int C>
+static cudaError_t launch_t(const LedArgs& a, cudaStream_t s, bool pdl) {
+  using L = LedLayout<M, C>;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(a.B * L::C), 1, 1);
+  cfg.gridDim = dim3((unsigned)(a.B * C), 1, 1);
   cfg.blockDim = dim3(L::NT, 1, 1);
   cfg.dynamicSmemBytes = L::bytes(a.W);
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = L::C;
+  attr[0].val.clusterDim.x = C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, led_kernel<M>, a);
+  cfg.numAttrs = pdl ? 2 : 1;
+  return cudaLaunchKernelEx(&cfg, led_kernel<M, C>, a);
 }
 
-cudaError_t launch_led(int m, const LedArgs& a, cudaStream_t s) {
-  switch (m) {
-    case 32: return launch_t<32>(a, s);
-    case 64: return launch_t<64>(a, s);
-    case 128: return launch_t<128>(a, s);
-    case 256: return launch_t<256>(a, s);
-  }
+cudaError_t launch_led(int m, int C, const LedArgs& a, cudaStream_t s, bool pdl) {
+  if (m == 32) return launch_t<32, 2>(a, s, pdl);
+  if (m == 64) return launch_t<64, 4>(a, s, pdl);
+  if (m == 128) return launch_t<128, 8>(a, s, pdl);
+  if (m == 256) return C == 16 ? launch_t<256, 16>(a, s, pdl) : launch_t<256, 8>(a, s, pdl);
   return cudaErrorInvalidValue;
 }
 

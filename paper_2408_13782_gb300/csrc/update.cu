@@ -1,11 +1,14 @@
 // Random-batch update (Section 2.3, Eq. 13) with Adam (Kingma & Ba 2015).
+// The bias corrections 1/(1 - b1^t) and 1/sqrt(1 - b2^t) of each step are
+// computed on the host in FP64 and passed in per step (no FP64 math here
+// apart from the fixed-order reduction of the FP64 partials).
 //
 // Object: every element of the update region (the union of all LEDs' crop
 // boxes; outside it the gradient has always been zero and Adam is an exact
 // no-op) gathers the per-LED gradient boxes in batch order - a fixed-order
 // sum, so results are bitwise reproducible - and takes one Adam step on its
 // real and imaginary parts. One CTA per spectrum column of the region.
-// Scalars: the last CTA reduces the per-CTA FP64 partials in a fixed order,
+// Scalars: the first CTA reduces the per-LED FP64 partials in a fixed order,
 // forms the gradients of the Zernike coefficients, defocus, intensity factors
 // and LED offsets, and updates all of them (every element, every step).
 #include <cmath>
@@ -24,33 +27,35 @@ __device__ __forceinline__ void adam1(float& w, float& m, float& v, float g, flo
   w -= lr_bc1 * m / fmaf(sqrtf(v), inv_sqrt_bc2, eps);
 }
 
-__device__ void scalar_update(const UpdArgs& a, double bc1, double bc2) {
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ void scalar_update(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc2) {
   extern __shared__ double gsh[];  // [sp_size(n_leds)] gradients, then NPART totals
   const int n = a.n_leds, P = sp_size(n);
   double* tot = gsh + P;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   for (int i = tid; i < P; i += blockDim.x) gsh[i] = 0.0;
-  __syncthreads();
-  // quantities shared by all LEDs: loss, Zernike, defocus (fixed summation order)
-  if (tid < NPART && tid != P_GAMMA && tid != P_DY && tid != P_DX) {
+  __syncthreads();  // part holds one FP64 set per batch slot (already summed over its cluster)
+  // quantities shared by all LEDs (loss, Zernike, defocus): one warp each,
+  // fixed per-lane order and a fixed shuffle tree, so the sum is reproducible
+  for (int qi = warp; qi < 16; qi += nwarp) {
+    const int q = qi == 0 ? P_LOSS : (qi <= 14 ? P_ZERN + qi - 1 : P_DEFOCUS);
     double s = 0.0;
-    for (int kk = 0; kk < a.B; ++kk)
-      for (int r = 0; r < a.C; ++r) s += a.part[((size_t)kk * a.C + r) * NPART + tid];
-    tot[tid] = s;
+    for (int kk = lane; kk < a.B; kk += 32) s += a.part[(size_t)kk * NPART + q];
+    s = warp_sum_d(s);
+    if (lane == 0) tot[q] = s;
   }
   // per-LED quantities
   for (int kk = tid; kk < a.B; kk += blockDim.x) {
     const int led = a.idx[kk];
-    double g = 0.0, dy = 0.0, dx = 0.0;
-    for (int r = 0; r < a.C; ++r) {
-      const double* p = a.part + ((size_t)kk * a.C + r) * NPART;
-      g += p[P_GAMMA];
-      dy += p[P_DY];
-      dx += p[P_DX];
-    }
-    gsh[SP_GAMMA + led] = g;
-    gsh[sp_offset(n) + 2 * led] = dy;
-    gsh[sp_offset(n) + 2 * led + 1] = dx;
+    const double* p = a.part + (size_t)kk * NPART;
+    gsh[SP_GAMMA + led] = p[P_GAMMA];
+    gsh[sp_offset(n) + 2 * led] = p[P_DY];
+    gsh[sp_offset(n) + 2 * led + 1] = p[P_DX];
   }
   __syncthreads();
   if (tid < 14) gsh[SP_ZERN + tid] = tot[P_ZERN + tid];
@@ -66,7 +71,6 @@ __device__ void scalar_update(const UpdArgs& a, double bc1, double bc2) {
     for (int i = tid; i < P; i += blockDim.x) a.g_sc[i] = (float)gsh[i];
     return;
   }
-  const float inv_sqrt_bc2 = (float)(1.0 / sqrt(bc2));
   for (int i = tid; i < P; i += blockDim.x) {
     float lr;
     unsigned bit;
@@ -76,7 +80,7 @@ __device__ void scalar_update(const UpdArgs& a, double bc1, double bc2) {
     else { lr = a.lr_off; bit = 1u << 4; }
     if (!(a.learn & bit)) continue;
     float w = a.sp[i], m = a.msp[i], v = a.vsp[i];
-    adam1(w, m, v, (float)gsh[i], (float)(lr / bc1), inv_sqrt_bc2, a.b1, a.b2, a.eps);
+    adam1(w, m, v, (float)gsh[i], lr * inv_bc1, inv_sqrt_bc2, a.b1, a.b2, a.eps);
     if (i >= sp_offset(n)) w = fminf(fmaxf(w, -a.offset_bound), a.offset_bound);
     a.sp[i] = w;
     a.msp[i] = m;
@@ -85,38 +89,68 @@ __device__ void scalar_update(const UpdArgs& a, double bc1, double bc2) {
 }
 
 __global__ void __launch_bounds__(UPD_NT) update_kernel(const UpdArgs a) {
-  const long long t = *a.t_base + a.step_off + 1;
-  const double bc1 = 1.0 - pow((double)a.b1, (double)t);
-  const double bc2 = 1.0 - pow((double)a.b2, (double)t);
-  if (blockIdx.x == (unsigned)a.n_cols) {
-    scalar_update(a, bc1, bc2);
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+  __shared__ int2 corner[MAX_BATCH];  // (first column, first row) of each slot's box
+  // bias corrections of this step, computed on the host in FP64
+  const float2 bc = a.coef ? a.coef[a.step_off] : make_float2(1.f, 1.f);
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");  // gradients of the LED kernel
+  if (blockIdx.x == 0) {  // first block: the scalar parameters (longest dependency chain)
+    scalar_update(a, bc.x, bc.y);
     return;
   }
   if (!a.assemble && !(a.learn & 1u)) return;
-  __shared__ int2 corner[MAX_BATCH];  // (first column, first row) of each slot's box
+  __shared__ int lst[MAX_BATCH];
+  __shared__ int nl;
+  const int x = a.x_lo + (int)blockIdx.x - 1;
+  const int W = a.W;
   for (int kk = threadIdx.x; kk < a.B; kk += blockDim.x) {
     const int2 n = a.n_int[a.idx[kk]];
     corner[kk] = make_int2(a.N / 2 + n.y - a.h, a.N / 2 + n.x - a.h);
   }
   __syncthreads();
-  const int x = a.x_lo + blockIdx.x;
+  if (threadIdx.x == 0) {  // batch slots whose box covers this column, in batch order
+    int c = 0;
+    for (int kk = 0; kk < a.B; ++kk)
+      if ((unsigned)(x - corner[kk].x) < (unsigned)W) lst[c++] = kk;
+    nl = c;
+  }
+  __syncthreads();
   const int2 span = a.span[x];
-  const float lr_bc1 = (float)(a.lr_obj / bc1);
-  const float inv_sqrt_bc2 = (float)(1.0 / sqrt(bc2));
-  const int W = a.W;
+  const float lr_bc1 = a.lr_obj * bc.x;
+  const float inv_sqrt_bc2 = bc.y;
+  const int n_l = nl;
   for (int y = span.x + threadIdx.x; y < span.y; y += blockDim.x) {
-    float2 g = make_float2(0.f, 0.f);
-    for (int kk = 0; kk < a.B; ++kk) {
-      const int cx = x - corner[kk].x, ry = y - corner[kk].y;
-      if ((unsigned)cx < (unsigned)W && (unsigned)ry < (unsigned)W)
-        g = cadd(g, a.gbox[((size_t)kk * W + cx) * W + ry]);
-    }
     const size_t o = (size_t)x * a.N + y;
+    float2 w, m, v;
+    if (!a.assemble) {  // independent of the gradient: issue first
+      w = a.Ot[o];
+      m = a.mO[o];
+      v = a.vO[o];
+    }
+    // sum of the covering boxes in batch order (adding zeros where a box
+    // does not reach this row), four loads in flight at a time
+    float2 g = make_float2(0.f, 0.f);
+    int q = 0;
+    for (; q + 4 <= n_l; q += 4) {
+      float2 t[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int kk = lst[q + u];
+        const int ry = y - corner[kk].y, cx = x - corner[kk].x;
+        t[u] = (unsigned)ry < (unsigned)W ? a.gbox[((size_t)kk * W + cx) * W + ry] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) g = cadd(g, t[u]);
+    }
+    for (; q < n_l; ++q) {
+      const int kk = lst[q];
+      const int ry = y - corner[kk].y, cx = x - corner[kk].x;
+      if ((unsigned)ry < (unsigned)W) g = cadd(g, a.gbox[((size_t)kk * W + cx) * W + ry]);
+    }
     if (a.assemble) {
       a.g_obj[o] = g;
       continue;
     }
-    float2 w = a.Ot[o], m = a.mO[o], v = a.vO[o];
     adam1(w.x, m.x, v.x, g.x, lr_bc1, inv_sqrt_bc2, a.b1, a.b2, a.eps);
     adam1(w.y, m.y, v.y, g.y, lr_bc1, inv_sqrt_bc2, a.b1, a.b2, a.eps);
     a.Ot[o] = w;
@@ -125,10 +159,19 @@ __global__ void __launch_bounds__(UPD_NT) update_kernel(const UpdArgs a) {
   }
 }
 
-cudaError_t launch_update(const UpdArgs& a, cudaStream_t s) {
+cudaError_t launch_update(const UpdArgs& a, cudaStream_t s, bool pdl) {
   const size_t smem = sizeof(double) * ((size_t)sp_size(a.n_leds) + NPART);
-  update_kernel<<<a.n_cols + 1, UPD_NT, smem, s>>>(a);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(a.n_cols + 1), 1, 1);
+  cfg.blockDim = dim3(UPD_NT, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, update_kernel, a);
 }
 
 }  // namespace fpmk

@@ -157,7 +157,9 @@ class Engine:
 
     # -- API ---------------------------------------------------------------
     def set_hparams(self, lr=None, betas=(0.9, 0.999), eps=1e-8, loss="amplitude", learn=("object",)):
-        lr = dict(object=0.1, zernike=0.01, defocus=0.1, gamma=0.01, offset=0.01, **(lr or {}))
+        rates = dict(object=0.1, zernike=0.01, defocus=0.1, gamma=0.01, offset=0.01)
+        rates.update(lr or {})
+        lr = rates
         mask = 0
         for k in learn:
             mask |= LEARN[k]

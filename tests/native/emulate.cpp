@@ -11,28 +11,46 @@ using namespace fpmk;
 
 template <int M>
 static void run_fft() {
-  std::vector<float2> tw(M), buf(M);
+  std::vector<float2> tw(M), buf(M + M / 8);
   for (int t = 0; t < M; ++t) {
     const double a = -2.0 * M_PI * t / M;
     tw[t] = make_float2((float)std::cos(a), (float)std::sin(a));
   }
   for (int dir = -1; dir <= 1; dir += 2) {
     for (int t = 0; t < M; ++t)
-      buf[t] = make_float2((float)std::sin(0.37 * t + 0.1 * M), (float)std::cos(0.91 * t) - 0.25f);
+      buf[pidx(t)] = make_float2((float)std::sin(0.37 * t + 0.1 * M), (float)std::cos(0.91 * t) - 0.25f);
     if (dir < 0) fft_group_emulate<M, -1>(buf.data(), tw.data());
     else fft_group_emulate<M, +1>(buf.data(), tw.data());
     std::printf("fft %d %d", M, dir);
-    for (int t = 0; t < M; ++t) std::printf(" %.9g %.9g", buf[t].x, buf[t].y);
+    for (int t = 0; t < M; ++t) std::printf(" %.9g %.9g", buf[pidx(t)].x, buf[pidx(t)].y);
+    std::printf("\n");
+  }
+}
+
+static void run_fft256() {
+  const int M = 256;
+  std::vector<float2> tw(M), buf(M + M / 16);
+  for (int t = 0; t < M; ++t) {
+    const double a = -2.0 * M_PI * t / M;
+    tw[t] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  for (int dir = -1; dir <= 1; dir += 2) {
+    for (int t = 0; t < M; ++t)
+      buf[pidx16(t)] = make_float2((float)std::sin(0.37 * t + 0.1 * M), (float)std::cos(0.91 * t) - 0.25f);
+    if (dir < 0) fft256_emulate<-1>(buf.data(), tw.data());
+    else fft256_emulate<+1>(buf.data(), tw.data());
+    std::printf("fft %d %d", M, dir);
+    for (int t = 0; t < M; ++t) std::printf(" %.9g %.9g", buf[pidx16(t)].x, buf[pidx16(t)].y);
     std::printf("\n");
   }
 }
 
 int main() {
+  run_fft256();
   run_fft<16>();
   run_fft<32>();
   run_fft<64>();
   run_fft<128>();
-  run_fft<256>();
   for (int i = 0; i < 40; ++i) {
     const float x = (float)std::sin(1.3 * i) * 1.05f, y = (float)std::cos(0.7 * i + 0.2) * 0.9f;
     Zern z;
@@ -40,6 +58,28 @@ int main() {
     std::printf("zern %.9g %.9g", x, y);
     for (int j = 0; j < 14; ++j) std::printf(" %.9g %.9g %.9g", z.v[j], z.dx[j], z.dy[j]);
     std::printf("\n");
+  }
+  // aberration phase and its gradient through the monomial basis
+  {
+    float c[14];
+    for (int j = 0; j < 14; ++j) c[j] = 0.3f * (float)std::cos(1.7 * j + 0.4);
+    float K[15], Dx[10], Dy[10];
+    theta_poly(c, K, Dx, Dy);
+    for (int i = 0; i < 30; ++i) {
+      const float x = (float)std::sin(2.3 * i) * 1.05f, y = (float)std::cos(0.37 * i + 1.0) * 1.05f;
+      float mo[15];
+      monomials(x, y, mo);
+      float th = 0.f, gx = 0.f, gy = 0.f;
+      for (int m = 0; m < 15; ++m) th += K[m] * mo[m];
+      for (int m = 0; m < 10; ++m) { gx += Dx[m] * mo[m]; gy += Dy[m] * mo[m]; }
+      std::printf("theta %.9g %.9g %.9g %.9g %.9g", x, y, th, gx, gy);
+      for (int j = 0; j < 14; ++j) {  // Z_j through the monomial rows
+        float z = 0.f;
+        for (int m = 0; m < 15; ++m) z += zern_mono(j, m) * mo[m];
+        std::printf(" %.9g", z);
+      }
+      std::printf("\n");
+    }
   }
   // pupil value on a few q for fixed coefficients
   float zc[14];

@@ -70,3 +70,15 @@ def test_pupil_matches_oracle(emulated):
         P = orc.pupil(g, zc, z, [-qy, -qx])
         ref = P["M"][0, 0]
         assert abs(complex(re, im) - ref) < 2e-5, (edge, qy, qx, complex(re, im), ref)
+
+
+def test_monomial_basis_matches_oracle(emulated):
+    c = 0.3 * np.cos(1.7 * np.arange(14) + 0.4)
+    for vals in emulated["theta"]:
+        v = np.array(vals, float)
+        x, y, th, gx, gy = v[:5]
+        zs = v[5:]
+        ref_th = sum(cj * orc.zernike(j, x, y) for j, cj in zip(range(2, 16), c))
+        ref_g = [sum(cj * orc.zernike_grad(j, x, y)[a] for j, cj in zip(range(2, 16), c)) for a in (0, 1)]
+        np.testing.assert_allclose([th, gx, gy], [ref_th, *ref_g], rtol=3e-6, atol=3e-6)
+        np.testing.assert_allclose(zs, [orc.zernike(j, x, y) for j in range(2, 16)], rtol=3e-6, atol=3e-6)
