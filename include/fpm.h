@@ -191,9 +191,54 @@ int fpm_dims(const fpm_handle* h, int32_t* N, int32_t* m, int32_t* n_leds, int32
  * identity (for i = n-1 .. 1: j = next() mod (i + 1); swap). No GPU needed. */
 int fpm_epoch_permutation(int32_t n, uint64_t seed, int32_t epoch, int32_t* out);
 
+/* ---- Allocation-free gradients -------------------------------------------
+ * For callers that cannot allocate device memory: code running while a host
+ * framework owns the device memory pool (where a cudaMalloc would bypass it or
+ * is not allowed), or real-time acquisition loops in which an allocation may
+ * block. The paper has no counterpart: this is an interface convenience, not
+ * a step of the method.
+ *
+ * Computes the same batch loss and gradients as fpm_backward with the built-in
+ * loss (same model, same kernels), without a handle and without allocating
+ * anything. Every input and output is a device buffer owned by the caller; the
+ * intermediates (per-LED gradient boxes, per-LED FP64 partials, LED tables)
+ * live in one static device array of FPM_STATIC_SCRATCH_BYTES inside the
+ * library, which every GPU that loads the library holds until the process
+ * exits. A batch needs about B * (2h+1)^2 * 8 + B * 152 bytes of it
+ * (h = floor(R + 1/2 + sqrt(2)) + 1) plus small tables; larger batches are
+ * rejected with FPM_ERR_SHAPE and a message giving both sizes.
+ *
+ * The array is shared by all calls on a device and keeps the last call's
+ * contents (each call clears what must start at zero); calls whose device
+ * work overlaps (two streams, two host threads) race on it.
+ * The first call on a device looks up the array's device address and sets the
+ * kernels' attributes (once per device, with that device current); make that
+ * first call before any stream capture.
+ *
+ * g, pupil_radius_px, upsample: as fpm_create (the rounded LED offsets give the
+ *   crop positions; delta comes from `params`).
+ * O_t      device [N][N][2] object spectrum, COLUMN-major: element (row y, col x)
+ *          at index x * N + y (the transpose of fpm_get's layout).
+ * params   device [15 + 3 n_leds]: zernike[14], defocus, gamma[n_leds], delta[n_leds][2].
+ * stack    device [n_leds][m][m] measured intensities.
+ * idx      host [B] distinct LED indices; B in [1, n_leds].
+ * loss     FPM_LOSS_AMPLITUDE or FPM_LOSS_INTENSITY.
+ * g_object_t  device [N][N][2], column-major like O_t; every element is written.
+ * g_params    device [15 + 3 n_leds], same layout as params; LEDs outside idx get 0.
+ * loss_out    device [1] FP64 batch loss (NaN/Inf if the data are not finite).
+ * cuda_stream cudaStream_t for all of the call's device work (NULL = default).
+ * Returns after enqueueing; results are ready when the stream reaches them.
+ * Errors are reported by fpm_last_error(NULL). */
+#define FPM_STATIC_SCRATCH_BYTES (4u << 20)
+int fpm_gradients_static(const fpm_geometry* g, float pupil_radius_px, int32_t upsample,
+                         const float* O_t, const float* params, const float* stack,
+                         const int32_t* idx, int32_t B, int32_t loss,
+                         float* g_object_t, float* g_params, double* loss_out, void* cuda_stream);
+
 void fpm_destroy(fpm_handle* h);
 
-/* Last error message of the handle (or of the last failed fpm_create when h is NULL). */
+/* Last error message of the handle (or, when h is NULL, of the last failed
+ * fpm_create or fpm_gradients_static on this thread). */
 const char* fpm_last_error(const fpm_handle* h);
 
 #ifdef __cplusplus

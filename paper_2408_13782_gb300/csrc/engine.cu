@@ -28,6 +28,8 @@ namespace {
 thread_local std::string g_create_error;
 }
 
+void fpmk::set_unbound_error(const char* msg) { g_create_error = msg; }
+
 struct fpm_handle {
   int N = 0, m = 0, n = 0, s = 0, h = 0, W = 0, C = 0;
   float R = 0.f, lambda = 0.f, dk = 0.f;

@@ -75,6 +75,9 @@ cudaError_t led_prepare(int m, int C, int W);
 cudaError_t launch_led(int m, int C, const LedArgs& a, cudaStream_t s, bool pdl);
 cudaError_t launch_update(const UpdArgs& a, cudaStream_t s, bool pdl);
 
+// Message returned by fpm_last_error(NULL) (calls that have no handle).
+void set_unbound_error(const char* msg);
+
 // Field kernels (initialisation, object transforms, layout changes).
 cudaError_t launch_upsample_centre(const float* I, int m, int s, float2* out_rowmajor, cudaStream_t st);
 cudaError_t launch_fft_rows(float2* data, int N, const float2* twN, int dir, cudaStream_t st);

@@ -29,7 +29,7 @@ LOAD_INIT = 1
 EXPORTS = ("fpm_create", "fpm_set_hparams", "fpm_get_hparams", "fpm_load", "fpm_step", "fpm_run",
            "fpm_epoch_loss", "fpm_profile_run", "fpm_forward", "fpm_backward", "fpm_get", "fpm_set", "fpm_set_object_field",
            "fpm_state_size", "fpm_get_state", "fpm_set_state", "fpm_dims", "fpm_epoch_permutation",
-           "fpm_destroy", "fpm_last_error")
+           "fpm_gradients_static", "fpm_destroy", "fpm_last_error")
 
 
 class FpmError(RuntimeError):
@@ -82,6 +82,8 @@ def lib():
         "fpm_set_state": ([vp, f32p], i32),
         "fpm_dims": ([vp, vp, vp, vp, vp], i32),
         "fpm_epoch_permutation": ([i32, ctypes.c_uint64, i32, vp], i32),
+        "fpm_gradients_static": ([ctypes.POINTER(Geometry), ctypes.c_float, i32, vp, vp, vp, vp, i32, i32,
+                                  vp, vp, vp, vp], i32),
         "fpm_destroy": ([vp], None),
         "fpm_last_error": ([vp], ctypes.c_char_p),
     }
@@ -112,6 +114,23 @@ def epoch_permutation(n: int, seed: int, epoch: int) -> np.ndarray:
     if rc:
         raise FpmError(rc, "bad arguments")
     return out
+
+
+def gradients_static(m, upsample, led_offset, pupil_radius, lambda_um, dk_per_um, edge, O_t, params, stack,
+                     idx, g_object_t, g_params, loss_out, loss="amplitude", stream=0):
+    """fpm_gradients_static: loss and gradients with caller-owned device buffers only.
+
+    For callers that cannot allocate device memory (see include/fpm.h). O_t,
+    params, stack, g_object_t, g_params and loss_out are CUDA tensors (column-major
+    O and gradient: element (row y, col x) at x * N + y); idx is a host sequence."""
+    off = np.ascontiguousarray(np.asarray(led_offset, np.float32).reshape(-1, 2))
+    g = Geometry(m, off.shape[0], off.ctypes.data, lambda_um, dk_per_um, EDGE[edge])
+    b = np.ascontiguousarray(np.asarray(idx, np.int32))
+    rc = lib().fpm_gradients_static(ctypes.byref(g), pupil_radius, upsample, _ptr(O_t), _ptr(params), _ptr(stack),
+                                    b.ctypes.data, b.size, LOSS[loss], _ptr(g_object_t), _ptr(g_params),
+                                    _ptr(loss_out), ctypes.c_void_p(stream))
+    if rc:
+        raise FpmError(rc, lib().fpm_last_error(None).decode())
 
 
 class Engine:
