@@ -204,8 +204,9 @@ int fpm_epoch_permutation(int32_t n, uint64_t seed, int32_t epoch, int32_t* out)
  * intermediates (per-LED gradient boxes, per-LED FP64 partials, LED tables)
  * live in one static device array of FPM_STATIC_SCRATCH_BYTES inside the
  * library, which every GPU that loads the library holds until the process
- * exits. A batch needs about B * (2h+1)^2 * 8 + B * 152 bytes of it
- * (h = floor(R + 1/2 + sqrt(2)) + 1) plus small tables; larger batches are
+ * exits. A batch needs about B * (2h+1)^2 * 8 + B * C * 152 bytes of it
+ * (h = floor(R + 1/2 + sqrt(2)) + 1; C = 8 for m = 256, m/16 below) plus small
+ * tables; larger batches are
  * rejected with FPM_ERR_SHAPE and a message giving both sizes.
  *
  * The array is shared by all calls on a device and keeps the last call's

@@ -96,7 +96,9 @@ FPM_HD void zernike_eval(float x, float y, Zern& z) {
     /* Z15 */ {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 4 * FPM_S10, 0, -4 * FPM_S10, 0},                    \
   }
 #if defined(__CUDACC__)
-static __constant__ float kZernMonoDev[14][15] = FPM_ZERN_MONO_TABLE;
+// global (not __constant__) memory: kernels read it with divergent indices,
+// which the constant cache would serialise
+static __device__ const float kZernMonoDev[14][15] = FPM_ZERN_MONO_TABLE;
 #endif
 static const float kZernMonoHost[14][15] = FPM_ZERN_MONO_TABLE;
 
@@ -115,6 +117,43 @@ FPM_HD void monomials(float x, float y, float (&mo)[15]) {
   mo[3] = x2; mo[4] = xy; mo[5] = y2;
   mo[6] = x2 * x; mo[7] = x2 * y; mo[8] = x * y2; mo[9] = y2 * y;
   mo[10] = x2 * x2; mo[11] = x2 * xy; mo[12] = x2 * y2; mo[13] = xy * y2; mo[14] = y2 * y2;
+}
+
+// Entry e of the 35 polynomial coefficients (K[15], Dx[10], Dy[10] below)
+// computed on its own, so 35 threads can fill them in parallel:
+// K[m] = sum_j c_j (Z_j)_m; Dx for monomial x^a y^b (a + b <= 3) is
+// (a+1) K[x^(a+1) y^b], Dy is (b+1) K[x^a y^(b+1)].
+// zm: the 14 x 15 table (row j-2 = Z_j), e.g. staged in shared memory.
+FPM_HD float theta_poly_entry_tab(const float* c, const float* zm, int e) {
+  int m = e, f = 1;
+  if (e >= 15) {
+    const int mm = e < 25 ? e - 15 : e - 25;
+    const int d = mm == 0 ? 0 : (mm < 3 ? 1 : (mm < 6 ? 2 : 3));
+    const int b = mm - d * (d + 1) / 2, a = d - b;
+    if (e < 25) { m = (d + 1) * (d + 2) / 2 + b; f = a + 1; }
+    else { m = (d + 1) * (d + 2) / 2 + b + 1; f = b + 1; }
+  }
+  float s = 0.f;
+  for (int j = 0; j < 14; ++j) s = fmaf(c[j], zm[j * 15 + m], s);
+  return (float)f * s;
+}
+
+#if defined(__CUDACC__)
+__device__ __forceinline__ const float* zern_mono_table() { return &kZernMonoDev[0][0]; }
+#endif
+
+FPM_HD float theta_poly_entry(const float* c, int e) {
+  int m = e, f = 1;
+  if (e >= 15) {
+    const int mm = e < 25 ? e - 15 : e - 25;
+    const int d = mm == 0 ? 0 : (mm < 3 ? 1 : (mm < 6 ? 2 : 3));
+    const int b = mm - d * (d + 1) / 2, a = d - b;
+    if (e < 25) { m = (d + 1) * (d + 2) / 2 + b; f = a + 1; }
+    else { m = (d + 1) * (d + 2) / 2 + b + 1; f = b + 1; }
+  }
+  float s = 0.f;
+  for (int j = 0; j < 14; ++j) s = fmaf(c[j], zern_mono(j, m), s);
+  return (float)f * s;
 }
 
 // For aberration coefficients c[14] (Noll 2..15): theta = sum_m K[m] mo[m],

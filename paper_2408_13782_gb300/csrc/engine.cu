@@ -50,7 +50,7 @@ struct fpm_handle {
   float2* gbox = nullptr;
   double* part = nullptr;
   int capB = 0;
-  int* sched = nullptr;
+  int4* sched = nullptr;  // batch slots (LED, n_row, n_col, 0) of the current run
   int cap_sched = 0;
   double* losses = nullptr;
   int cap_losses = 0;
@@ -60,7 +60,7 @@ struct fpm_handle {
   int cap_coef = 0;
   int* err = nullptr;
   // pinned staging
-  int* h_sched = nullptr;
+  int4* h_sched = nullptr;
   int cap_h_sched = 0;
   float2* h_coef = nullptr;
   int cap_h_coef = 0;
@@ -207,7 +207,7 @@ int ensure_batch(fpm_handle* h, int B) {
   h->part = nullptr;
   h->capB = 0;
   CK(h, cudaMalloc(&h->gbox, sizeof(float2) * (size_t)B * h->W * h->W));
-  CK(h, cudaMalloc(&h->part, sizeof(double) * (size_t)B * NPART));
+  CK(h, cudaMalloc(&h->part, sizeof(double) * (size_t)B * h->C * NPART));
   h->capB = B;
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();
@@ -224,13 +224,20 @@ int ensure_fbuf(fpm_handle* h, size_t floats) {
   return FPM_OK;
 }
 
-LedArgs led_args(fpm_handle* h, const int* idx_dev, int B, int mode) {
+// Batch slots for LED indices idx[0..count): (LED, crop row, crop col, 0).
+void fill_slots(const fpm_handle* h, const int32_t* idx, int count, int4* dst) {
+  for (int q = 0; q < count; ++q) {
+    const int i = idx[q];
+    dst[q] = make_int4(i, h->nint_h[i].x, h->nint_h[i].y, 0);
+  }
+}
+
+LedArgs led_args(fpm_handle* h, const int4* slot_dev, int B, int mode) {
   LedArgs a{};
   a.Ot = h->Ot;
   a.meas = h->meas;
   a.sp = h->sp;
-  a.n_int = h->nint;
-  a.idx = idx_dev;
+  a.slot = slot_dev;
   a.gbox = h->gbox;
   a.part = h->part;
   a.tw = h->tw_m;
@@ -250,7 +257,7 @@ LedArgs led_args(fpm_handle* h, const int* idx_dev, int B, int mode) {
   return a;
 }
 
-UpdArgs upd_args(fpm_handle* h, const int* idx_dev, int B, int step_off, double* loss_slot, int assemble) {
+UpdArgs upd_args(fpm_handle* h, const int4* slot_dev, int B, int step_off, double* loss_slot, int assemble) {
   UpdArgs u{};
   u.Ot = h->Ot;
   u.mO = h->mO;
@@ -260,8 +267,7 @@ UpdArgs upd_args(fpm_handle* h, const int* idx_dev, int B, int step_off, double*
   u.vsp = h->vsp;
   u.gbox = h->gbox;
   u.part = h->part;
-  u.idx = idx_dev;
-  u.n_int = h->nint;
+  u.slot = slot_dev;
   u.span = h->span;
   u.x_lo = h->x_lo;
   u.n_cols = h->n_cols;
@@ -322,14 +328,14 @@ int copy_out(fpm_handle* h, void* dst, const void* src, size_t bytes, bool* host
 int build_graph(fpm_handle* h, int n_steps, int B, cudaGraphExec_t* out) {
   cudaGraph_t g = nullptr;
   CK(h, cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = cudaMemcpyAsync(h->sched, h->h_sched, sizeof(int) * (size_t)n_steps * B,
+  cudaError_t e = cudaMemcpyAsync(h->sched, h->h_sched, sizeof(int4) * (size_t)n_steps * B,
                                   cudaMemcpyHostToDevice, h->st);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(h->coef, h->h_coef, sizeof(float2) * n_steps, cudaMemcpyHostToDevice, h->st);
   // kernels after the first may start early (programmatic dependent launch)
   // and wait in-kernel for their predecessor's results
   for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
-    const int* idx = h->sched + (size_t)s * B;
+    const int4* idx = h->sched + (size_t)s * B;
     e = launch_led(h->m, h->C, led_args(h, idx, B, MODE_LOSS), h->st, s > 0);
     if (e == cudaSuccess) e = launch_update(upd_args(h, idx, B, s, h->losses + s, 0), h->st, true);
   }
@@ -453,7 +459,8 @@ int fpm_create(const fpm_geometry* g, float R, int32_t upsample, void* cuda_stre
             ck(cudaMalloc(&h->epoch, sizeof(double)), "alloc") &&
             ck(cudaMalloc(&h->err, sizeof(int)), "alloc") &&
             ck(cudaMallocHost(&h->h_err, sizeof(int)), "pinned") &&
-            ck(led_prepare(h->m, (h->C = led_choose_cluster(h->m, h->W)), h->W), "kernel attributes");
+            ck(led_prepare(h->m, (h->C = led_choose_cluster(h->m, h->W)), h->W), "kernel attributes") &&
+            ck(update_prepare(), "kernel attributes");
   if (ok) {
     const auto twm = twiddles(h->m), twN = twiddles(h->N);
     ok = ck(cudaMemcpy(h->tw_m, twm.data(), sizeof(float2) * h->m, cudaMemcpyHostToDevice), "copy") &&
@@ -557,12 +564,12 @@ int fpm_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int32_t B, 
     if (h->h_sched) CK(h, cudaFreeHost(h->h_sched));
     h->h_sched = nullptr;
     h->cap_h_sched = 0;
-    CK(h, cudaMallocHost(&h->h_sched, sizeof(int) * (size_t)n_steps * B));
+    CK(h, cudaMallocHost(&h->h_sched, sizeof(int4) * (size_t)n_steps * B));
     h->cap_h_sched = n_steps * B;
     for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
     h->graphs.clear();
   }
-  std::memcpy(h->h_sched, schedule, sizeof(int) * (size_t)n_steps * B);
+  fill_slots(h, schedule, n_steps * B, h->h_sched);
   fill_coef(h, n_steps, h->h_coef);
   auto key = std::make_pair(n_steps, B);
   auto it = h->graphs.find(key);
@@ -599,7 +606,9 @@ int fpm_profile_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int
   if ((rc = grow(h, &h->losses, &h->cap_losses, n_steps))) return rc;
   if ((rc = enter(h))) return rc;
   if ((rc = grow(h, &h->coef, &h->cap_coef, n_steps))) return rc;
-  CK(h, cudaMemcpyAsync(h->sched, schedule, sizeof(int) * (size_t)n_steps * B, cudaMemcpyHostToDevice, h->st));
+  std::vector<int4> slots((size_t)n_steps * B);
+  fill_slots(h, schedule, n_steps * B, slots.data());
+  CK(h, cudaMemcpyAsync(h->sched, slots.data(), sizeof(int4) * slots.size(), cudaMemcpyHostToDevice, h->st));
   std::vector<float2> coef(n_steps);
   fill_coef(h, n_steps, coef.data());
   CK(h, cudaMemcpyAsync(h->coef, coef.data(), sizeof(float2) * n_steps, cudaMemcpyHostToDevice, h->st));
@@ -618,7 +627,7 @@ int fpm_profile_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int
   // each timed window holds only device work.
   cudaError_t e = cudaSuccess;
   for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
-    const int* idx = h->sched + (size_t)s * B;
+    const int4* idx = h->sched + (size_t)s * B;
     if (flush) e = cudaMemsetAsync(flush, s & 0xff, (size_t)flush_bytes, h->st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s], h->st);
     if (e == cudaSuccess) e = launch_led(h->m, h->C, led_args(h, idx, B, MODE_LOSS), h->st, false);
@@ -673,7 +682,9 @@ int fpm_forward(fpm_handle* h, const int32_t* idx, int32_t B, float* I_out) {
   const bool dev_out = is_device_ptr(I_out);
   if (!dev_out && (rc = ensure_fbuf(h, img))) return rc;
   if ((rc = enter(h))) return rc;
-  CK(h, cudaMemcpyAsync(h->sched, idx, sizeof(int) * B, cudaMemcpyHostToDevice, h->st));
+  std::vector<int4> slots(B);
+  fill_slots(h, idx, B, slots.data());
+  CK(h, cudaMemcpyAsync(h->sched, slots.data(), sizeof(int4) * B, cudaMemcpyHostToDevice, h->st));
   LedArgs a = led_args(h, h->sched, B, MODE_FORWARD);
   a.I_out = dev_out ? I_out : h->fbuf;
   CK(h, launch_led(h->m, h->C, a, h->st, false));
@@ -698,7 +709,9 @@ int fpm_backward(fpm_handle* h, const int32_t* idx, int32_t B, const float* dL_d
   if (dev_in && ((uintptr_t)dL_dI & 15)) return fail(h, FPM_ERR_ARG, "device dL_dI must be 16-byte aligned");
   if (dL_dI && !dev_in && (rc = ensure_fbuf(h, img))) return rc;
   if ((rc = enter(h))) return rc;
-  CK(h, cudaMemcpyAsync(h->sched, idx, sizeof(int) * B, cudaMemcpyHostToDevice, h->st));
+  std::vector<int4> slots(B);
+  fill_slots(h, idx, B, slots.data());
+  CK(h, cudaMemcpyAsync(h->sched, slots.data(), sizeof(int4) * B, cudaMemcpyHostToDevice, h->st));
   LedArgs a = led_args(h, h->sched, B, dL_dI ? MODE_UPSTREAM : MODE_LOSS);
   if (dL_dI) {
     if (!dev_in) CK(h, cudaMemcpyAsync(h->fbuf, dL_dI, sizeof(float) * img, cudaMemcpyHostToDevice, h->st));

@@ -28,10 +28,9 @@ struct LedArgs {
   const float* dLdI;    // [B][m][m] upstream gradient of the intensities (MODE_UPSTREAM)
   float* I_out;         // [B][m][m] predicted intensities (MODE_FORWARD)
   const float* sp;      // scalar parameters, layout above
-  const int2* n_int;    // [n_leds] integer crop offsets (x = row, y = col)
-  const int* idx;       // [B] LED of each batch slot
+  const int4* slot;     // [B] batch slots: (LED, crop row offset n_row, crop col offset n_col, 0)
   float2* gbox;         // [B][W][W] per-LED object-gradient boxes, [slot][col][row]
-  double* part;         // [B][NPART], summed over the LED's cluster
+  double* part;         // [B][cluster][NPART] per-CTA FP64 partials
   const float2* tw;     // [m] exp(-2 pi i t / m)
   int N, n_leds, B, h, W;
   float R, Rinv, inv_lambda, dk2;
@@ -48,8 +47,7 @@ struct UpdArgs {
   float* vsp;
   const float2* gbox;   // from the LED kernel
   const double* part;
-  const int* idx;
-  const int2* n_int;
+  const int4* slot;     // [B] batch slots, as in LedArgs
   const int2* span;     // [N] per column: [row_lo, row_hi) of the update region
   int x_lo, n_cols;     // update-region columns [x_lo, x_lo + n_cols)
   int N, n_leds, B, C, h, W;
@@ -77,6 +75,9 @@ cudaError_t launch_update(const UpdArgs& a, cudaStream_t s, bool pdl);
 
 // Message returned by fpm_last_error(NULL) (calls that have no handle).
 void set_unbound_error(const char* msg);
+
+// Shared-memory carveout and attributes of the update kernel (call once).
+cudaError_t update_prepare();
 
 // Field kernels (initialisation, object transforms, layout changes).
 cudaError_t launch_upsample_centre(const float* I, int m, int s, float2* out_rowmajor, cudaStream_t st);

@@ -16,6 +16,7 @@
 // kernel exposes global-memory latency about once.
 #include <cooperative_groups.h>
 
+#include "../../include/fpm.h"
 #include "device.cuh"
 #include "internal.h"
 
@@ -50,7 +51,7 @@ struct LedLayout {
     const int chunk = (W + C - 1) / C;
     return sizeof(float) * (size_t)ROWS * M +
            sizeof(float2) * ((size_t)chunk * TS + (size_t)NG * FS + M + NTW2 + (size_t)chunk * W) +
-           sizeof(float) * (NPOLY + (size_t)NW * NACC) + sizeof(double) * (16 + NPART + 1);
+           sizeof(float) * (NPOLY + 14 * 15 + 2 + (size_t)NW * NACC) + sizeof(double) * 16;
   }
 };
 
@@ -107,59 +108,59 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, 2) led_kernel(const LedArgs a) 
   float2* tw2 = tws + M;                                  // [15][16] second-pass twiddles (M = 256)
   float2* Ob = tw2 + L::NTW2;                             // [chunk][W] O on this CTA's box columns
   float* poly = reinterpret_cast<float*>(Ob + (size_t)chunk * W);  // K[15] Dx[10] Dy[10]
-  float* red = poly + L::NPOLY;                           // [NW][NACC]
-  double* dsum = reinterpret_cast<double*>(red + NW * NACC);  // [16 + NPART] (8-byte aligned: float counts are even)
+  float* zmt = poly + L::NPOLY;                           // [14 * 15] Zernike -> monomial table
+  float* red = zmt + 14 * 15 + 2;                         // [NW][NACC]
+  double* dsum = reinterpret_cast<double*>(red + NW * NACC);  // [16] (8-byte aligned: float counts are even)
 
   const int tid = threadIdx.x;
-  const int led = a.idx[k];
+  const int4 slot = a.slot[k];  // (LED, crop row, crop col): one load gives every address
+  const int led = slot.x;
   if (led < 0 || led >= a.n_leds) {  // the same for every CTA of the cluster: uniform exit
     if (tid == 0 && rank == 0) atomicOr(a.err, DERR_INDEX);
     return;
   }
-  // inputs that no earlier kernel writes: image rows, twiddles
+  for (int t = tid; t < M; t += NT) tws[t] = a.tw[t];
+  for (int t = tid; t < 14 * 15; t += NT) zmt[t] = zern_mono_table()[t];
+  pdl_wait();  // O and the scalar parameters come from the previous update
+  // Only now may the next kernel (this step's update) start: it reads O, m
+  // and v before its own wait, which is safe once the previous update, the
+  // one this kernel just waited for, has completed.
+  pdl_launch_dependents();
+  // column-major spectrum: box column c is spectrum column N/2 + n_col - h + c,
+  // and row ky of it sits at offset N/2 + n_row + ky
+  const size_t col0 = (size_t)(N / 2 + slot.z - h);
+  const int row0 = N / 2 + slot.y;
+  {
+    // O on a disk that contains the support for every admissible delta
+    // (|delta| <= sqrt(2) * bound), so the copy does not wait for delta
+    const float rs = (a.hard_edge ? a.R : a.R + 0.5f) + 1.41422f * FPM_OFFSET_BOUND_PX + 1e-3f;
+    const int ncol = c1 > c0 ? c1 - c0 : 0;
+    for (int q = tid; q < ncol * W; q += NT) {
+      const int cl = q / W, r = q - cl * W;
+      const float px = (float)(c0 + cl - h), py = (float)(r - h);
+      if (px * px + py * py <= rs * rs)
+        cp_async8(Ob + q, a.Ot + (col0 + c0 + cl) * N + (row0 - h + r));
+    }
+  }
+  cp_async_commit();  // group 1: O (needed by phase A)
+  // group 2: this CTA's image rows (needed by phase B), arriving during phase A
   const float* rows_src = a.mode == MODE_LOSS ? a.meas + ((size_t)led * M + y0) * M
                         : a.mode == MODE_UPSTREAM ? a.dLdI + ((size_t)k * M + y0) * M : nullptr;
   if (rows_src)
     for (int q = tid; q < ROWS * M / 4; q += NT) cp_async16(ms + 4 * q, rows_src + 4 * q);
   cp_async_commit();
-  for (int t = tid; t < M; t += NT) tws[t] = a.tw[t];
-  pdl_launch_dependents();
-  pdl_wait();  // O and the scalar parameters come from the previous update
-
-  if (tid == 0) {  // aberration phase as a polynomial in the monomials of q/R
-    float c[14], K[15], Dx[10], Dy[10];
-    for (int q = 0; q < 14; ++q) c[q] = a.sp[SP_ZERN + q];
-    theta_poly(c, K, Dx, Dy);
-    for (int q = 0; q < 15; ++q) poly[q] = K[q];
-    for (int q = 0; q < 10; ++q) {
-      poly[15 + q] = Dx[q];
-      poly[25 + q] = Dy[q];
-    }
-  }
+  float zc = 0.f;
+  if (tid < 14) zc = a.sp[SP_ZERN + tid];
   const float zdef = a.sp[SP_DEFOCUS];
   const float gam = a.sp[SP_GAMMA + led];
   const float dly = a.sp[sp_offset(a.n_leds) + 2 * led];
   const float dlx = a.sp[sp_offset(a.n_leds) + 2 * led + 1];
-  const int2 nn = a.n_int[led];
   const PupilConst P{a.R, a.Rinv, a.inv_lambda, a.dk2, a.hard_edge};
-  // column-major spectrum: box column c is spectrum column N/2 + n.y - h + c,
-  // and row ky of it sits at offset N/2 + n.x + ky
-  const size_t col0 = (size_t)(N / 2 + nn.y - h);
-  const int row0 = N / 2 + nn.x;
-  {
-    // radius with a margin: a superset of every pixel where A > 0
-    const float rs = (P.hard_edge ? P.R : P.R + 0.5f) + 1e-3f;
-    const int ncol = c1 > c0 ? c1 - c0 : 0;
-    for (int q = tid; q < ncol * W; q += NT) {
-      const int cl = q / W, r = q - cl * W;
-      const float qx = (float)(c0 + cl - h) - dlx, qy = (float)(r - h) - dly;
-      if (qx * qx + qy * qy <= rs * rs)  // support pixels only (superset of A > 0)
-        cp_async8(Ob + q, a.Ot + (col0 + c0 + cl) * N + (row0 - h + r));
-    }
-  }
-  cp_async_commit();
   const int grp = tid / G, j = tid % G;
   float2* buf = fb + grp * FS;
+  if (tid < 14) red[tid] = zc;   // the aberration coefficients, via the (still unused) reduction area
+  __syncthreads();
+  if (tid < 35) poly[tid] = theta_poly_entry_tab(red, zmt, tid);  // aberration phase as monomials of q/R
   FftTw<M == 256 ? 128 : M> TW;  // radix-8 path: per-thread twiddles in registers
   __syncthreads();                // twiddle table
   if constexpr (M == 256) {
@@ -167,8 +168,8 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, 2) led_kernel(const LedArgs a) 
   } else {
     fft_twiddles<M>(tws, j, TW);
   }
-  cp_async_wait<0>();
-  __syncthreads();  // O slice and image rows in shared memory
+  cp_async_wait<1>();  // all but the most recent group: the O slice
+  __syncthreads();     // O slice in shared memory
 
   // ---------------- phase A: column inverse transforms over ky -------------
   for (int cb = c0; cb < c1; cb += NG) {
@@ -176,14 +177,15 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, 2) led_kernel(const LedArgs a) 
     const bool act = c < c1;
     const float2* Oc = Ob + (size_t)(act ? c - c0 : 0) * W + h;   // index by ky
     const float qx = (float)(c - h) - dlx;
-    for (int t = j; t < M; t += G) {
-      const int ky = t < M / 2 ? t : t - M;
+    for (int t = h + 1 + j; t < M - h; t += G) buf[bidx<M>(t)] = make_float2(0.f, 0.f);  // outside the box
+    for (int r = j; r < W; r += G) {
+      const int ky = r - h;
       float2 v = make_float2(0.f, 0.f);
-      if (act && ky >= -h && ky <= h) {
+      if (act) {
         const float2 Mv = pupil_value_poly((float)ky - dly, qx, P, poly, zdef);
         if (Mv.x != 0.f || Mv.y != 0.f) v = cmul(Oc[ky], Mv);
       }
-      buf[bidx<M>(t)] = v;
+      buf[bidx<M>(ky & (M - 1))] = v;
     }
     __syncwarp();
     transform<M, +1>(buf, TW, tw2, j);
@@ -191,7 +193,8 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, 2) led_kernel(const LedArgs a) 
       for (int t = j; t < M; t += G) T[(c - c0) * TS + t] = buf[bidx<M>(t)];
     __syncwarp();
   }
-  cluster.sync();
+  cp_async_wait<0>();  // image rows
+  cluster.sync();      // (also a block-wide barrier for the rows)
 
   // ---------------- phase B: rows: psi, residual, adjoint row transform ----
   const float inv_m2 = 1.f / (float)(M * M);
@@ -201,15 +204,12 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, 2) led_kernel(const LedArgs a) 
     const int rr = rb + grp;
     const bool act = rr < ROWS;
     const int yl = act ? rr : 0, y = y0 + yl;
-    for (int t = j; t < M; t += G) {
-      const int kx = t < M / 2 ? t : t - M;
+    for (int t = h + 1 + j; t < M - h; t += G) buf[bidx<M>(t)] = make_float2(0.f, 0.f);  // outside the box
+    for (int c = j; c < W; c += G) {
+      const int own = c / chunk, lc = c - own * chunk;
       float2 v = make_float2(0.f, 0.f);
-      if (act && kx >= -h && kx <= h) {
-        const int c = kx + h, own = c / chunk, lc = c - own * chunk;
-        const float2* Tr = cluster.map_shared_rank(T, own);
-        v = Tr[lc * TS + y];
-      }
-      buf[bidx<M>(t)] = v;
+      if (act) v = cluster.map_shared_rank(T, own)[lc * TS + y];
+      buf[bidx<M>((c - h) & (M - 1))] = v;
     }
     __syncwarp();
     transform<M, +1>(buf, TW, tw2, j);
@@ -347,24 +347,18 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, 2) led_kernel(const LedArgs a) 
     for (int w = 0; w < NW; ++w) tot += (double)red[w * NACC + tid];
   if (tid >= A_MONO && tid < A_MONO + 15) dsum[tid - A_MONO] = tot;
   __syncthreads();
-  // this CTA's partials in Zernike form, then summed over the cluster in rank order
-  if (tid == A_LOSS) dsum[16 + P_LOSS] = tot;
-  if (tid == A_GAMMA) dsum[16 + P_GAMMA] = (a.mode == MODE_LOSS && a.loss == 0) ? tot / (double)sg : tot;
-  if (tid == A_DEF) dsum[16 + P_DEFOCUS] = tot;
-  if (tid == A_DY) dsum[16 + P_DY] = tot;
-  if (tid == A_DX) dsum[16 + P_DX] = tot;
+  // this CTA's partials in Zernike form; the update kernel sums the ranks
+  double* out = a.part + ((size_t)k * C + rank) * NPART;
+  if (tid == A_LOSS) out[P_LOSS] = tot;
+  if (tid == A_GAMMA) out[P_GAMMA] = (a.mode == MODE_LOSS && a.loss == 0) ? tot / (double)sg : tot;
+  if (tid == A_DEF) out[P_DEFOCUS] = tot;
+  if (tid == A_DY) out[P_DY] = tot;
+  if (tid == A_DX) out[P_DX] = tot;
   if (tid < 14) {  // dL/dc_j = sum_m (Z_j)_m * (sum_p t(p) mo_m(p))
     double z = 0.0;
-    for (int m = 0; m < 15; ++m) z += (double)zern_mono(tid, m) * dsum[m];
-    dsum[16 + P_ZERN + tid] = z;
+    for (int m = 0; m < 15; ++m) z += (double)zmt[tid * 15 + m] * dsum[m];
+    out[P_ZERN + tid] = z;
   }
-  cluster.sync();
-  if (rank == 0 && tid < NPART) {
-    double s = 0.0;
-    for (int r = 0; r < C; ++r) s += cluster.map_shared_rank(dsum, r)[16 + tid];
-    a.part[(size_t)k * NPART + tid] = s;
-  }
-  cluster.sync();  // keep every CTA's shared memory alive until rank 0 has read it
 }
 
 int led_cluster_size(int m) {
@@ -434,6 +428,10 @@ static cudaError_t prepare_t(int W) {
     e = cudaFuncSetAttribute(led_kernel<M, C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
   }
+  // the largest shared-memory carveout, so the SM configuration does not flip between kernels
+  e = cudaFuncSetAttribute(led_kernel<M, C>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(led_kernel<M, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
 }
 

@@ -6,7 +6,7 @@
 // acquisition loop in which an allocation can block for an unbounded time.
 // They pass their own device buffers for every input and output; the
 // intermediates of the per-LED kernel (per-LED gradient boxes, per-LED FP64
-// partials, LED tables, twiddles, error flag) live in one fixed array,
+// partials, batch slots, column spans, twiddles, error flag) live in one fixed array,
 // g_static_scratch, declared below. Every GPU that loads this library holds
 // that array until the process exits.
 //
@@ -66,6 +66,9 @@ int setup_device(int dev, unsigned char** out) {
       if (e != cudaSuccess)
         return fail_static(FPM_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
     }
+    e = update_prepare();
+    if (e != cudaSuccess)
+      return fail_static(FPM_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
     g_scratch_ptr[dev] = (unsigned char*)p;
     g_ready[dev] = true;
   }
@@ -134,12 +137,11 @@ extern "C" int fpm_gradients_static(const fpm_geometry* g, float R, int32_t upsa
   }
   // ---- layout of the static array; reject what does not fit ----
   const size_t o_tw = 0;
-  const size_t o_nint = align256(o_tw + sizeof(float2) * m);
-  const size_t o_span = align256(o_nint + sizeof(int2) * n);
-  const size_t o_idx = align256(o_span + sizeof(int2) * N);
-  const size_t o_flags = align256(o_idx + sizeof(int) * B);  // int err, then a double sink
+  const size_t o_span = align256(o_tw + sizeof(float2) * m);
+  const size_t o_slot = align256(o_span + sizeof(int2) * N);
+  const size_t o_flags = align256(o_slot + sizeof(int4) * B);  // int err, then a double sink
   const size_t o_part = align256(o_flags + 16);
-  const size_t o_box = align256(o_part + sizeof(double) * (size_t)B * NPART);
+  const size_t o_box = align256(o_part + sizeof(double) * (size_t)B * static_cluster(m) * NPART);
   const size_t need = o_box + sizeof(float2) * (size_t)B * W * W;
   if (need > FPM_STATIC_SCRATCH_BYTES)
     return fail_static(FPM_ERR_SHAPE, "this batch needs " + std::to_string(need) +
@@ -166,9 +168,8 @@ extern "C" int fpm_gradients_static(const fpm_geometry* g, float R, int32_t upsa
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   float2* d_tw = (float2*)(base + o_tw);
-  int2* d_nint = (int2*)(base + o_nint);
   int2* d_span = (int2*)(base + o_span);
-  int* d_idx = (int*)(base + o_idx);
+  int4* d_slot = (int4*)(base + o_slot);
   int* d_err = (int*)(base + o_flags);
   double* d_sink = (double*)(base + o_flags + 8);
   double* d_part = (double*)(base + o_part);
@@ -179,9 +180,10 @@ extern "C" int fpm_gradients_static(const fpm_geometry* g, float R, int32_t upsa
     if (e_ != cudaSuccess) return fail_static(FPM_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
   } while (0)
   CKS(cudaMemcpyAsync(d_tw, tw.data(), sizeof(float2) * m, cudaMemcpyHostToDevice, st));
-  CKS(cudaMemcpyAsync(d_nint, nint.data(), sizeof(int2) * n, cudaMemcpyHostToDevice, st));
+  std::vector<int4> slots(B);
+  for (int b = 0; b < B; ++b) slots[b] = make_int4(idx[b], nint[idx[b]].x, nint[idx[b]].y, 0);
   CKS(cudaMemcpyAsync(d_span, span.data(), sizeof(int2) * N, cudaMemcpyHostToDevice, st));
-  CKS(cudaMemcpyAsync(d_idx, idx, sizeof(int) * B, cudaMemcpyHostToDevice, st));
+  CKS(cudaMemcpyAsync(d_slot, slots.data(), sizeof(int4) * B, cudaMemcpyHostToDevice, st));
   CKS(cudaMemsetAsync(d_err, 0, 16, st));
   CKS(cudaMemsetAsync(g_object_t, 0, sizeof(float2) * (size_t)N * N, st));
 
@@ -189,8 +191,7 @@ extern "C" int fpm_gradients_static(const fpm_geometry* g, float R, int32_t upsa
   a.Ot = (const float2*)O_t;
   a.meas = stack;
   a.sp = params;
-  a.n_int = d_nint;
-  a.idx = d_idx;
+  a.slot = d_slot;
   a.gbox = d_box;
   a.part = d_part;
   a.tw = d_tw;
@@ -212,8 +213,7 @@ extern "C" int fpm_gradients_static(const fpm_geometry* g, float R, int32_t upsa
   UpdArgs u{};
   u.gbox = d_box;
   u.part = d_part;
-  u.idx = d_idx;
-  u.n_int = d_nint;
+  u.slot = d_slot;
   u.span = d_span;
   u.x_lo = lo_x;
   u.n_cols = hi_x - lo_x;

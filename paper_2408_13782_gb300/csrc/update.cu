@@ -8,7 +8,7 @@
 // no-op) gathers the per-LED gradient boxes in batch order - a fixed-order
 // sum, so results are bitwise reproducible - and takes one Adam step on its
 // real and imaginary parts. One CTA per spectrum column of the region.
-// Scalars: the first CTA reduces the per-LED FP64 partials in a fixed order,
+// Scalars: the first CTA reduces the per-CTA FP64 partials in a fixed order,
 // forms the gradients of the Zernike coefficients, defocus, intensity factors
 // and LED offsets, and updates all of them (every element, every step).
 #include <cmath>
@@ -39,23 +39,30 @@ __device__ void scalar_update(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc
   double* tot = gsh + P;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
   for (int i = tid; i < P; i += blockDim.x) gsh[i] = 0.0;
-  __syncthreads();  // part holds one FP64 set per batch slot (already summed over its cluster)
-  // quantities shared by all LEDs (loss, Zernike, defocus): one warp each,
-  // fixed per-lane order and a fixed shuffle tree, so the sum is reproducible
+  __syncthreads();  // part holds one FP64 set per CTA of each slot's cluster
+  // quantities shared by all LEDs (loss, Zernike, defocus): one warp each over
+  // the B x C per-CTA partials, fixed per-lane order and a fixed shuffle tree
+  const int nparts = a.B * a.C;
   for (int qi = warp; qi < 16; qi += nwarp) {
     const int q = qi == 0 ? P_LOSS : (qi <= 14 ? P_ZERN + qi - 1 : P_DEFOCUS);
     double s = 0.0;
-    for (int kk = lane; kk < a.B; kk += 32) s += a.part[(size_t)kk * NPART + q];
+    for (int e = lane; e < nparts; e += 32) s += a.part[(size_t)e * NPART + q];
     s = warp_sum_d(s);
     if (lane == 0) tot[q] = s;
   }
-  // per-LED quantities
+  // per-LED quantities: the C ranks of each slot in rank order
   for (int kk = tid; kk < a.B; kk += blockDim.x) {
-    const int led = a.idx[kk];
-    const double* p = a.part + (size_t)kk * NPART;
-    gsh[SP_GAMMA + led] = p[P_GAMMA];
-    gsh[sp_offset(n) + 2 * led] = p[P_DY];
-    gsh[sp_offset(n) + 2 * led + 1] = p[P_DX];
+    const int led = a.slot[kk].x;
+    double sg = 0.0, sy = 0.0, sx = 0.0;
+    for (int r = 0; r < a.C; ++r) {
+      const double* p = a.part + ((size_t)kk * a.C + r) * NPART;
+      sg += p[P_GAMMA];
+      sy += p[P_DY];
+      sx += p[P_DX];
+    }
+    gsh[SP_GAMMA + led] = sg;
+    gsh[sp_offset(n) + 2 * led] = sy;
+    gsh[sp_offset(n) + 2 * led + 1] = sx;
   }
   __syncthreads();
   if (tid < 14) gsh[SP_ZERN + tid] = tot[P_ZERN + tid];
@@ -91,21 +98,34 @@ __device__ void scalar_update(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc
 __global__ void __launch_bounds__(UPD_NT) update_kernel(const UpdArgs a) {
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   __shared__ int2 corner[MAX_BATCH];  // (first column, first row) of each slot's box
-  // bias corrections of this step, computed on the host in FP64
+  __shared__ int lst[MAX_BATCH];
+  __shared__ int nl;
+  // Everything read before the wait is untouched by the LED kernel this
+  // kernel depends on: step coefficients, LED tables, and O, m, v (the LED
+  // kernel only reads O, and lets this kernel start only after the previous
+  // update has completed). The gradient boxes and partials come after it.
   const float2 bc = a.coef ? a.coef[a.step_off] : make_float2(1.f, 1.f);
-  asm volatile("griddepcontrol.wait;\n" ::: "memory");  // gradients of the LED kernel
   if (blockIdx.x == 0) {  // first block: the scalar parameters (longest dependency chain)
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
     scalar_update(a, bc.x, bc.y);
     return;
   }
   if (!a.assemble && !(a.learn & 1u)) return;
-  __shared__ int lst[MAX_BATCH];
-  __shared__ int nl;
   const int x = a.x_lo + (int)blockIdx.x - 1;
   const int W = a.W;
+  const int2 span = a.span[x];
   for (int kk = threadIdx.x; kk < a.B; kk += blockDim.x) {
-    const int2 n = a.n_int[a.idx[kk]];
-    corner[kk] = make_int2(a.N / 2 + n.y - a.h, a.N / 2 + n.x - a.h);
+    const int4 sl = a.slot[kk];
+    corner[kk] = make_int2(a.N / 2 + sl.z - a.h, a.N / 2 + sl.y - a.h);
+  }
+  // this thread's first element of the column (most columns need one per thread)
+  const int y0 = span.x + (int)threadIdx.x;
+  float2 w0 = make_float2(0.f, 0.f), m0 = w0, v0 = w0;
+  if (!a.assemble && y0 < span.y) {
+    const size_t o = (size_t)x * a.N + y0;
+    w0 = __ldcg(a.Ot + o);  // L2 (not L1): written by the previous update kernel
+    m0 = __ldcg(a.mO + o);
+    v0 = __ldcg(a.vO + o);
   }
   __syncthreads();
   if (threadIdx.x == 0) {  // batch slots whose box covers this column, in batch order
@@ -114,18 +134,20 @@ __global__ void __launch_bounds__(UPD_NT) update_kernel(const UpdArgs a) {
       if ((unsigned)(x - corner[kk].x) < (unsigned)W) lst[c++] = kk;
     nl = c;
   }
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");  // gradient boxes of the LED kernel
   __syncthreads();
-  const int2 span = a.span[x];
   const float lr_bc1 = a.lr_obj * bc.x;
   const float inv_sqrt_bc2 = bc.y;
   const int n_l = nl;
-  for (int y = span.x + threadIdx.x; y < span.y; y += blockDim.x) {
+  for (int y = y0; y < span.y; y += blockDim.x) {
     const size_t o = (size_t)x * a.N + y;
     float2 w, m, v;
-    if (!a.assemble) {  // independent of the gradient: issue first
-      w = a.Ot[o];
-      m = a.mO[o];
-      v = a.vO[o];
+    if (!a.assemble) {
+      if (y == y0) {
+        w = w0; m = m0; v = v0;
+      } else {
+        w = a.Ot[o]; m = a.mO[o]; v = a.vO[o];
+      }
     }
     // sum of the covering boxes in batch order (adding zeros where a box
     // does not reach this row), four loads in flight at a time
@@ -157,6 +179,11 @@ __global__ void __launch_bounds__(UPD_NT) update_kernel(const UpdArgs a) {
     a.mO[o] = m;
     a.vO[o] = v;
   }
+}
+
+cudaError_t update_prepare() {
+  return cudaFuncSetAttribute(update_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                              cudaSharedmemCarveoutMaxShared);
 }
 
 cudaError_t launch_update(const UpdArgs& a, cudaStream_t s, bool pdl) {

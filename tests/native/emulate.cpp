@@ -65,6 +65,12 @@ int main() {
     for (int j = 0; j < 14; ++j) c[j] = 0.3f * (float)std::cos(1.7 * j + 0.4);
     float K[15], Dx[10], Dy[10];
     theta_poly(c, K, Dx, Dy);
+    float dmax = 0.f;  // the per-entry form used by the kernels must agree
+    for (int e = 0; e < 35; ++e) {
+      const float ref = e < 15 ? K[e] : (e < 25 ? Dx[e - 15] : Dy[e - 25]);
+      dmax = std::fmax(dmax, std::fabs(theta_poly_entry(c, e) - ref));
+    }
+    std::printf("polyentry %.9g\n", dmax);
     for (int i = 0; i < 30; ++i) {
       const float x = (float)std::sin(2.3 * i) * 1.05f, y = (float)std::cos(0.37 * i + 1.0) * 1.05f;
       float mo[15];

@@ -82,3 +82,7 @@ def test_monomial_basis_matches_oracle(emulated):
         ref_g = [sum(cj * orc.zernike_grad(j, x, y)[a] for j, cj in zip(range(2, 16), c)) for a in (0, 1)]
         np.testing.assert_allclose([th, gx, gy], [ref_th, *ref_g], rtol=3e-6, atol=3e-6)
         np.testing.assert_allclose(zs, [orc.zernike(j, x, y) for j in range(2, 16)], rtol=3e-6, atol=3e-6)
+
+
+def test_parallel_polynomial_entries_equal_serial(emulated):
+    assert float(emulated["polyentry"][0][0]) <= 1e-6
