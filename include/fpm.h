@@ -87,7 +87,7 @@ typedef struct fpm_handle fpm_handle;
 
 /* Imaging geometry (Section 2.1). */
 typedef struct fpm_geometry {
-  int32_t m;                /* low-res image side: 32, 64, 128 or 256 */
+  int32_t m;                /* low-res image side: 32, 64, 128, 256 or 512 (512 needs 16-CTA thread-block clusters) */
   int32_t n_leds;           /* number of LED images, >= 1 */
   const float* led_offset;  /* [n_leds][2] (row, col) nominal spectral LED centre in px of the
                                spectrum grid, relative to DC; host memory. The rounded value is
@@ -216,7 +216,7 @@ int fpm_epoch_permutation(int32_t n, uint64_t seed, int32_t epoch, int32_t* out)
  * kernels' attributes (once per device, with that device current); make that
  * first call before any stream capture.
  *
- * g, pupil_radius_px, upsample: as fpm_create (the rounded LED offsets give the
+ * g, pupil_radius_px, upsample: as fpm_create, m up to 256 (the rounded LED offsets give the
  *   crop positions; delta comes from `params`).
  * O_t      device [N][N][2] object spectrum, COLUMN-major: element (row y, col x)
  *          at index x * N + y (the transpose of fpm_get's layout).

@@ -304,11 +304,11 @@ FPM_HD int pidx(int i) { return i + (i >> 3); }
 // their access pattern one pad point every 16 makes every pass conflict-free.
 FPM_HD int pidx16(int i) { return i + (i >> 4); }
 template <int M>
-FPM_HD int bidx(int i) { return M == 256 ? pidx16(i) : pidx(i); }
+FPM_HD int bidx(int i) { return M >= 256 ? pidx16(i) : pidx(i); }
 template <int M>
 struct FftBuf {
-  static constexpr int SIZE = M == 256 ? M + M / 16 : M + M / 8;   // padded length of one buffer
-  static constexpr int G = M == 256 ? 16 : M / 8;                   // threads per transform
+  static constexpr int SIZE = M >= 256 ? M + M / 16 : M + M / 8;   // padded length of one buffer
+  static constexpr int G = M == 256 ? 16 : (M == 512 ? 32 : M / 8);  // threads per transform
 };
 
 // Per-thread twiddles: thread j of a group only ever needs W_{R Ns}^{r k}
@@ -463,6 +463,77 @@ __device__ __forceinline__ void fft256_group(float2* __restrict__ buf, const flo
   }
 }
 #endif
+
+// ---- 512 points: radix 16, radix 16, radix 2 (32 threads x 16 points) ----
+// Second-pass twiddles depend on k = j mod 16 only: tw2[(r-1) * 16 + k] =
+// W256^(r k) = tw[2 r k] of the 512-point table.
+FPM_HD void fft512_twiddles(const float2* tw, float2* tw2, int k) {
+  for (int r = 1; r < 16; ++r) tw2[(r - 1) * 16 + k] = tw[2 * r * k];
+}
+
+template <int DIR>
+FPM_HD void r16x512_load(const float2* buf, const float2* tw2, int j, int pass, float2 (&v)[16]) {
+  for (int r = 0; r < 16; ++r) v[r] = buf[pidx16(j + 32 * r)];
+  if (pass == 1)
+    for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw_dir<DIR>(tw2[(r - 1) * 16 + (j & 15)]));
+  dft16<DIR>(v);
+}
+FPM_HD void r16x512_store(float2* buf, int j, int pass, const float2 (&v)[16]) {
+  const int Ns = pass == 0 ? 1 : 16;
+  const int k = j & (Ns - 1);
+  const int base = (j - k) * 16 + k;
+  for (int r = 0; r < 16; ++r) buf[pidx16(base + r * Ns)] = v[r];
+}
+// final radix-2 pass (Ns = 256): butterflies jj = j + 32 b, twiddle W512^jj
+template <int DIR>
+FPM_HD void r2x512_load(const float2* buf, const float2* tw, int j, float2 (&v)[16]) {
+  for (int b = 0; b < 8; ++b) {
+    const int jj = j + 32 * b;
+    v[2 * b] = buf[pidx16(jj)];
+    v[2 * b + 1] = cmul(buf[pidx16(jj + 256)], tw_dir<DIR>(tw[jj]));
+    dft2<DIR>(v[2 * b], v[2 * b + 1]);
+  }
+}
+FPM_HD void r2x512_store(float2* buf, int j, const float2 (&v)[16]) {
+  for (int b = 0; b < 8; ++b) {
+    const int jj = j + 32 * b;
+    buf[pidx16(jj)] = v[2 * b];
+    buf[pidx16(jj + 256)] = v[2 * b + 1];
+  }
+}
+
+#if defined(__CUDACC__)
+// 512-point transform by one warp; tw: 512-point table, tw2: second-pass twiddles.
+template <int DIR>
+__device__ __forceinline__ void fft512_group(float2* __restrict__ buf, const float2* __restrict__ tw,
+                                             const float2* __restrict__ tw2, int j) {
+  float2 v[16];
+#pragma unroll
+  for (int pass = 0; pass < 2; ++pass) {
+    r16x512_load<DIR>(buf, tw2, j, pass, v);
+    __syncwarp();
+    r16x512_store(buf, j, pass, v);
+    __syncwarp();
+  }
+  r2x512_load<DIR>(buf, tw, j, v);
+  __syncwarp();
+  r2x512_store(buf, j, v);
+  __syncwarp();
+}
+#endif
+
+template <int DIR>
+inline void fft512_emulate(float2* buf, const float2* tw) {
+  float2 tw2[15 * 16];
+  for (int k = 0; k < 16; ++k) fft512_twiddles(tw, tw2, k);
+  float2 V[32][16];
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int j = 0; j < 32; ++j) r16x512_load<DIR>(buf, tw2, j, pass, V[j]);
+    for (int j = 0; j < 32; ++j) r16x512_store(buf, j, pass, V[j]);
+  }
+  for (int j = 0; j < 32; ++j) r2x512_load<DIR>(buf, tw, j, V[j]);
+  for (int j = 0; j < 32; ++j) r2x512_store(buf, j, V[j]);
+}
 
 template <int DIR>
 inline void fft256_emulate(float2* buf, const float2* tw) {

@@ -359,7 +359,7 @@ int fpm_create(const fpm_geometry* g, float R, int32_t upsample, void* cuda_stre
   g_create_error.clear();
   if (!g || !out || !g->led_offset) return fail(nullptr, FPM_ERR_ARG, "null argument");
   *out = nullptr;
-  if (led_cluster_size(g->m) == 0) return fail(nullptr, FPM_ERR_SHAPE, "m=%d not in {32, 64, 128, 256}", g->m);
+  if (led_cluster_size(g->m) == 0) return fail(nullptr, FPM_ERR_SHAPE, "m=%d not in {32, 64, 128, 256, 512}", g->m);
   if (upsample < 1 || (long long)g->m * upsample > 8192 || (upsample & (upsample - 1)))
     return fail(nullptr, FPM_ERR_SHAPE, "upsample=%d must be a power of two with m*upsample <= 8192", upsample);
   if (g->n_leds < 1 || g->n_leds > 1024) return fail(nullptr, FPM_ERR_SHAPE, "n_leds=%d outside [1, 1024]", g->n_leds);
@@ -459,7 +459,9 @@ int fpm_create(const fpm_geometry* g, float R, int32_t upsample, void* cuda_stre
             ck(cudaMalloc(&h->epoch, sizeof(double)), "alloc") &&
             ck(cudaMalloc(&h->err, sizeof(int)), "alloc") &&
             ck(cudaMallocHost(&h->h_err, sizeof(int)), "pinned") &&
-            ck(led_prepare(h->m, (h->C = led_choose_cluster(h->m, h->W)), h->W), "kernel attributes") &&
+            ck((h->C = led_choose_cluster(h->m, h->W)) > 0 ? cudaSuccess : cudaErrorNotSupported,
+               "this device cannot run the per-LED kernel for this size") &&
+            ck(led_prepare(h->m, h->C, h->W), "kernel attributes") &&
             ck(update_prepare(), "kernel attributes");
   if (ok) {
     const auto twm = twiddles(h->m), twN = twiddles(h->N);

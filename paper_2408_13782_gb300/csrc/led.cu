@@ -31,6 +31,7 @@ template <> struct LedCfg<32> { static constexpr int NT = 64; };
 template <> struct LedCfg<64> { static constexpr int NT = 128; };
 template <> struct LedCfg<128> { static constexpr int NT = 256; };
 template <> struct LedCfg<256> { static constexpr int NT = 256; };
+template <> struct LedCfg<512> { static constexpr int NT = 256; };
 
 // per-thread accumulators: loss, gamma, 15 monomial moments, defocus, delta_y, delta_x
 constexpr int NACC = 20;
@@ -46,7 +47,7 @@ struct LedLayout {
   static constexpr int FS = FftBuf<M>::SIZE;       // padded per-group buffer (stride = 8 mod 16 when G = 8)
   static constexpr int NW = NT / 32;
   static constexpr int NPOLY = 40;                 // K[15], Dx[10], Dy[10], pad
-  static constexpr int NTW2 = M == 256 ? 15 * 16 : 0;  // per-thread second-pass twiddles (M = 256)
+  static constexpr int NTW2 = M >= 256 ? 15 * 16 : 0;  // second-pass twiddles (M = 256, 512)
   static size_t bytes(int W) {
     const int chunk = (W + C - 1) / C;
     return sizeof(float) * (size_t)ROWS * M +
@@ -80,14 +81,15 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\
 
 // In-place transform of one padded buffer by its thread group.
 template <int M, int DIR>
-__device__ __forceinline__ void transform(float2* buf, const FftTw<M == 256 ? 128 : M>& TW, const float2* tw2,
-                                          int j) {
+__device__ __forceinline__ void transform(float2* buf, const FftTw<(M >= 256) ? 128 : M>& TW, const float2* tws,
+                                          const float2* tw2, int j) {
   if constexpr (M == 256) fft256_group<DIR>(buf, tw2, j);
+  else if constexpr (M == 512) fft512_group<DIR>(buf, tws, tw2, j);
   else fft_group<M, DIR>(buf, TW, j);
 }
 
 template <int M, int C>
-__global__ void __launch_bounds__(LedCfg<M>::NT, 2) led_kernel(const LedArgs a) {
+__global__ void __launch_bounds__(LedCfg<M>::NT, M == 512 ? 1 : 2) led_kernel(const LedArgs a) {
   using L = LedLayout<M, C>;
   constexpr int NT = L::NT, G = L::G, NG = L::NG, ROWS = L::ROWS, TS = L::TS, FS = L::FS;
   constexpr int NW = L::NW;
@@ -161,10 +163,12 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, 2) led_kernel(const LedArgs a) 
   if (tid < 14) red[tid] = zc;   // the aberration coefficients, via the (still unused) reduction area
   __syncthreads();
   if (tid < 35) poly[tid] = theta_poly_entry_tab(red, zmt, tid);  // aberration phase as monomials of q/R
-  FftTw<M == 256 ? 128 : M> TW;  // radix-8 path: per-thread twiddles in registers
+  FftTw<(M >= 256) ? 128 : M> TW;  // radix-8 path: per-thread twiddles in registers
   __syncthreads();                // twiddle table
   if constexpr (M == 256) {
     if (tid < 16) fft256_twiddles(tws, tw2, tid);
+  } else if constexpr (M == 512) {
+    if (tid < 16) fft512_twiddles(tws, tw2, tid);
   } else {
     fft_twiddles<M>(tws, j, TW);
   }
@@ -188,7 +192,7 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, 2) led_kernel(const LedArgs a) 
       buf[bidx<M>(ky & (M - 1))] = v;
     }
     __syncwarp();
-    transform<M, +1>(buf, TW, tw2, j);
+    transform<M, +1>(buf, TW, tws, tw2, j);
     if (act)
       for (int t = j; t < M; t += G) T[(c - c0) * TS + t] = buf[bidx<M>(t)];
     __syncwarp();
@@ -212,7 +216,7 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, 2) led_kernel(const LedArgs a) 
       buf[bidx<M>((c - h) & (M - 1))] = v;
     }
     __syncwarp();
-    transform<M, +1>(buf, TW, tw2, j);
+    transform<M, +1>(buf, TW, tws, tw2, j);
     for (int t = j; t < M; t += G) {
       const float2 psi = cscale(buf[bidx<M>(t)], inv_m2);
       const float mag2 = psi.x * psi.x + psi.y * psi.y;
@@ -245,7 +249,7 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, 2) led_kernel(const LedArgs a) 
     }
     __syncwarp();
     if (a.mode != MODE_FORWARD) {
-      transform<M, -1>(buf, TW, tw2, j);
+      transform<M, -1>(buf, TW, tws, tw2, j);
       if (act)
         for (int c = j; c < W; c += G) {
           const int kx = c - h, own = c / chunk, lc = c - own * chunk;
@@ -269,7 +273,7 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, 2) led_kernel(const LedArgs a) 
     const bool act = c < c1;
     for (int t = j; t < M; t += G) buf[bidx<M>(t)] = act ? T[(c - c0) * TS + t] : make_float2(0.f, 0.f);
     __syncwarp();
-    transform<M, -1>(buf, TW, tw2, j);
+    transform<M, -1>(buf, TW, tws, tw2, j);
     if (act) {
       const float2* Oc = Ob + (size_t)(c - c0) * W + h;
       const float qx = (float)(c - h) - dlx;
@@ -361,12 +365,14 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, 2) led_kernel(const LedArgs a) 
   }
 }
 
+// Cluster sizes built for each low-res size (CTAs cooperating on one LED).
 int led_cluster_size(int m) {
   switch (m) {
     case 32: return 2;
     case 64: return 4;
     case 128: return 8;
-    case 256: return 16;
+    case 256: return 8;
+    case 512: return 16;
   }
   return 0;
 }
@@ -377,29 +383,40 @@ static const void* kernel_ptr() { return (const void*)led_kernel<M, C>; }
 template <int M, int C>
 static cudaError_t prepare_t(int W);
 
-// A 16-CTA cluster (a non-portable size) is used for m = 256 only when the
-// device can hold 16 of them at once (a whole 16-LED batch in one wave);
-// otherwise 8.
-int led_choose_cluster(int m, int W) {
-  if (m != 256) return led_cluster_size(m);
-  const void* k16 = kernel_ptr<256, 16>();
-  if (prepare_t<256, 16>(W) != cudaSuccess) {  // non-portable size + shared-memory limit
-    cudaGetLastError();
-    return 8;
-  }
+template <int M, int C>
+static int max_active_clusters(int W) {
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(16, 1, 1);
-  cfg.blockDim = dim3(LedCfg<256>::NT, 1, 1);
-  cfg.dynamicSmemBytes = LedLayout<256, 16>::bytes(W);
+  cfg.gridDim = dim3(C, 1, 1);
+  cfg.blockDim = dim3(LedCfg<M>::NT, 1, 1);
+  cfg.dynamicSmemBytes = LedLayout<M, C>::bytes(W);
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 16;
+  attr[0].val.clusterDim.x = C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, k16, &cfg) != cudaSuccess || n < 16) {
+  if (cudaOccupancyMaxActiveClusters(&n, kernel_ptr<M, C>(), &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+// m = 256: a 16-CTA cluster (a non-portable size) only when the device can
+// hold 16 of them at once (a whole 16-LED batch in one wave), else 8.
+// m = 512 needs 16 (shared memory per CTA); 0 if the device cannot run it.
+int led_choose_cluster(int m, int W) {
+  if (m == 512) {
+    if (prepare_t<512, 16>(W) != cudaSuccess || max_active_clusters<512, 16>(W) < 1) {
+      cudaGetLastError();
+      return 0;
+    }
+    return 16;
+  }
+  if (m != 256) return led_cluster_size(m);
+  if (prepare_t<256, 16>(W) != cudaSuccess || max_active_clusters<256, 16>(W) < 16) {
     cudaGetLastError();
     return 8;  // a 16-LED batch of 16-CTA clusters would need a second wave
   }
@@ -411,6 +428,7 @@ size_t led_smem_bytes(int m, int C, int W) {
   if (m == 64) return LedLayout<64, 4>::bytes(W);
   if (m == 128) return LedLayout<128, 8>::bytes(W);
   if (m == 256) return C == 16 ? LedLayout<256, 16>::bytes(W) : LedLayout<256, 8>::bytes(W);
+  if (m == 512) return LedLayout<512, 16>::bytes(W);
   return 0;
 }
 
@@ -440,6 +458,7 @@ cudaError_t led_prepare(int m, int C, int W) {
   if (m == 64) return prepare_t<64, 4>(W);
   if (m == 128) return prepare_t<128, 8>(W);
   if (m == 256) return C == 16 ? prepare_t<256, 16>(W) : prepare_t<256, 8>(W);
+  if (m == 512 && C == 16) return prepare_t<512, 16>(W);
   return cudaErrorInvalidValue;
 }
 
@@ -468,6 +487,7 @@ cudaError_t launch_led(int m, int C, const LedArgs& a, cudaStream_t s, bool pdl)
   if (m == 64) return launch_t<64, 4>(a, s, pdl);
   if (m == 128) return launch_t<128, 8>(a, s, pdl);
   if (m == 256) return C == 16 ? launch_t<256, 16>(a, s, pdl) : launch_t<256, 8>(a, s, pdl);
+  if (m == 512 && C == 16) return launch_t<512, 16>(a, s, pdl);
   return cudaErrorInvalidValue;
 }
 

@@ -95,7 +95,8 @@ extern "C" int fpm_gradients_static(const fpm_geometry* g, float R, int32_t upsa
   if (!g || !g->led_offset || !O_t || !params || !stack || !idx || !g_object_t || !g_params || !loss_out)
     return fail_static(FPM_ERR_ARG, "null argument");
   const int m = g->m, n = g->n_leds;
-  if (led_cluster_size(m) == 0) return fail_static(FPM_ERR_SHAPE, "m not in {32, 64, 128, 256}");
+  if (led_cluster_size(m) == 0 || m == 512)
+    return fail_static(FPM_ERR_SHAPE, "m not in {32, 64, 128, 256}");
   if (upsample < 1 || (long long)m * upsample > 8192 || (upsample & (upsample - 1)))
     return fail_static(FPM_ERR_SHAPE, "upsample must be a power of two with m * upsample <= 8192");
   if (n < 1 || n > 1024) return fail_static(FPM_ERR_SHAPE, "n_leds outside [1, 1024]");

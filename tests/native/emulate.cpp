@@ -27,8 +27,8 @@ static void run_fft() {
   }
 }
 
-static void run_fft256() {
-  const int M = 256;
+template <int M>
+static void run_fft_big() {
   std::vector<float2> tw(M), buf(M + M / 16);
   for (int t = 0; t < M; ++t) {
     const double a = -2.0 * M_PI * t / M;
@@ -37,8 +37,13 @@ static void run_fft256() {
   for (int dir = -1; dir <= 1; dir += 2) {
     for (int t = 0; t < M; ++t)
       buf[pidx16(t)] = make_float2((float)std::sin(0.37 * t + 0.1 * M), (float)std::cos(0.91 * t) - 0.25f);
-    if (dir < 0) fft256_emulate<-1>(buf.data(), tw.data());
-    else fft256_emulate<+1>(buf.data(), tw.data());
+    if (M == 256) {
+      if (dir < 0) fft256_emulate<-1>(buf.data(), tw.data());
+      else fft256_emulate<+1>(buf.data(), tw.data());
+    } else {
+      if (dir < 0) fft512_emulate<-1>(buf.data(), tw.data());
+      else fft512_emulate<+1>(buf.data(), tw.data());
+    }
     std::printf("fft %d %d", M, dir);
     for (int t = 0; t < M; ++t) std::printf(" %.9g %.9g", buf[pidx16(t)].x, buf[pidx16(t)].y);
     std::printf("\n");
@@ -46,7 +51,8 @@ static void run_fft256() {
 }
 
 int main() {
-  run_fft256();
+  run_fft_big<256>();
+  run_fft_big<512>();
   run_fft<16>();
   run_fft<32>();
   run_fft<64>();

@@ -35,7 +35,7 @@ def _grad_errors(tag, eng_g, ref_g, idx, n_leds):
 # forward model
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("m,edge", [(32, "aa"), (64, "hard"), (64, "aa"), (128, "aa"), (256, "aa")])
+@pytest.mark.parametrize("m,edge", [(32, "aa"), (64, "hard"), (64, "aa"), (128, "aa"), (256, "aa"), (512, "aa")])
 def test_forward_multiparam(m, edge):
     c, I, g, prm, O = multiparam_problem(m=m, edge=edge, grid=5 if m < 256 else 3)
     eng = engine_for(g)
@@ -65,14 +65,15 @@ def test_forward_config1_literal():
 # gradients (built-in loss and upstream dL/dI)
 # --------------------------------------------------------------------------
 
-@pytest.mark.parametrize("m,loss", [(64, "amplitude"), (64, "intensity"), (128, "amplitude"), (32, "amplitude")])
+@pytest.mark.parametrize("m,loss", [(64, "amplitude"), (64, "intensity"), (128, "amplitude"), (32, "amplitude"),
+                                    (512, "amplitude")])
 def test_gradients_builtin_loss(m, loss):
-    c, I, g, prm, O = multiparam_problem(m=m)
+    c, I, g, prm, O = multiparam_problem(m=m, grid=5 if m < 512 else 3)
     eng = engine_for(g)
     eng.set_hparams(loss=loss)
     eng.load(I, init=False)
     push(eng, O, prm)
-    idx = [3, 0, 11, 7][: min(4, g.n_leds)]
+    idx = [i for i in (3, 0, 11, 7) if i < g.n_leds]
     got = eng.backward(idx)
     L, ref, _ = orc.loss_and_grad(O, prm, g, idx, I.astype(np.float64), loss)
     record(f"grad.m{m}.{loss}.loss", abs(got["loss"] - L) / L)
