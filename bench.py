@@ -237,6 +237,62 @@ def run_cpu_child(stack, sample_s: float, leds_per_step: int, max_steps: int):
 
 
 # --------------------------------------------------------------------------
+# serving: continuous batching of uneven reconstructions vs the same jobs serially
+# --------------------------------------------------------------------------
+
+def serving_jobs(n_jobs: int, rate_hz: float, seed: int):
+    """Seeded Poisson arrivals; ROI from {256, 512, 1024, 2048}^2 at upsample 4, grids
+    {7, 11, 15}^2, the 64-px recipe (hard pupil, aberration-free, noise-free) per job."""
+    from paper_2408_13782_gb300 import Engine
+    from paper_2408_13782_gb300 import serve as sv
+    from synth import recipes as S
+    rng = np.random.default_rng([seed, 40])
+    t = np.cumsum(rng.exponential(1.0 / rate_hz, n_jobs))
+    jobs = []
+    for k in range(n_jobs):
+        N = int(rng.choice([256, 512, 1024, 2048]))
+        grid = int(rng.choice([7, 11, 15]))
+        c = S.serving_job_config(N, grid, seed * 1000 + k)
+        nominal, truth = S.led_grid(c.grid, c.pitch, c.jitter, c.seed)
+        eng = Engine(c.m, c.s, truth, c.R, c.lambda_um, c.dk_per_um, c.edge)
+        eng.set_object_field(S.make_object(c.N, c.seed))
+        stack = np.concatenate([eng.forward(np.arange(i, min(i + 64, c.n_leds))) for i in range(0, c.n_leds, 64)])
+        eng.close()
+        desc = sv.job_desc(c.m, c.s, nominal, c.R, c.lambda_um, c.dk_per_um, c.edge, batch=c.B,
+                           max_epochs=c.epochs, rel_tol=1e-4, seed=c.seed, lr=dict(c.lr))
+        jobs.append((desc, stack, float(t[k]), N, grid))
+    return jobs
+
+
+def serving_run(jobs, budget: int, max_active: int):
+    from paper_2408_13782_gb300 import serve as sv
+    srv = sv.Server(budget, max_active)
+    ids, st, wall = sv.run_arrivals(srv, [(d, s, t) for d, s, t, _, _ in jobs])
+    srv.close()
+    ttc = np.array([x["t_done"] - x["t_submit"] for x in st])
+    upd = sum(x["led_updates"] for x in st)
+    span = max(x["t_done"] for x in st) - min(x["t_submit"] for x in st)
+    return {"p50_ttc_s": float(np.percentile(ttc, 50)), "p99_ttc_s": float(np.percentile(ttc, 99)),
+            "led_updates_per_s": upd / span, "jobs_done": int(sum(x["state"] == sv.JOB_DONE for x in st)),
+            "epochs": [int(x["epochs"]) for x in st], "makespan_s": span}
+
+
+def serving_section(n_jobs=16, rate_hz=40.0, seed=5):
+    import torch
+    jobs = serving_jobs(n_jobs, rate_hz, seed)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.6 * free)
+    run_serving = serving_run(jobs, budget, max_active=64)
+    run_serial = serving_run(jobs, budget, max_active=1)
+    return {"what": f"{n_jobs} jobs, Poisson arrivals {rate_hz:g}/s, ROI from {{256,512,1024,2048}}^2 at "
+                    "upsample 4, LED grids {7,11,15}^2, stop at relative epoch-loss change < 1e-4 or 40 epochs; "
+                    "continuous batching (jobs admitted by device-memory footprint, overlapping) vs the same "
+                    "jobs one at a time (FCFS) on the same GPU",
+            "mix": [f"{N}^2/{g}x{g}" for _, _, _, N, g in jobs],
+            "hbm_budget_bytes": budget, "continuous": run_serving, "serial": run_serial}
+
+
+# --------------------------------------------------------------------------
 # distributed helpers (torchrun: one rank per GPU, independent jobs)
 # --------------------------------------------------------------------------
 
@@ -370,6 +426,8 @@ def engine_arm(args):
                              "initialisation, the steps, per-step losses and the final state read back"}
     assert np.all(np.isfinite(losses)) and np.isfinite(out["object"]).all()
 
+    if rank == 0 and world == 1 and not args.no_serving:
+        result["serving"] = serving_section()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = run_cpu_child(stack, args.cpu_sample_s, B, 10_000)
         result["cpu_baseline"] = {"value": r["updates"] / r["seconds"], "unit": UNIT, "cores": 1,
@@ -425,10 +483,11 @@ def reference_arm(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("engine", "reference"), default="engine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--cpu-worker", default=None)
     ap.add_argument("--cpu-leds", type=int, default=16)

@@ -236,6 +236,64 @@ int fpm_gradients_static(const fpm_geometry* g, float pupil_radius_px, int32_t u
                          const int32_t* idx, int32_t B, int32_t loss,
                          float* g_object_t, float* g_params, double* loss_out, void* cuda_stream);
 
+/* ---- Serving: continuous batching of reconstruction jobs -----------------
+ * A request loop for many reconstructions of uneven size. Submitted jobs are
+ * queued and admitted in arrival order, each as soon as its device-memory
+ * footprint fits the rest of the server's budget and a slot is free (first fit;
+ * a job too large for now does not hold back smaller ones) (the paper picks the
+ * batch size from the available GPU memory, Section 2.2; here memory decides
+ * which jobs are resident). An admitted job keeps its object spectrum, pupil,
+ * defocus, LED parameters and Adam state resident on the device and runs on
+ * its own stream, so the epochs of all admitted jobs overlap on the GPU. Each
+ * epoch is a fresh random batch order (Eq. 13-14, seed = job seed) as at most
+ * two graph launches. A job stops when the relative change of its epoch loss
+ * drops below rel_tol, or after max_epochs; its result is then copied to host
+ * memory and its device memory freed for the next admissions.
+ * All server calls are made from one host thread. */
+typedef struct fpm_server fpm_server;
+
+typedef struct fpm_job_desc {
+  fpm_geometry geometry;     /* led_offset is copied at submit */
+  float pupil_radius_px;
+  int32_t upsample;
+  fpm_hparams hparams;
+  int32_t batch;             /* B, in [1, n_leds] */
+  int32_t max_epochs;
+  double rel_tol;            /* stop when |L_e - L_{e-1}| < rel_tol * L_{e-1} */
+  uint64_t seed;             /* batch order seed */
+} fpm_job_desc;
+
+#define FPM_JOB_QUEUED 0
+#define FPM_JOB_ACTIVE 1
+#define FPM_JOB_DONE   2
+#define FPM_JOB_FAILED 3
+
+typedef struct fpm_job_status {
+  int32_t state;             /* FPM_JOB_* */
+  int32_t epochs;            /* completed */
+  double loss;               /* last epoch loss */
+  double t_submit, t_admit, t_done;  /* seconds on the server clock */
+  int64_t led_updates;       /* LED images processed (forward + backward) */
+  int64_t footprint;         /* device bytes reserved while resident */
+} fpm_job_status;
+
+/* Device bytes a job holds while resident (its admission size). */
+int64_t fpm_job_footprint(const fpm_job_desc* d);
+int fpm_server_create(int64_t hbm_budget_bytes, int32_t max_active, fpm_server** out);
+/* Queue a job; stack is host [n_leds][m][m] intensities, copied. FPM_ERR_OOM if
+ * its footprint exceeds the whole budget. */
+int fpm_server_submit(fpm_server* s, const fpm_job_desc* d, const float* stack, int64_t* job_id);
+/* Make progress without blocking: retire finished epochs, stop converged jobs,
+ * admit queued ones. Outputs (nullable): jobs resident, jobs waiting. */
+int fpm_server_tick(fpm_server* s, int32_t* n_active, int32_t* n_queued);
+int fpm_server_status(const fpm_server* s, int64_t job_id, fpm_job_status* st);
+/* Result of a finished job (host buffers, each nullable; layouts as fpm_get). */
+int fpm_server_result(fpm_server* s, int64_t job_id, float* O, float* zernike, float* defocus,
+                      float* gamma, float* offset);
+double fpm_server_clock(const fpm_server* s);      /* seconds since fpm_server_create */
+const char* fpm_server_error(const fpm_server* s);
+void fpm_server_destroy(fpm_server* s);
+
 void fpm_destroy(fpm_handle* h);
 
 /* Last error message of the handle (or, when h is NULL, of the last failed

@@ -40,7 +40,7 @@ struct fpm_handle {
   std::vector<float> sp0;  // initial scalar parameters
   int x_lo = 0, n_cols = 0;
   cudaStream_t user = nullptr, st = nullptr;
-  cudaEvent_t ev_in = nullptr, ev_out = nullptr, ev_stage = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   fpm_hparams hp{};
   // device state
   float2 *Ot = nullptr, *mO = nullptr, *vO = nullptr, *tmp = nullptr, *tmp2 = nullptr;
@@ -59,15 +59,21 @@ struct fpm_handle {
   float2* coef = nullptr;  // per-step Adam bias corrections of the current run
   int cap_coef = 0;
   int* err = nullptr;
-  // pinned staging
-  int4* h_sched = nullptr;
-  int cap_h_sched = 0;
-  float2* h_coef = nullptr;
-  int cap_h_coef = 0;
+  // pinned staging of handle-free copies
   int* h_err = nullptr;
   long long t_host = 0;
   bool loaded = false;
-  std::map<std::pair<int, int>, cudaGraphExec_t> graphs;
+  // One captured graph per (n_steps, B), each with its own pinned staging for
+  // the batch slots and Adam coefficients its first nodes copy, and an event
+  // marking the end of its last launch: different graphs of a handle can be
+  // queued back to back without waiting on the host.
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    int4* h_slots = nullptr;
+    float2* h_coef = nullptr;
+    cudaEvent_t done = nullptr;
+  };
+  std::map<std::pair<int, int>, Graph> graphs;
   std::string msg;
 };
 
@@ -110,20 +116,27 @@ bool is_pageable_host(const void* p) {
   return at.type == cudaMemoryTypeUnregistered;
 }
 
-void free_all(fpm_handle* h) {
-  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+void destroy_graphs(fpm_handle* h) {
+  for (auto& kv : h->graphs) {
+    if (kv.second.done) cudaEventSynchronize(kv.second.done);
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (kv.second.h_slots) cudaFreeHost(kv.second.h_slots);
+    if (kv.second.h_coef) cudaFreeHost(kv.second.h_coef);
+    if (kv.second.done) cudaEventDestroy(kv.second.done);
+  }
   h->graphs.clear();
+}
+
+void free_all(fpm_handle* h) {
+  destroy_graphs(h);
   void* dev[] = {h->Ot, h->mO, h->vO, h->tmp, h->tmp2, h->tw_m, h->tw_N, h->meas, h->sp, h->msp, h->vsp,
                  h->gsc, h->fbuf, h->nint, h->span, h->gbox, h->part, h->sched, h->losses, h->epoch,
                  h->coef, h->err};
   for (void* p : dev)
     if (p) cudaFree(p);
-  if (h->h_sched) cudaFreeHost(h->h_sched);
-  if (h->h_coef) cudaFreeHost(h->h_coef);
   if (h->h_err) cudaFreeHost(h->h_err);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
-  if (h->ev_stage) cudaEventDestroy(h->ev_stage);
   if (h->st) cudaStreamDestroy(h->st);
 }
 
@@ -184,8 +197,7 @@ int grow(fpm_handle* h, T** p, int* cap, int need) {
   *cap = 0;
   CK(h, cudaMalloc((void**)p, sizeof(T) * (size_t)need));
   *cap = need;
-  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);  // graphs hold the old address
-  h->graphs.clear();
+  destroy_graphs(h);  // graphs hold the old address
   return FPM_OK;
 }
 
@@ -209,8 +221,7 @@ int ensure_batch(fpm_handle* h, int B) {
   CK(h, cudaMalloc(&h->gbox, sizeof(float2) * (size_t)B * h->W * h->W));
   CK(h, cudaMalloc(&h->part, sizeof(double) * (size_t)B * h->C * NPART));
   h->capB = B;
-  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
-  h->graphs.clear();
+  destroy_graphs(h);
   return FPM_OK;
 }
 
@@ -325,13 +336,16 @@ int copy_out(fpm_handle* h, void* dst, const void* src, size_t bytes, bool* host
   return FPM_OK;
 }
 
-int build_graph(fpm_handle* h, int n_steps, int B, cudaGraphExec_t* out) {
+int build_graph(fpm_handle* h, int n_steps, int B, fpm_handle::Graph* gr) {
+  CK(h, cudaMallocHost(&gr->h_slots, sizeof(int4) * (size_t)n_steps * B));
+  CK(h, cudaMallocHost(&gr->h_coef, sizeof(float2) * (size_t)n_steps));
+  CK(h, cudaEventCreateWithFlags(&gr->done, cudaEventDisableTiming));
   cudaGraph_t g = nullptr;
   CK(h, cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = cudaMemcpyAsync(h->sched, h->h_sched, sizeof(int4) * (size_t)n_steps * B,
+  cudaError_t e = cudaMemcpyAsync(h->sched, gr->h_slots, sizeof(int4) * (size_t)n_steps * B,
                                   cudaMemcpyHostToDevice, h->st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h->coef, h->h_coef, sizeof(float2) * n_steps, cudaMemcpyHostToDevice, h->st);
+    e = cudaMemcpyAsync(h->coef, gr->h_coef, sizeof(float2) * n_steps, cudaMemcpyHostToDevice, h->st);
   // kernels after the first may start early (programmatic dependent launch)
   // and wait in-kernel for their predecessor's results
   for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
@@ -345,13 +359,20 @@ int build_graph(fpm_handle* h, int n_steps, int B, cudaGraphExec_t* out) {
     return fail(h, FPM_ERR_CUDA, "graph capture failed: %s",
                 cudaGetErrorString(e != cudaSuccess ? e : e2));
   }
-  e = cudaGraphInstantiate(out, g, 0);
+  e = cudaGraphInstantiate(&gr->exec, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return fail(h, FPM_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
   return FPM_OK;
 }
 
 }  // namespace
+
+int fpmk::engine_snapshot_loss(fpm_handle* h, double* pinned) {
+  int rc = enter(h);
+  if (rc) return rc;
+  CK(h, cudaMemcpyAsync(pinned, h->epoch, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  return leave(h);
+}
 
 extern "C" {
 
@@ -441,7 +462,6 @@ int fpm_create(const fpm_geometry* g, float R, int32_t upsample, void* cuda_stre
   bool ok = ck(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking), "stream") &&
             ck(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming), "event") &&
             ck(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming), "event") &&
-            ck(cudaEventCreateWithFlags(&h->ev_stage, cudaEventDisableTiming), "event") &&
             ck(cudaMalloc(&h->Ot, sizeof(float2) * NN), "alloc O") &&
             ck(cudaMalloc(&h->mO, sizeof(float2) * NN), "alloc m") &&
             ck(cudaMalloc(&h->vO, sizeof(float2) * NN), "alloc v") &&
@@ -504,10 +524,7 @@ int fpm_set_hparams(fpm_handle* h, const fpm_hparams* hp) {
   if (!lr_ok) return fail(h, FPM_ERR_ARG, "non-finite learning rate");
   const bool graph_relevant = hp->loss != h->hp.loss || std::memcmp(hp, &h->hp, sizeof *hp) != 0;
   h->hp = *hp;
-  if (graph_relevant) {  // the captured kernels hold the hyper-parameters by value
-    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
-    h->graphs.clear();
-  }
+  if (graph_relevant) destroy_graphs(h);  // the captured kernels hold the hyper-parameters by value
   return FPM_OK;
 }
 
@@ -551,38 +568,28 @@ int fpm_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int32_t B, 
   if ((rc = grow(h, &h->sched, &h->cap_sched, n_steps * B))) return rc;
   if ((rc = grow(h, &h->losses, &h->cap_losses, n_steps))) return rc;
   if ((rc = grow(h, &h->coef, &h->cap_coef, n_steps))) return rc;
-  // the previous run's graph may still be reading the staging buffers
-  CK(h, cudaEventSynchronize(h->ev_stage));
-  if (h->cap_h_coef < n_steps) {
-    if (h->h_coef) CK(h, cudaFreeHost(h->h_coef));
-    h->h_coef = nullptr;
-    h->cap_h_coef = 0;
-    CK(h, cudaMallocHost(&h->h_coef, sizeof(float2) * (size_t)n_steps));
-    h->cap_h_coef = n_steps;
-    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
-    h->graphs.clear();
-  }
-  if (h->cap_h_sched < n_steps * B) {
-    if (h->h_sched) CK(h, cudaFreeHost(h->h_sched));
-    h->h_sched = nullptr;
-    h->cap_h_sched = 0;
-    CK(h, cudaMallocHost(&h->h_sched, sizeof(int4) * (size_t)n_steps * B));
-    h->cap_h_sched = n_steps * B;
-    for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
-    h->graphs.clear();
-  }
-  fill_slots(h, schedule, n_steps * B, h->h_sched);
-  fill_coef(h, n_steps, h->h_coef);
   auto key = std::make_pair(n_steps, B);
   auto it = h->graphs.find(key);
   if (it == h->graphs.end()) {
-    cudaGraphExec_t ex;
-    if ((rc = build_graph(h, n_steps, B, &ex))) return rc;
-    it = h->graphs.emplace(key, ex).first;
+    it = h->graphs.emplace(key, fpm_handle::Graph{}).first;
+    if ((rc = build_graph(h, n_steps, B, &it->second))) {
+      fpm_handle::Graph g = it->second;
+      h->graphs.erase(it);
+      if (g.exec) cudaGraphExecDestroy(g.exec);
+      if (g.h_slots) cudaFreeHost(g.h_slots);
+      if (g.h_coef) cudaFreeHost(g.h_coef);
+      if (g.done) cudaEventDestroy(g.done);
+      return rc;
+    }
+  } else {
+    // the previous launch of this graph may still be reading its staging
+    CK(h, cudaEventSynchronize(it->second.done));
   }
+  fill_slots(h, schedule, n_steps * B, it->second.h_slots);
+  fill_coef(h, n_steps, it->second.h_coef);
   if ((rc = enter(h))) return rc;
-  CK(h, cudaGraphLaunch(it->second, h->st));
-  CK(h, cudaEventRecord(h->ev_stage, h->st));
+  CK(h, cudaGraphLaunch(it->second.exec, h->st));
+  CK(h, cudaEventRecord(it->second.done, h->st));
   h->t_host += n_steps;
   if (losses_out) {
     bool host = false;

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+struct fpm_handle;
+
 namespace fpmk {
 
 // Per-CTA partial sums written by the LED kernel (FP64).
@@ -72,6 +74,10 @@ cudaError_t led_prepare(int m, int C, int W);
 // pdl: allow programmatic dependent launch after the previous kernel in the stream.
 cudaError_t launch_led(int m, int C, const LedArgs& a, cudaStream_t s, bool pdl);
 cudaError_t launch_update(const UpdArgs& a, cudaStream_t s, bool pdl);
+
+// Enqueue a copy of the handle's running FP64 loss sum into pinned host
+// memory, ordered after all earlier work of the handle on its caller stream.
+int engine_snapshot_loss(fpm_handle* h, double* pinned);
 
 // Message returned by fpm_last_error(NULL) (calls that have no handle).
 void set_unbound_error(const char* msg);

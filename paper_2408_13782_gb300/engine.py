@@ -29,7 +29,9 @@ LOAD_INIT = 1
 EXPORTS = ("fpm_create", "fpm_set_hparams", "fpm_get_hparams", "fpm_load", "fpm_step", "fpm_run",
            "fpm_epoch_loss", "fpm_profile_run", "fpm_forward", "fpm_backward", "fpm_get", "fpm_set", "fpm_set_object_field",
            "fpm_state_size", "fpm_get_state", "fpm_set_state", "fpm_dims", "fpm_epoch_permutation",
-           "fpm_gradients_static", "fpm_destroy", "fpm_last_error")
+           "fpm_gradients_static", "fpm_job_footprint", "fpm_server_create", "fpm_server_submit",
+           "fpm_server_tick", "fpm_server_status", "fpm_server_result", "fpm_server_clock",
+           "fpm_server_error", "fpm_server_destroy", "fpm_destroy", "fpm_last_error")
 
 
 class FpmError(RuntimeError):

@@ -1,0 +1,77 @@
+"""The continuous-batching server: results alone vs in a mix, agreement with a
+direct engine run, and admission by device-memory footprint."""
+
+import numpy as np
+import pytest
+
+from paper_2408_13782_gb300 import Engine
+from paper_2408_13782_gb300 import serve as sv
+from synth import recipes as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _job(N, grid, seed, max_epochs=6, rel_tol=0.0):
+    """A serving request (the 64-px recipe scaled to N) with a stack simulated by the engine."""
+    c = S.serving_job_config(N, grid, seed)
+    nominal, truth = S.led_grid(c.grid, c.pitch, c.jitter, c.seed)
+    eng = Engine(c.m, c.s, truth, c.R, c.lambda_um, c.dk_per_um, c.edge)
+    eng.set_object_field(S.make_object(c.N, c.seed))
+    stack = eng.forward(np.arange(c.n_leds))
+    eng.close()
+    desc = sv.job_desc(c.m, c.s, nominal, c.R, c.lambda_um, c.dk_per_um, c.edge, batch=c.B,
+                       max_epochs=max_epochs, rel_tol=rel_tol, seed=c.seed, lr=dict(object=0.5))
+    return c, desc, stack
+
+
+def _serve(jobs, budget=8 << 30, max_active=16):
+    srv = sv.Server(budget, max_active)
+    ids, st, wall = sv.run_arrivals(srv, [(d, s, t) for (c, d, s), t in jobs])
+    res = [srv.result(i, c.N, c.n_leds) for i, ((c, d, s), t) in zip(ids, jobs)]
+    srv.close()
+    return st, res
+
+
+def test_result_alone_equals_result_in_a_mix():
+    a = _job(512, 11, 5)
+    others = [_job(256, 7, 6), _job(1024, 7, 7), _job(256, 15, 8)]
+    st_alone, res_alone = _serve([(a, 0.0)])
+    st_mix, res_mix = _serve([(others[0], 0.0), (a, 0.0), (others[1], 0.0), (others[2], 0.002)])
+    assert st_alone[0]["state"] == sv.JOB_DONE and st_mix[1]["state"] == sv.JOB_DONE
+    assert st_alone[0]["epochs"] == st_mix[1]["epochs"] == 6
+    assert np.array_equal(res_alone[0]["object"], res_mix[1]["object"])
+    assert abs(st_alone[0]["loss"] - st_mix[1]["loss"]) <= 1e-12 * abs(st_alone[0]["loss"])
+    # the jobs of the mix overlapped on the device
+    t_admit = [s["t_admit"] for s in st_mix]
+    t_done = [s["t_done"] for s in st_mix]
+    assert max(t_admit) < min(t_done)
+
+
+def test_served_job_equals_a_direct_run():
+    c, desc, stack = _job(256, 11, 9, max_epochs=4)
+    st, res = _serve([((c, desc, stack), 0.0)])
+    nominal = S.led_grid(c.grid, c.pitch, c.jitter, c.seed)[0]
+    eng = Engine(c.m, c.s, nominal, c.R, c.lambda_um, c.dk_per_um, c.edge)
+    eng.set_hparams(lr=dict(object=0.5))
+    eng.load(stack, init=True)
+    for e in range(4):   # the server's epoch: full batches, then the short one
+        perm = S.epoch_permutation(c.n_leds, c.seed, e)
+        nfull = c.n_leds // c.B
+        eng.run(perm[:nfull * c.B].reshape(nfull, c.B))
+        if c.n_leds % c.B:
+            eng.step(perm[nfull * c.B:])
+    assert np.array_equal(eng.get()["object"], res[0]["object"])
+
+
+def test_admission_waits_for_memory():
+    big1, big2 = _job(1024, 11, 10, max_epochs=3), _job(1024, 11, 11, max_epochs=3)
+    small = _job(256, 7, 12, max_epochs=3)
+    fp_big, fp_small = sv.footprint(big1[1]), sv.footprint(small[1])
+    budget = fp_big + fp_small + (fp_big // 2)   # room for one big and one small job
+    st, res = _serve([(big1, 0.0), (big2, 0.0), (small, 0.0)], budget=budget)
+    assert all(s["state"] == sv.JOB_DONE for s in st)
+    assert st[1]["t_admit"] >= st[0]["t_done"]       # the second big job waited for memory
+    assert st[2]["t_admit"] < st[0]["t_done"]        # the small one did not
+    with pytest.raises(Exception):                    # a job larger than the whole budget is refused
+        srv = sv.Server(fp_small, 4)
+        srv.submit(big1[1], big1[2])
