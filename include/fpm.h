@@ -77,6 +77,19 @@ extern "C" {
 #define FPM_LEARN_ALL      0x1Fu
 
 #define FPM_PRECISION_FP32_FFT 0  /* hand-written shared-memory FFTs, FP32 */
+/* The m-point 2-D (inverse) DFTs of the forward model (Section 2.1, Eq. 3) and
+ * their adjoints computed as dense complex contractions with the DFT matrix on
+ * the tensor cores (tcgen05.mma, FP32 accumulation in tensor memory), one CTA
+ * per LED image. Operands rounded to BF16 or TF32; the X3 forms split every
+ * operand into hi + lo parts and sum hi*hi + hi*lo + lo*hi (three products).
+ * Need m in {64, 128, 256} and a crop box of at most 128 px
+ * (2 * (floor(R + 1/2 + sqrt 2) + 1) + 1 <= 128, i.e. R <= 61); fpm_set_hparams
+ * returns FPM_ERR_SHAPE otherwise. Loss, gradients and the Adam step are the
+ * same as in the FFT path; only the transforms' arithmetic differs. */
+#define FPM_PRECISION_BF16_GEMM   1
+#define FPM_PRECISION_BF16X3_GEMM 2
+#define FPM_PRECISION_TF32_GEMM   3
+#define FPM_PRECISION_TF32X3_GEMM 4
 
 #define FPM_LOAD_INIT      1  /* fpm_load flag: initialise O from the centre LED and reset parameters and Adam state */
 
@@ -103,7 +116,7 @@ typedef struct fpm_hparams {
   float beta1, beta2, eps;
   int32_t loss;             /* FPM_LOSS_AMPLITUDE or FPM_LOSS_INTENSITY */
   uint32_t learn_mask;      /* FPM_LEARN_* bits; cleared groups are held fixed */
-  int32_t precision;        /* FPM_PRECISION_FP32_FFT */
+  int32_t precision;        /* FPM_PRECISION_*: FP32 FFTs (default) or a tensor-core DFT form */
 } fpm_hparams;
 
 /* Create an engine for N = m * upsample, pupil radius R (spectral px).

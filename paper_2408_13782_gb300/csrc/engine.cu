@@ -75,6 +75,11 @@ struct fpm_handle {
   };
   std::map<std::pair<int, int>, Graph> graphs;
   std::string msg;
+  // tensor-core DFT form (hp.precision != FPM_PRECISION_FP32_FFT)
+  GemmPlan gp;
+  unsigned char* gconst = nullptr;  // constant DFT factors of gp
+  unsigned char* gscr = nullptr;    // per-slot scratch, capacity cap_gscr slots
+  int cap_gscr = 0;
 };
 
 namespace {
@@ -131,7 +136,7 @@ void free_all(fpm_handle* h) {
   destroy_graphs(h);
   void* dev[] = {h->Ot, h->mO, h->vO, h->tmp, h->tmp2, h->tw_m, h->tw_N, h->meas, h->sp, h->msp, h->vsp,
                  h->gsc, h->fbuf, h->nint, h->span, h->gbox, h->part, h->sched, h->losses, h->epoch,
-                 h->coef, h->err};
+                 h->coef, h->err, h->gconst, h->gscr};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (h->h_err) cudaFreeHost(h->h_err);
@@ -161,6 +166,7 @@ int check_device_error(fpm_handle* h) {
   if (e) {
     CK(h, cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
     if (e & DERR_NONFINITE) return fail(h, FPM_ERR_NONFINITE, "a batch loss was not finite");
+    if (e & DERR_TIMEOUT) return fail(h, FPM_ERR_TIMEOUT, "a bounded wait in a kernel gave up");
     return fail(h, FPM_ERR_RANGE, "a kernel saw an LED index out of range");
   }
   return FPM_OK;
@@ -212,6 +218,14 @@ void fill_coef(const fpm_handle* h, int n_steps, float2* dst) {
 }
 
 int ensure_batch(fpm_handle* h, int B) {
+  if (h->hp.precision != FPM_PRECISION_FP32_FFT && h->cap_gscr < B) {
+    if (h->gscr) CK(h, cudaFree(h->gscr));
+    h->gscr = nullptr;
+    h->cap_gscr = 0;
+    CK(h, cudaMalloc(&h->gscr, h->gp.slot_bytes * (size_t)B));
+    h->cap_gscr = B;
+    destroy_graphs(h);
+  }
   if (h->capB >= B) return FPM_OK;
   if (h->gbox) CK(h, cudaFree(h->gbox));
   if (h->part) CK(h, cudaFree(h->part));
@@ -268,6 +282,12 @@ LedArgs led_args(fpm_handle* h, const int4* slot_dev, int B, int mode) {
   return a;
 }
 
+// The per-LED kernel of the handle's precision mode.
+cudaError_t launch_led_mode(fpm_handle* h, const LedArgs& a, bool pdl) {
+  if (h->hp.precision != FPM_PRECISION_FP32_FFT) return launch_led_gemm(h->gp, a, h->gconst, h->gscr, h->st, pdl);
+  return launch_led(h->m, h->C, a, h->st, pdl);
+}
+
 UpdArgs upd_args(fpm_handle* h, const int4* slot_dev, int B, int step_off, double* loss_slot, int assemble) {
   UpdArgs u{};
   u.Ot = h->Ot;
@@ -285,7 +305,7 @@ UpdArgs upd_args(fpm_handle* h, const int4* slot_dev, int B, int step_off, doubl
   u.N = h->N;
   u.n_leds = h->n;
   u.B = B;
-  u.C = h->C;
+  u.C = h->hp.precision != FPM_PRECISION_FP32_FFT ? 1 : h->C;  // partials per LED
   u.h = h->h;
   u.W = h->W;
   u.lr_obj = h->hp.lr_object;
@@ -350,7 +370,7 @@ int build_graph(fpm_handle* h, int n_steps, int B, fpm_handle::Graph* gr) {
   // and wait in-kernel for their predecessor's results
   for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
     const int4* idx = h->sched + (size_t)s * B;
-    e = launch_led(h->m, h->C, led_args(h, idx, B, MODE_LOSS), h->st, s > 0);
+    e = launch_led_mode(h, led_args(h, idx, B, MODE_LOSS), s > 0);
     if (e == cudaSuccess) e = launch_update(upd_args(h, idx, B, s, h->losses + s, 0), h->st, true);
   }
   cudaError_t e2 = cudaStreamEndCapture(h->st, &g);
@@ -516,13 +536,38 @@ int fpm_set_hparams(fpm_handle* h, const fpm_hparams* hp) {
   if (!h || !hp) return fail(h, FPM_ERR_ARG, "null argument");
   if (hp->loss != FPM_LOSS_AMPLITUDE && hp->loss != FPM_LOSS_INTENSITY) return fail(h, FPM_ERR_ARG, "unknown loss");
   if (hp->learn_mask & ~FPM_LEARN_ALL) return fail(h, FPM_ERR_ARG, "unknown learn bits");
-  if (hp->precision != FPM_PRECISION_FP32_FFT) return fail(h, FPM_ERR_ARG, "unsupported precision mode");
+  if (hp->precision < FPM_PRECISION_FP32_FFT || hp->precision > FPM_PRECISION_TF32X3_GEMM)
+    return fail(h, FPM_ERR_ARG, "unknown precision mode");
   if (!(hp->beta1 >= 0.f && hp->beta1 < 1.f && hp->beta2 >= 0.f && hp->beta2 < 1.f && hp->eps > 0.f))
     return fail(h, FPM_ERR_ARG, "betas must lie in [0, 1) and eps be positive");
   const bool lr_ok = std::isfinite(hp->lr_object) && std::isfinite(hp->lr_zernike) &&
                      std::isfinite(hp->lr_defocus) && std::isfinite(hp->lr_gamma) && std::isfinite(hp->lr_offset);
   if (!lr_ok) return fail(h, FPM_ERR_ARG, "non-finite learning rate");
   const bool graph_relevant = hp->loss != h->hp.loss || std::memcmp(hp, &h->hp, sizeof *hp) != 0;
+  if (hp->precision != h->hp.precision) {
+    // a new DFT form: plan it, build its constant factors, drop the old buffers
+    GemmPlan gp;
+    if (hp->precision != FPM_PRECISION_FP32_FFT) {
+      const char* why = "";
+      const int rc = gemm_plan(h->m, h->W, h->h, hp->precision, &gp, &why);
+      if (rc) return fail(h, rc, "%s", why);
+    }
+    CK(h, cudaStreamSynchronize(h->st));  // kernels in flight may still read the old buffers
+    destroy_graphs(h);
+    if (h->gconst) CK(h, cudaFree(h->gconst));
+    if (h->gscr) CK(h, cudaFree(h->gscr));
+    h->gconst = nullptr;
+    h->gscr = nullptr;
+    h->cap_gscr = 0;
+    h->gp = gp;
+    h->hp.precision = FPM_PRECISION_FP32_FFT;  // until the new form is ready
+    if (hp->precision != FPM_PRECISION_FP32_FFT) {
+      const std::vector<unsigned char> cst = gemm_constants(gp);
+      CK(h, gemm_prepare(gp));
+      CK(h, cudaMalloc(&h->gconst, cst.size()));
+      CK(h, cudaMemcpy(h->gconst, cst.data(), cst.size(), cudaMemcpyHostToDevice));
+    }
+  }
   h->hp = *hp;
   if (graph_relevant) destroy_graphs(h);  // the captured kernels hold the hyper-parameters by value
   return FPM_OK;
@@ -639,7 +684,7 @@ int fpm_profile_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int
     const int4* idx = h->sched + (size_t)s * B;
     if (flush) e = cudaMemsetAsync(flush, s & 0xff, (size_t)flush_bytes, h->st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s], h->st);
-    if (e == cudaSuccess) e = launch_led(h->m, h->C, led_args(h, idx, B, MODE_LOSS), h->st, false);
+    if (e == cudaSuccess) e = launch_led_mode(h, led_args(h, idx, B, MODE_LOSS), false);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 1], h->st);
     if (e == cudaSuccess) e = launch_update(upd_args(h, idx, B, s, h->losses + s, 0), h->st, false);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 2], h->st);
@@ -689,6 +734,7 @@ int fpm_forward(fpm_handle* h, const int32_t* idx, int32_t B, float* I_out) {
   if ((rc = grow(h, &h->sched, &h->cap_sched, B))) return rc;
   const size_t img = (size_t)B * h->m * h->m;
   const bool dev_out = is_device_ptr(I_out);
+  if (dev_out && ((uintptr_t)I_out & 15)) return fail(h, FPM_ERR_ARG, "device I_out must be 16-byte aligned");
   if (!dev_out && (rc = ensure_fbuf(h, img))) return rc;
   if ((rc = enter(h))) return rc;
   std::vector<int4> slots(B);
@@ -696,7 +742,7 @@ int fpm_forward(fpm_handle* h, const int32_t* idx, int32_t B, float* I_out) {
   CK(h, cudaMemcpyAsync(h->sched, slots.data(), sizeof(int4) * B, cudaMemcpyHostToDevice, h->st));
   LedArgs a = led_args(h, h->sched, B, MODE_FORWARD);
   a.I_out = dev_out ? I_out : h->fbuf;
-  CK(h, launch_led(h->m, h->C, a, h->st, false));
+  CK(h, launch_led_mode(h, a, false));
   if (!dev_out) {
     CK(h, cudaMemcpyAsync(I_out, h->fbuf, sizeof(float) * img, cudaMemcpyDeviceToHost, h->st));
     CK(h, cudaStreamSynchronize(h->st));
@@ -726,7 +772,7 @@ int fpm_backward(fpm_handle* h, const int32_t* idx, int32_t B, const float* dL_d
     if (!dev_in) CK(h, cudaMemcpyAsync(h->fbuf, dL_dI, sizeof(float) * img, cudaMemcpyHostToDevice, h->st));
     a.dLdI = dev_in ? dL_dI : h->fbuf;
   }
-  CK(h, launch_led(h->m, h->C, a, h->st, false));
+  CK(h, launch_led_mode(h, a, false));
   const size_t NN = (size_t)h->N * h->N;
   CK(h, cudaMemsetAsync(h->tmp, 0, sizeof(float2) * NN, h->st));
   CK(h, launch_update(upd_args(h, h->sched, B, 0, h->losses, 1), h->st, false));

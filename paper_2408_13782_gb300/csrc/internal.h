@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 struct fpm_handle;
 
 namespace fpmk {
@@ -20,7 +22,7 @@ __host__ __device__ inline int sp_size(int n_leds) { return SP_GAMMA + 3 * n_led
 enum LedMode : int { MODE_LOSS = 0, MODE_FORWARD = 1, MODE_UPSTREAM = 2 };
 
 // Device error flags (bit set, OR-accumulated).
-enum : int { DERR_INDEX = 1, DERR_NONFINITE = 2 };
+enum : int { DERR_INDEX = 1, DERR_NONFINITE = 2, DERR_TIMEOUT = 4 };
 
 constexpr int MAX_BATCH = 1024;
 
@@ -81,6 +83,32 @@ int engine_snapshot_loss(fpm_handle* h, double* pinned);
 
 // Message returned by fpm_last_error(NULL) (calls that have no handle).
 void set_unbound_error(const char* msg);
+
+// Tensor-core DFT form of the per-LED kernel (gemm_led.cu). Every operand of
+// the four contractions is stored in K-step slices (see tc.cuh): the constant
+// DFT factors once per handle, the per-LED data operands in a scratch area
+// per batch slot. Sizes in bytes.
+struct GemmPlan {
+  int prec = 0, tf32 = 0, split = 0, e = 2;  // element bytes e: 2 (BF16) or 4 (TF32)
+  int m = 0, W = 0, h = 0, Wp = 0;           // box width W padded to Wp (multiple of 16)
+  int YT = 0, ntile = 0;                     // image rows per tile (<= 128), tiles
+  int X = 0, nchunk = 0;                     // image columns per chunk, chunks
+  int ks1 = 0, ks3 = 0, ks4 = 0;             // K-steps of contractions 1 and 2, 3, 4
+  size_t S1 = 0, S2 = 0, S3 = 0, S4 = 0;     // one hi copy of each constant block
+  size_t c2_base = 0, c3_base = 0, c4_base = 0, const_bytes = 0;
+  size_t SP = 0, SA = 0, SB = 0, SU = 0;     // one hi copy of each data operand
+  size_t o_phi = 0, o_at = 0, o_bg = 0, o_au = 0, o_spill = 0, slot_bytes = 0;
+  int ns = 0;                                // pipeline stages
+  size_t stage = 0, smem = 0;
+};
+
+// 0 if the form is available for this size, else an FPM_ERR_* code with why.
+int gemm_plan(int m, int W, int h, int prec, GemmPlan* p, const char** why);
+// The constant DFT factors of a plan (host bytes, laid out for the device).
+std::vector<unsigned char> gemm_constants(const GemmPlan& p);
+cudaError_t gemm_prepare(const GemmPlan& p);
+cudaError_t launch_led_gemm(const GemmPlan& p, const LedArgs& a, const unsigned char* consts,
+                            unsigned char* scratch, cudaStream_t s, bool pdl);
 
 // Shared-memory carveout and attributes of the update kernel (call once).
 cudaError_t update_prepare();

@@ -19,6 +19,7 @@
 #include "../../include/fpm.h"
 #include "device.cuh"
 #include "internal.h"
+#include "pixel.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -33,9 +34,6 @@ template <> struct LedCfg<128> { static constexpr int NT = 256; };
 template <> struct LedCfg<256> { static constexpr int NT = 256; };
 template <> struct LedCfg<512> { static constexpr int NT = 256; };
 
-// per-thread accumulators: loss, gamma, 15 monomial moments, defocus, delta_y, delta_x
-constexpr int NACC = 20;
-enum : int { A_LOSS = 0, A_GAMMA = 1, A_MONO = 2, A_DEF = 17, A_DY = 18, A_DX = 19 };
 
 template <int M, int C>
 struct LedLayout {
@@ -56,11 +54,6 @@ struct LedLayout {
   }
 };
 
-__device__ __forceinline__ float warp_sum_f(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -219,31 +212,12 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, M == 512 ? 1 : 2) led_kernel(co
     transform<M, +1>(buf, TW, tws, tw2, j);
     for (int t = j; t < M; t += G) {
       const float2 psi = cscale(buf[bidx<M>(t)], inv_m2);
-      const float mag2 = psi.x * psi.x + psi.y * psi.y;
       float2 gp = make_float2(0.f, 0.f);
       if (act) {
-        if (a.mode == MODE_FORWARD) {
-          a.I_out[((size_t)k * M + y) * M + t] = gam * mag2;
-        } else if (a.mode == MODE_LOSS) {
-          const float meas = ms[yl * M + t];
-          if (a.loss == 0) {
-            const float rinv = mag2 > 0.f ? rsqrtf(mag2) : 0.f;
-            const float mag = mag2 * rinv;
-            const float res = sg * mag - sqrtf(fmaxf(meas, 0.f));
-            acc_loss = fmaf(res, res, acc_loss);
-            acc_g = fmaf(res, mag, acc_g);
-            gp = cscale(psi, 2.f * res * sg * rinv);   // 0 where psi = 0
-          } else {
-            const float res = gam * mag2 - meas;
-            acc_loss = fmaf(res, res, acc_loss);
-            acc_g = fmaf(2.f * res, mag2, acc_g);
-            gp = cscale(psi, 4.f * gam * res);
-          }
-        } else {
-          const float d = ms[yl * M + t];
-          acc_g = fmaf(d, mag2, acc_g);
-          gp = cscale(psi, 2.f * gam * d);
-        }
+        if (a.mode == MODE_FORWARD)
+          a.I_out[((size_t)k * M + y) * M + t] = gam * (psi.x * psi.x + psi.y * psi.y);
+        else
+          gp = residual_pixel(psi, ms[yl * M + t], a.mode, a.loss, gam, sg, acc_loss, acc_g);
       }
       buf[bidx<M>(t)] = gp;
     }
@@ -263,10 +237,8 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, M == 512 ? 1 : 2) led_kernel(co
   if (a.mode == MODE_FORWARD) return;
 
   // ---------------- phase C: column transforms over y, box gradients -------
-  float acc_m[15];
-#pragma unroll
-  for (int q = 0; q < 15; ++q) acc_m[q] = 0.f;
-  float acc_def = 0.f, acc_dy = 0.f, acc_dx = 0.f;
+  BoxAcc bacc;
+  box_acc_zero(bacc);
   float2* gb = a.gbox + (size_t)k * W * W;
   for (int cb = c0; cb < c1; cb += NG) {
     const int c = cb + grp;
@@ -282,46 +254,8 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, M == 512 ? 1 : 2) led_kernel(co
         const float qy = (float)ky - dly;
         float2 out = make_float2(0.f, 0.f);
         const float A = pupil_amp(qy, qx, P);
-        if (A > 0.f) {
-          const float2 gphi = cscale(buf[bidx<M>(ky & (M - 1))], inv_m2);
-          float mo[15];
-          monomials(qx * P.Rinv, qy * P.Rinv, mo);
-          float th = 0.f, dthx = 0.f, dthy = 0.f;
-#pragma unroll
-          for (int q = 0; q < 15; ++q) th = fmaf(poly[q], mo[q], th);
-#pragma unroll
-          for (int q = 0; q < 10; ++q) {
-            dthx = fmaf(poly[15 + q], mo[q], dthx);
-            dthy = fmaf(poly[25 + q], mo[q], dthy);
-          }
-          const float r2 = qx * qx + qy * qy;
-          float root;
-          const float kap = defocus_kappa(r2, P, &root);
-          float sn, cs;
-          sincosf(fmaf(zdef, kap, th), &sn, &cs);
-          const float2 e = make_float2(cs, sn);
-          const float2 Mv = cscale(e, A);
-          out = cmulc(Mv, gphi);                   // conj(M) gPhi
-          const float2 gM = cmulc(Oc[ky], gphi);   // conj(O) gPhi
-          const float tt = -cmulc(gM, Mv).y;       // dL/dchi = Re(conj(gM) i M)
-          const float ee = cmulc(gM, e).x;         // dL/dA   = Re(conj(gM) e^{i chi})
-#pragma unroll
-          for (int q = 0; q < 15; ++q) acc_m[q] = fmaf(tt, mo[q], acc_m[q]);
-          acc_def = fmaf(tt, kap, acc_def);
-          const float dk = -6.283185307179586f * P.dk2 / root;  // d kappa / d q = dk * q
-          const float dchiy = fmaf(dthy, P.Rinv, zdef * dk * qy);
-          const float dchix = fmaf(dthx, P.Rinv, zdef * dk * qx);
-          float dAy = 0.f, dAx = 0.f;
-          if (!P.hard_edge) {
-            const float rad = sqrtf(r2);
-            if (rad > P.R - 0.5f && rad < P.R + 0.5f) {
-              dAy = -qy / rad;
-              dAx = -qx / rad;
-            }
-          }
-          acc_dy -= fmaf(tt, dchiy, ee * dAy);
-          acc_dx -= fmaf(tt, dchix, ee * dAx);
-        }
+        if (A > 0.f)
+          out = box_pixel(qy, qx, A, cscale(buf[bidx<M>(ky & (M - 1))], inv_m2), Oc[ky], P, poly, zdef, bacc);
         gb[(size_t)c * W + r] = out;
       }
     }
@@ -329,40 +263,8 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, M == 512 ? 1 : 2) led_kernel(co
   }
 
   // ---------------- reduction of the scalar partials -----------------------
-  // FP32 within a thread (a few dozen terms) and across a warp, FP64 across
-  // warps; the monomial moments become Zernike gradients in FP64 at the end.
-  const int warp = tid >> 5, lane = tid & 31;
-  float vals[NACC];
-  vals[A_LOSS] = acc_loss;
-  vals[A_GAMMA] = acc_g;
-#pragma unroll
-  for (int q = 0; q < 15; ++q) vals[A_MONO + q] = acc_m[q];
-  vals[A_DEF] = acc_def;
-  vals[A_DY] = acc_dy;
-  vals[A_DX] = acc_dx;
-#pragma unroll
-  for (int q = 0; q < NACC; ++q) {
-    const float s = warp_sum_f(vals[q]);
-    if (lane == 0) red[warp * NACC + q] = s;
-  }
-  __syncthreads();
-  double tot = 0.0;
-  if (tid < NACC)
-    for (int w = 0; w < NW; ++w) tot += (double)red[w * NACC + tid];
-  if (tid >= A_MONO && tid < A_MONO + 15) dsum[tid - A_MONO] = tot;
-  __syncthreads();
-  // this CTA's partials in Zernike form; the update kernel sums the ranks
-  double* out = a.part + ((size_t)k * C + rank) * NPART;
-  if (tid == A_LOSS) out[P_LOSS] = tot;
-  if (tid == A_GAMMA) out[P_GAMMA] = (a.mode == MODE_LOSS && a.loss == 0) ? tot / (double)sg : tot;
-  if (tid == A_DEF) out[P_DEFOCUS] = tot;
-  if (tid == A_DY) out[P_DY] = tot;
-  if (tid == A_DX) out[P_DX] = tot;
-  if (tid < 14) {  // dL/dc_j = sum_m (Z_j)_m * (sum_p t(p) mo_m(p))
-    double z = 0.0;
-    for (int m = 0; m < 15; ++m) z += (double)zmt[tid * 15 + m] * dsum[m];
-    out[P_ZERN + tid] = z;
-  }
+  write_partials(acc_loss, acc_g, bacc, a.mode == MODE_LOSS && a.loss == 0, sg, red, dsum, zmt,
+                 a.part + ((size_t)k * C + rank) * NPART);
 }
 
 // Cluster sizes built for each low-res size (CTAs cooperating on one LED).

@@ -1,0 +1,139 @@
+// Per-pixel pieces of the per-LED step shared by the FFT and the GEMM kernels:
+// the loss residual (Section 2.2, Eq. 4-5) and the box gradients of the object
+// and of the pupil parameters (adjoint of Section 2.1, Eq. 3).
+#pragma once
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace fpmk {
+
+// Residual at one pixel for a predicted field psi (already 1/m^2 scaled).
+// v is the measured intensity (loss modes) or the upstream dL/dI. Returns
+// the field gradient dL/dpsi and accumulates the loss and dL/dgamma terms.
+__device__ __forceinline__ float2 residual_pixel(float2 psi, float v, int mode, int loss, float gam, float sg,
+                                                 float& acc_loss, float& acc_g) {
+  const float mag2 = psi.x * psi.x + psi.y * psi.y;
+  if (mode == MODE_LOSS) {
+    if (loss == 0) {
+      const float rinv = mag2 > 0.f ? rsqrtf(mag2) : 0.f;
+      const float mag = mag2 * rinv;
+      const float res = sg * mag - sqrtf(fmaxf(v, 0.f));
+      acc_loss = fmaf(res, res, acc_loss);
+      acc_g = fmaf(res, mag, acc_g);
+      return cscale(psi, 2.f * res * sg * rinv);  // 0 where psi = 0
+    }
+    const float res = gam * mag2 - v;
+    acc_loss = fmaf(res, res, acc_loss);
+    acc_g = fmaf(2.f * res, mag2, acc_g);
+    return cscale(psi, 4.f * gam * res);
+  }
+  acc_g = fmaf(v, mag2, acc_g);
+  return cscale(psi, 2.f * gam * v);
+}
+
+struct BoxAcc {
+  float m[15];  // monomial moments sum t(p) x^a y^b
+  float def, dy, dx;
+};
+
+__device__ __forceinline__ void box_acc_zero(BoxAcc& b) {
+#pragma unroll
+  for (int q = 0; q < 15; ++q) b.m[q] = 0.f;
+  b.def = b.dy = b.dx = 0.f;
+}
+
+// One pixel of an LED's support box at q = (qy, qx) = p - delta with the
+// spectrum gradient gphi and the object value o there: returns the object
+// gradient conj(M) gphi and accumulates the pupil-parameter gradient terms.
+// poly: K[15], Dx[10], Dy[10] of the aberration phase. Caller checks A > 0.
+__device__ __forceinline__ float2 box_pixel(float qy, float qx, float A, float2 gphi, float2 o, const PupilConst& P,
+                                            const float* poly, float zdef, BoxAcc& acc) {
+  float mo[15];
+  monomials(qx * P.Rinv, qy * P.Rinv, mo);
+  float th = 0.f, dthx = 0.f, dthy = 0.f;
+#pragma unroll
+  for (int q = 0; q < 15; ++q) th = fmaf(poly[q], mo[q], th);
+#pragma unroll
+  for (int q = 0; q < 10; ++q) {
+    dthx = fmaf(poly[15 + q], mo[q], dthx);
+    dthy = fmaf(poly[25 + q], mo[q], dthy);
+  }
+  const float r2 = qx * qx + qy * qy;
+  float root;
+  const float kap = defocus_kappa(r2, P, &root);
+  float sn, cs;
+  sincosf(fmaf(zdef, kap, th), &sn, &cs);
+  const float2 e = make_float2(cs, sn);
+  const float2 Mv = cscale(e, A);
+  const float2 gM = cmulc(o, gphi);     // conj(O) gPhi
+  const float tt = -cmulc(gM, Mv).y;    // dL/dchi = Re(conj(gM) i M)
+  const float ee = cmulc(gM, e).x;      // dL/dA   = Re(conj(gM) e^{i chi})
+#pragma unroll
+  for (int q = 0; q < 15; ++q) acc.m[q] = fmaf(tt, mo[q], acc.m[q]);
+  acc.def = fmaf(tt, kap, acc.def);
+  const float dk = -6.283185307179586f * P.dk2 / root;  // d kappa / d q = dk * q
+  const float dchiy = fmaf(dthy, P.Rinv, zdef * dk * qy);
+  const float dchix = fmaf(dthx, P.Rinv, zdef * dk * qx);
+  float dAy = 0.f, dAx = 0.f;
+  if (!P.hard_edge) {
+    const float rad = sqrtf(r2);
+    if (rad > P.R - 0.5f && rad < P.R + 0.5f) {
+      dAy = -qy / rad;
+      dAx = -qx / rad;
+    }
+  }
+  acc.dy -= fmaf(tt, dchiy, ee * dAy);
+  acc.dx -= fmaf(tt, dchix, ee * dAx);
+  return cmulc(Mv, gphi);               // conj(M) gPhi
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Per-thread accumulators: loss, gamma, 15 monomial moments, defocus, dy, dx.
+constexpr int NACC = 20;
+enum : int { A_LOSS = 0, A_GAMMA = 1, A_MONO = 2, A_DEF = 17, A_DY = 18, A_DX = 19 };
+
+// Reduce the block's accumulators and write its FP64 partials (NPART values):
+// FP32 within threads and warps, FP64 across warps; the monomial moments become
+// Zernike gradients through the table zmt (row j-2 = Z_j). red: [nwarps][NACC]
+// floats, dsum: [16] doubles of shared memory. Called by every thread.
+__device__ __forceinline__ void write_partials(float acc_loss, float acc_g, const BoxAcc& b, bool amp_loss_gamma,
+                                               float sg, float* red, double* dsum, const float* zmt, double* out) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
+  float vals[NACC];
+  vals[A_LOSS] = acc_loss;
+  vals[A_GAMMA] = acc_g;
+#pragma unroll
+  for (int q = 0; q < 15; ++q) vals[A_MONO + q] = b.m[q];
+  vals[A_DEF] = b.def;
+  vals[A_DY] = b.dy;
+  vals[A_DX] = b.dx;
+#pragma unroll
+  for (int q = 0; q < NACC; ++q) {
+    const float s = warp_sum_f(vals[q]);
+    if (lane == 0) red[warp * NACC + q] = s;
+  }
+  __syncthreads();
+  double tot = 0.0;
+  if (tid < NACC)
+    for (int w = 0; w < nw; ++w) tot += (double)red[w * NACC + tid];
+  if (tid >= A_MONO && tid < A_MONO + 15) dsum[tid - A_MONO] = tot;
+  __syncthreads();
+  if (tid == A_LOSS) out[P_LOSS] = tot;
+  if (tid == A_GAMMA) out[P_GAMMA] = amp_loss_gamma ? tot / (double)sg : tot;
+  if (tid == A_DEF) out[P_DEFOCUS] = tot;
+  if (tid == A_DY) out[P_DY] = tot;
+  if (tid == A_DX) out[P_DX] = tot;
+  if (tid < 14) {  // dL/dc_j = sum_m (Z_j)_m * (sum_p t(p) mo_m(p))
+    double z = 0.0;
+    for (int m = 0; m < 15; ++m) z += (double)zmt[tid * 15 + m] * dsum[m];
+    out[P_ZERN + tid] = z;
+  }
+}
+
+}  // namespace fpmk

@@ -23,6 +23,9 @@ ERRORS = {-1: "FPM_ERR_ARG", -2: "FPM_ERR_SHAPE", -3: "FPM_ERR_RANGE", -4: "FPM_
 EDGE = {"aa": 0, "hard": 1}
 LOSS = {"amplitude": 0, "intensity": 1}
 LEARN = {"object": 1, "zernike": 2, "defocus": 4, "gamma": 8, "offset": 16}
+# transform arithmetic: FP32 shared-memory FFTs, or the DFT as tensor-core
+# contractions with BF16 / TF32 operands (x3: hi + lo split, three products)
+PRECISION = {"fp32_fft": 0, "bf16": 1, "bf16x3": 2, "tf32": 3, "tf32x3": 4}
 LOAD_INIT = 1
 
 # every symbol include/fpm.h declares
@@ -177,7 +180,8 @@ class Engine:
         return self._h
 
     # -- API ---------------------------------------------------------------
-    def set_hparams(self, lr=None, betas=(0.9, 0.999), eps=1e-8, loss="amplitude", learn=("object",)):
+    def set_hparams(self, lr=None, betas=(0.9, 0.999), eps=1e-8, loss="amplitude", learn=("object",),
+                    precision="fp32_fft"):
         rates = dict(object=0.1, zernike=0.01, defocus=0.1, gamma=0.01, offset=0.01)
         rates.update(lr or {})
         lr = rates
@@ -185,7 +189,7 @@ class Engine:
         for k in learn:
             mask |= LEARN[k]
         hp = Hparams(lr["object"], lr["zernike"], lr["defocus"], lr["gamma"], lr["offset"],
-                     betas[0], betas[1], eps, LOSS[loss], mask, 0)
+                     betas[0], betas[1], eps, LOSS[loss], mask, PRECISION[precision])
         self._check(lib().fpm_set_hparams(self._h, ctypes.byref(hp)))
 
     def load(self, stack, init: bool = True):
