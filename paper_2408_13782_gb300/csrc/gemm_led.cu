@@ -92,7 +92,8 @@ struct GemmArgs {
   LedArgs a;
   const unsigned char* cst;  // constant DFT factors
   unsigned char* scr;        // per-slot scratch
-  int m, Wp, YT, ntile, X, nchunk, ks1, ks3, ks4, ns;
+  int m, Wp, YT, ntile, X, nchunk, ks1, ks3, ks4, ns, kps;
+  size_t aux;
   uint32_t S1, S2, S3, S4, SP, SA, SB, SU, stage;
   size_t c2_base, c3_base, c4_base, slot_bytes, o_phi, o_at, o_bg, o_au, o_spill;
 };
@@ -112,83 +113,85 @@ struct Call {
   int accum;
 };
 
-// Bytes of one K-step stage of a contraction.
-template <bool SPLIT>
-__device__ __forceinline__ uint32_t stage_bytes_of(const Call& c) {
-  constexpr int F = SPLIT ? 2 : 1;
-  return (uint32_t)(c.nA * F) * A_SLICE + F * c.b_slice;
-}
-
-// Producer (one thread): bulk-copies the K-step slices of A and B into the
+// Producer (one thread): bulk-copies groups of up to kps K-steps of A and B
+// (one copy per operand and group: a group's slices are contiguous) into the
 // stage ring, reusing a stage once the MMAs that read it have completed.
-// q counts K-steps through the ring (the same count as the issuer's).
+// q counts groups through the ring (the same count as the issuer's).
 template <bool SPLIT>
-__device__ bool gemm_produce(const Call& c, unsigned char* stages, uint32_t stage_bytes, int ns, uint64_t* full,
-                             uint64_t* empty, uint32_t& q) {
+__device__ bool gemm_produce(const Call& c, unsigned char* stages, uint32_t stage_bytes, int ns, int kps,
+                             uint64_t* full, uint64_t* empty, uint32_t& q) {
   constexpr int F = SPLIT ? 2 : 1;
-  const uint32_t bytes = stage_bytes_of<SPLIT>(c);
+  const int ngrp = (c.ks + kps - 1) / kps;
   const uint32_t q0 = q;
   int issued = 0;
   bool ok = true;
-  for (int i = 0; i < c.ks; ++i) {
-    const uint32_t Q = q0 + i, s = Q % ns, u = Q / ns;
+  for (int gi = 0; gi < ngrp; ++gi) {
+    const uint32_t Q = q0 + gi, s = Q % ns, u = Q / ns;
     if (u > 0 && !tc::mbar_wait(&empty[s], (u - 1) & 1, WAIT_NS)) {
       ok = false;
       break;
     }
+    const int k0 = gi * kps, nk = min(kps, c.ks - k0);
+    const uint32_t abytes = (uint32_t)nk * A_SLICE, bbytes = (uint32_t)nk * c.b_slice;
     unsigned char* st = stages + (size_t)s * stage_bytes;
-    tc::mbar_expect_tx(&full[s], bytes);
+    tc::mbar_expect_tx(&full[s], (uint32_t)(c.nA * F) * abytes + F * bbytes);
     for (int j = 0; j < c.nA; ++j) {
-      tc::bulk_g2s(st + (j * F) * A_SLICE, c.A[j] + (size_t)i * A_SLICE, A_SLICE, &full[s]);
-      if (SPLIT) tc::bulk_g2s(st + (j * F + 1) * A_SLICE, c.A[j] + c.a_lo + (size_t)i * A_SLICE, A_SLICE, &full[s]);
+      tc::bulk_g2s(st + (size_t)(j * F) * kps * A_SLICE, c.A[j] + (size_t)k0 * A_SLICE, abytes, &full[s]);
+      if (SPLIT)
+        tc::bulk_g2s(st + (size_t)(j * F + 1) * kps * A_SLICE, c.A[j] + c.a_lo + (size_t)k0 * A_SLICE, abytes,
+                     &full[s]);
     }
-    unsigned char* sb = st + (c.nA * F) * A_SLICE;
-    tc::bulk_g2s(sb, c.B + (size_t)i * c.b_slice, c.b_slice, &full[s]);
-    if (SPLIT) tc::bulk_g2s(sb + c.b_slice, c.B + c.b_lo + (size_t)i * c.b_slice, c.b_slice, &full[s]);
-    issued = i + 1;
+    unsigned char* sb = st + (size_t)(c.nA * F) * kps * A_SLICE;
+    tc::bulk_g2s(sb, c.B + (size_t)k0 * c.b_slice, bbytes, &full[s]);
+    if (SPLIT) tc::bulk_g2s(sb + (size_t)kps * c.b_slice, c.B + c.b_lo + (size_t)k0 * c.b_slice, bbytes, &full[s]);
+    issued = gi + 1;
   }
   if (!ok)  // let the copies in flight land before anything is torn down
-    for (int i = issued > ns ? issued - ns : 0; i < issued; ++i) {
-      const uint32_t Q = q0 + i;
+    for (int gi = issued > ns ? issued - ns : 0; gi < issued; ++gi) {
+      const uint32_t Q = q0 + gi;
       tc::mbar_wait(&full[Q % ns], (Q / ns) & 1, WAIT_NS);
     }
-  q = q0 + (uint32_t)c.ks;
+  q = q0 + (uint32_t)ngrp;
   return ok;
 }
 
 // MMA issuer (one thread): waits for each stage, issues its MMAs (three per
-// output block in the split forms), releases the stage; commits `done` at the
-// end, also after a failed wait.
+// output block and K-step in the split forms), releases the stage; commits
+// `done` at the end, also after a failed wait.
 template <bool TF32, bool SPLIT>
-__device__ bool gemm_issue(const Call& c, unsigned char* stages, uint32_t stage_bytes, int ns, uint64_t* full,
-                           uint64_t* empty, uint64_t* done, uint32_t tbase, uint32_t& q) {
+__device__ bool gemm_issue(const Call& c, unsigned char* stages, uint32_t stage_bytes, int ns, int kps,
+                           uint64_t* full, uint64_t* empty, uint64_t* done, uint32_t tbase, uint32_t& q) {
   constexpr int F = SPLIT ? 2 : 1;
+  const int ngrp = (c.ks + kps - 1) / kps;
   const uint32_t q0 = q;
   bool ok = true;
-  for (int i = 0; i < c.ks; ++i) {
-    const uint32_t Q = q0 + i, s = Q % ns, u = Q / ns;
+  for (int gi = 0; gi < ngrp; ++gi) {
+    const uint32_t Q = q0 + gi, s = Q % ns, u = Q / ns;
     if (!tc::mbar_wait(&full[s], u & 1, WAIT_NS)) {
       ok = false;
       break;
     }
     tc::fence_after_sync();
+    const int k0 = gi * kps, nk = min(kps, c.ks - k0);
     const uint32_t sa = tc::smem_u32(stages + (size_t)s * stage_bytes);
-    const uint32_t sbb = sa + (uint32_t)(c.nA * F) * A_SLICE;
-    const uint64_t bh = tc::sdesc(sbb, 128, 256);
-    const uint64_t bl = SPLIT ? tc::sdesc(sbb + c.b_slice, 128, 256) : 0;
-    for (int j = 0; j < c.nA; ++j) {
-      const uint64_t ah = tc::sdesc(sa + (uint32_t)(j * F) * A_SLICE, 128, 256);
-      const uint32_t d = tbase + c.dcol[j];
-      tc::mma<TF32>(d, ah, bh, c.id, (c.accum || i > 0) ? 1u : 0u);
-      if constexpr (SPLIT) {
-        const uint64_t al = tc::sdesc(sa + (uint32_t)(j * F + 1) * A_SLICE, 128, 256);
-        tc::mma<TF32>(d, ah, bl, c.id, 1u);
-        tc::mma<TF32>(d, al, bh, c.id, 1u);
+    const uint32_t sbb = sa + (uint32_t)(c.nA * F * kps) * A_SLICE;
+    for (int kk = 0; kk < nk; ++kk) {
+      const uint64_t bh = tc::sdesc(sbb + kk * c.b_slice, 128, 256);
+      const uint64_t bl = SPLIT ? tc::sdesc(sbb + (kps + kk) * c.b_slice, 128, 256) : 0;
+      for (int j = 0; j < c.nA; ++j) {
+        const uint64_t ah = tc::sdesc(sa + (uint32_t)(j * F * kps + kk) * A_SLICE, 128, 256);
+        const uint32_t d = tbase + c.dcol[j];
+        tc::mma<TF32>(d, ah, bh, c.id, (c.accum || k0 + kk > 0) ? 1u : 0u);
+        if constexpr (SPLIT) {
+          const uint64_t al = tc::sdesc(sa + (uint32_t)((j * F + 1) * kps + kk) * A_SLICE, 128, 256);
+          tc::mma<TF32>(d, ah, bl, c.id, 1u);
+          tc::mma<TF32>(d, al, bh, c.id, 1u);
+        }
       }
     }
     tc::mma_commit(&empty[s]);
   }
-  q = q0 + (uint32_t)c.ks;
+  q = q0 + (uint32_t)ngrp;
   tc::mma_commit(done);
   return ok;
 }
@@ -199,7 +202,11 @@ __global__ void __launch_bounds__(GT, 1) gemm_led_kernel(const GemmArgs g) {
   const LedArgs& a = g.a;
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* stages = smem;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)g.ns * g.stage);
+  // staging of per-pixel inputs: the O box [W][W] (column c contiguous in r),
+  // or one tile-chunk of the image / dL/dI rows [YT][X + 4]
+  float2* ob = reinterpret_cast<float2*>(smem + (size_t)g.ns * g.stage);
+  float* ms = reinterpret_cast<float*>(ob);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + (size_t)g.ns * g.stage + g.aux);
   uint64_t* empty = full + g.ns;
   uint64_t* done = empty + g.ns;
   volatile uint32_t* misc = reinterpret_cast<volatile uint32_t*>(done + 1);  // [0] TMEM base, [1] abort
@@ -262,6 +269,33 @@ __global__ void __launch_bounds__(GT, 1) gemm_led_kernel(const GemmArgs g) {
   const float inv_m2 = 1.f / (float)(m * m);
   const float sg = sqrtf(gam);
 
+  // O on a disk that contains the support for every admissible delta
+  // (|delta| <= sqrt(2) * bound) -> ob[c][r], one cp.async group
+  const float rs = (a.hard_edge ? a.R : a.R + 0.5f) + 1.41422f * FPM_OFFSET_BOUND_PX + 1e-3f;
+  auto fetch_box = [&]() {
+    for (int qq = tid; qq < W * W; qq += GT) {
+      const int c = qq / W, r = qq - c * W;
+      const float px = (float)(c - h), py = (float)(r - h);
+      if (px * px + py * py <= rs * rs) tc::cp_async8(ob + qq, a.Ot + (col0 + c) * N + rowb + r);
+    }
+    tc::cp_async_commit();
+  };
+  // image (or dL/dI) rows of tile t, columns of chunk ch -> ms[row][X + 4]
+  const int MS = X + 4;
+  auto fetch_rows = [&](int t, int ch) {
+    const float* src = a.mode == MODE_LOSS ? a.meas + (size_t)led * m * m
+                     : a.mode == MODE_UPSTREAM ? a.dLdI + (size_t)k * m * m : nullptr;
+    if (src)
+      for (int qq = tid; qq < YT * (X / 4); qq += GT) {
+        const int yl = qq / (X / 4), x4 = qq - yl * (X / 4);
+        tc::cp_async16(ms + yl * MS + 4 * x4, src + (size_t)(t * YT + yl) * m + ch * X + 4 * x4);
+      }
+    tc::cp_async_commit();
+  };
+  fetch_box();
+  tc::cp_async_wait_all();
+  __syncthreads();
+
   // ---- Phi = O x M on the box, as the B operand of step 1 (rows c, K = [Re r | Im r])
   for (int it = tid; it < Wp * (Wp / 8); it += GT) {
     const int c = it % Wp, r0 = (it / Wp) * 8;
@@ -272,7 +306,7 @@ __global__ void __launch_bounds__(GT, 1) gemm_led_kernel(const GemmArgs g) {
       float2 v = make_float2(0.f, 0.f);
       if (c < W && r < W) {
         const float2 Mv = pupil_value_poly((float)(r - h) - dly, (float)(c - h) - dlx, P, poly, zdef);
-        if (Mv.x != 0.f || Mv.y != 0.f) v = cmul(a.Ot[(col0 + c) * N + rowb + r], Mv);
+        if (Mv.x != 0.f || Mv.y != 0.f) v = cmul(ob[c * W + r], Mv);
       }
       re[e] = v.x;
       im[e] = v.y;
@@ -291,12 +325,12 @@ __global__ void __launch_bounds__(GT, 1) gemm_led_kernel(const GemmArgs g) {
     __syncthreads();
     if (tid == 0) {  // MMA issuer
       tc::fence_after_sync();
-      if (!gemm_issue<TF32, SPLIT>(c, stages, g.stage, g.ns, full, empty, done, tbase, q)) {
+      if (!gemm_issue<TF32, SPLIT>(c, stages, g.stage, g.ns, g.kps, full, empty, done, tbase, q)) {
         misc[1] = 1;
         atomicOr(a.err, DERR_TIMEOUT);
       }
     } else if (tid == 32) {  // producer
-      if (!gemm_produce<SPLIT>(c, stages, g.stage, g.ns, full, empty, q)) {
+      if (!gemm_produce<SPLIT>(c, stages, g.stage, g.ns, g.kps, full, empty, q)) {
         misc[1] = 1;
         atomicOr(a.err, DERR_TIMEOUT);
       }
@@ -357,7 +391,11 @@ __global__ void __launch_bounds__(GT, 1) gemm_led_kernel(const GemmArgs g) {
         c.dcol[0] = 256;
         c.id = tc::idesc(FMT, 128, 2 * X);
         c.accum = 0;
-        if (!(ok = run(c))) break;
+        if (a.mode != MODE_FORWARD) fetch_rows(t, ch);  // lands while step 2 runs
+        ok = run(c);
+        tc::cp_async_wait_all();
+        __syncthreads();
+        if (!ok) break;
       }
       // residual (Eq. 4-5) per pixel; g rows -> B operand of step 3 (K = [Re x | Im x])
       for (int x0 = half * (X / 2); x0 < (half + 1) * (X / 2); x0 += 8) {
@@ -378,10 +416,8 @@ __global__ void __launch_bounds__(GT, 1) gemm_led_kernel(const GemmArgs g) {
           dst[1] = make_float4(Iv[4], Iv[5], Iv[6], Iv[7]);
           continue;
         }
-        const float* src = a.mode == MODE_LOSS ? a.meas + ((size_t)led * m + y) * m + xa
-                                               : a.dLdI + ((size_t)k * m + y) * m + xa;
-        const float4 v0 = __ldg(reinterpret_cast<const float4*>(src));
-        const float4 v1 = __ldg(reinterpret_cast<const float4*>(src) + 1);
+        const float4 v0 = *reinterpret_cast<const float4*>(ms + row * MS + x0);
+        const float4 v1 = *reinterpret_cast<const float4*>(ms + row * MS + x0 + 4);
         const float vv[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
         float gr[8], gi[8];
 #pragma unroll
@@ -435,7 +471,11 @@ __global__ void __launch_bounds__(GT, 1) gemm_led_kernel(const GemmArgs g) {
       c.dcol[0] = 256;
       c.id = tc::idesc(FMT, 128, 2 * Wp);
       c.accum = 0;
-      if (!(ok = run(c))) break;
+      if (t == g.ntile - 1) fetch_box();  // lands while step 4 runs
+      ok = run(c);
+      tc::cp_async_wait_all();
+      __syncthreads();
+      if (!ok) break;
     }
     // box column c = row: sum over tiles (in this thread's scratch row), then
     // the object and pupil-parameter gradients per box pixel
@@ -462,7 +502,7 @@ __global__ void __launch_bounds__(GT, 1) gemm_led_kernel(const GemmArgs g) {
         }
       }
       if (c >= W) continue;
-      const float2* Oc = a.Ot + (col0 + c) * N + rowb;
+      const float2* Oc = ob + c * W;
       const float qx = (float)(c - h) - dlx;
       float2* gb = a.gbox + ((size_t)k * W + c) * W;
 #pragma unroll
@@ -595,16 +635,18 @@ int gemm_plan(int m, int W, int h, int prec, GemmPlan* p, const char** why) {
   // bytes of one K-step of each contraction; the stage holds the largest
   const size_t st1 = F * (2 * A_SLICE + (size_t)Wp * 32), st2 = F * (A_SLICE + (size_t)2 * p->X * 32);
   const size_t st3 = F * (2 * A_SLICE + (size_t)p->YT * 32), st4 = F * (A_SLICE + (size_t)2 * Wp * 32);
-  p->stage = round_up(std::max(std::max(st1, st2), std::max(st3, st4)), 1024);
+  p->kps = p->split ? 1 : 2;  // K-steps per stage (one bulk copy per operand and stage)
+  p->stage = round_up((size_t)p->kps * std::max(std::max(st1, st2), std::max(st3, st4)), 1024);
+  p->aux = round_up(std::max((size_t)W * W * sizeof(float2), (size_t)p->YT * (p->X + 4) * sizeof(float)), 1024);
   const size_t misc = (2 * MAX_STAGES + 1) * 8 + 16 + sizeof(float) * (40 + 14 * 15 + 2 + (GT / 32) * NACC) +
                       sizeof(double) * 16;
-  const size_t budget = 227 * 1024 - round_up(misc, 1024);
+  const size_t budget = 227 * 1024 - round_up(misc, 1024) - p->aux;
   p->ns = (int)std::min<size_t>(MAX_STAGES, budget / p->stage);
   if (p->ns < 2) {
     *why = "tensor-core DFT stages do not fit in shared memory";
     return FPM_ERR_SHAPE;
   }
-  p->smem = (size_t)p->ns * p->stage + misc;
+  p->smem = (size_t)p->ns * p->stage + p->aux + misc;
   return FPM_OK;
 }
 
@@ -698,6 +740,8 @@ cudaError_t launch_led_gemm(const GemmPlan& p, const LedArgs& a, const unsigned 
   g.ks3 = p.ks3;
   g.ks4 = p.ks4;
   g.ns = p.ns;
+  g.kps = p.kps;
+  g.aux = p.aux;
   g.S1 = (uint32_t)p.S1;
   g.S2 = (uint32_t)p.S2;
   g.S3 = (uint32_t)p.S3;

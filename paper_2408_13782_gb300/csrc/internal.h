@@ -98,8 +98,8 @@ struct GemmPlan {
   size_t c2_base = 0, c3_base = 0, c4_base = 0, const_bytes = 0;
   size_t SP = 0, SA = 0, SB = 0, SU = 0;     // one hi copy of each data operand
   size_t o_phi = 0, o_at = 0, o_bg = 0, o_au = 0, o_spill = 0, slot_bytes = 0;
-  int ns = 0;                                // pipeline stages
-  size_t stage = 0, smem = 0;
+  int ns = 0, kps = 0;                       // pipeline stages, K-steps per stage
+  size_t stage = 0, aux = 0, smem = 0;       // stage bytes, staging area of per-pixel inputs
 };
 
 // 0 if the form is available for this size, else an FPM_ERR_* code with why.
