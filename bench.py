@@ -52,6 +52,16 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+def _peak_bf16():
+    """Measured dense BF16 tensor throughput (burst: a kernel timed on its own)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
 # --------------------------------------------------------------------------
 # workload
 # --------------------------------------------------------------------------
@@ -296,6 +306,95 @@ def serving_section(n_jobs=16, rate_hz=40.0, seed=5):
 # distributed helpers (torchrun: one rank per GPU, independent jobs)
 # --------------------------------------------------------------------------
 
+def gemm_mma_flops(m: int, W: int, split: bool) -> float:
+    """Tensor-core FLOPs of one LED in the DFT-as-contraction form (padded shapes
+    as issued: box W padded to a multiple of 16, row tiles and column chunks of
+    at most 128, complex contractions as real ones of twice the depth)."""
+    Wp = -(-W // 16) * 16
+    YT = X = min(m, 128)
+    ntile, nchunk = m // YT, m // X
+    macs = ntile * (2 * 128 * Wp * 2 * Wp                      # step 1, real and imaginary blocks
+                    + nchunk * (128 * 2 * X * 2 * Wp)          # step 2
+                    + nchunk * (2 * 128 * YT * 2 * X)          # step 3
+                    + 128 * 2 * Wp * 2 * YT)                   # step 4
+    return 2.0 * macs * (3 if split else 1)
+
+
+def tensor_forms_section(c, nominal, stack, flush, n_steps=40):
+    """The per-LED kernel in each tensor-core DFT form on the same workload and
+    schedule (L2 flushed before every step): kernel time and tensor throughput
+    against the measured BF16 peak (TF32 at half of it, the nominal ratio)."""
+    from paper_2408_13782_gb300 import Engine
+    peak_bf16, kind = _peak_bf16()
+    box = 2 * (int(np.floor(c.R + 0.5 + np.sqrt(2.0))) + 1) + 1
+    out = {}
+    sched = full_batches(c.n_leds, c.B, n_steps + 3, c.seed, first_epoch=500)
+    for form in ("bf16", "bf16x3", "tf32", "tf32x3"):
+        eng = Engine(c.m, c.s, nominal, c.R, c.lambda_um, c.dk_per_um, c.edge)
+        eng.set_hparams(lr=dict(c.lr), learn=c.learn, precision=form)
+        eng.load(stack, init=True)
+        eng.run(sched[:3], losses=False)
+        led_ms, upd_ms, step_ms = eng.profile_run(sched[3:], flush=flush)
+        eng.close()
+        flops = c.B * gemm_mma_flops(c.m, box, form.endswith("x3"))
+        t = float(np.mean(led_ms)) / 1e3
+        peak = peak_bf16 if form.startswith("bf16") else peak_bf16 / 2
+        out[form] = {"led_kernel_ms": t * 1e3, "update_kernel_ms": float(np.mean(upd_ms)),
+                     "led_updates_per_s": c.B / (float(np.mean(step_ms)) / 1e3),
+                     "tensor_tflops": flops / t / 1e12, "peak_tflops": peak,
+                     "frac": flops / t / 1e12 / peak, "mma_flops_per_launch": flops}
+    out["peak_source"] = kind
+    return out
+
+
+def autograd_section(dev, reps=3):
+    """Recompute-in-backward vs stored fields through the torch.autograd.Function
+    on the 2048^2 / 512^2, 15 x 15-LED instance at batch 64: device memory held
+    by torch across forward + backward and the time of the pair."""
+    import torch
+    from paper_2408_13782_gb300 import Engine
+    from paper_2408_13782_gb300.autograd import fpm_intensities
+    from synth import recipes as S
+    c = S.config("c3_mem")
+    nominal, truth = S.led_grid(c.grid, c.pitch, c.jitter, c.seed)
+    eng = Engine(c.m, c.s, nominal, c.R, c.lambda_um, c.dk_per_um, c.edge)
+    rng = np.random.default_rng(c.seed)
+    O = torch.tensor((S.make_object(c.N, c.seed)).astype(np.complex64), device=dev)
+    leaves = [O, torch.tensor(S.zernike_coeffs(c.zernike_sigma, c.seed), dtype=torch.float32, device=dev),
+              torch.tensor([c.z_um], dtype=torch.float32, device=dev),
+              torch.ones(c.n_leds, dtype=torch.float32, device=dev),
+              torch.zeros((c.n_leds, 2), dtype=torch.float32, device=dev)]
+    leaves = [x.requires_grad_(True) for x in leaves]
+    idx = rng.permutation(c.n_leds)[:c.B].astype(np.int32)
+    w = torch.tensor(rng.normal(size=(c.B, c.m, c.m)).astype(np.float32), device=dev)
+    res = {"workload": f"{c.N}^2 object, {c.m}^2 images, {c.n_leds} LEDs, batch {c.B}",
+           "field_bytes": c.B * c.m * c.m * 8}
+    for store in (False, True):
+        for x in leaves:
+            x.grad = None
+        torch.cuda.synchronize()
+        torch.cuda.reset_peak_memory_stats(dev)
+        base = torch.cuda.memory_allocated(dev)
+        times = []
+        for r in range(reps + 1):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            I = fpm_intensities(eng, idx, *leaves, store_fields=store)
+            (I * w).sum().backward()
+            e1.record()
+            torch.cuda.synchronize()
+            if r:
+                times.append(e0.elapsed_time(e1))
+            del I
+            for x in leaves:
+                x.grad = None
+        res["store" if store else "recompute"] = {
+            "peak_torch_bytes": int(torch.cuda.max_memory_allocated(dev) - base),
+            "fwd_bwd_ms": float(np.median(times))}
+    eng.close()
+    return res
+
+
 def dist_setup():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -428,6 +527,9 @@ def engine_arm(args):
 
     if rank == 0 and world == 1 and not args.no_serving:
         result["serving"] = serving_section()
+    if rank == 0 and world == 1 and not args.no_variants:
+        result["tensor_core_forms"] = tensor_forms_section(c, nominal, stack, flush)
+        result["autograd_memory"] = autograd_section(dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = run_cpu_child(stack, args.cpu_sample_s, B, 10_000)
         result["cpu_baseline"] = {"value": r["updates"] / r["seconds"], "unit": UNIT, "cores": 1,
@@ -488,6 +590,8 @@ def main():
     ap.add_argument("--impl", choices=("engine", "reference"), default="engine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the tensor-core DFT forms and the autograd memory study")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--cpu-worker", default=None)
     ap.add_argument("--cpu-leds", type=int, default=16)

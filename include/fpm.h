@@ -178,6 +178,20 @@ int fpm_backward(fpm_handle* h, const int32_t* idx, int32_t B, const float* dL_d
                  float* g_object, float* g_zernike, float* g_defocus, float* g_gamma,
                  float* g_offset, double* loss_out);
 
+/* Store-the-fields form of the pair above (the alternative to recomputing the
+ * fields in the backward pass; FP32 FFT form only). fpm_forward_fields is
+ * fpm_forward that also writes the low-res fields psi_i = IFFT(Phi_i) (Section
+ * 2.1, Eq. 3, before |.|^2) to psi_out [B][m][m][2] (device memory, 8-byte
+ * aligned; I_out device memory, 16-byte aligned). fpm_backward_fields takes
+ * those fields (device) and the upstream dL_dI [B][m][m] (device) for the same
+ * idx and the same engine state, and returns the gradients of fpm_backward
+ * without recomputing psi (outputs as in fpm_backward). The caller owns the
+ * field buffer: B * m * m * 8 bytes between the two calls. */
+int fpm_forward_fields(fpm_handle* h, const int32_t* idx, int32_t B, float* I_out, float* psi_out);
+int fpm_backward_fields(fpm_handle* h, const int32_t* idx, int32_t B, const float* psi, const float* dL_dI,
+                        float* g_object, float* g_zernike, float* g_defocus, float* g_gamma,
+                        float* g_offset);
+
 /* Read / write the current estimate; each pointer nullable (skipped).
  * O [N][N][2], zernike [14], defocus [1], gamma [n_leds], offset [n_leds][2] (delta). */
 int fpm_get(fpm_handle* h, float* O, float* zernike, float* defocus, float* gamma, float* offset);

@@ -387,6 +387,13 @@ int build_graph(fpm_handle* h, int n_steps, int B, fpm_handle::Graph* gr) {
 
 }  // namespace
 
+namespace {
+int forward_impl(fpm_handle* h, const int32_t* idx, int32_t B, float* I_out, float2* psi_out);
+int backward_impl(fpm_handle* h, const int32_t* idx, int32_t B, const float* dL_dI, const float2* psi,
+                  float* g_object, float* g_zernike, float* g_defocus, float* g_gamma, float* g_offset,
+                  double* loss_out);
+}  // namespace
+
 int fpmk::engine_snapshot_loss(fpm_handle* h, double* pinned) {
   int rc = enter(h);
   if (rc) return rc;
@@ -727,7 +734,36 @@ int fpm_epoch_loss(fpm_handle* h, double* out, int32_t reset) {
 }
 
 int fpm_forward(fpm_handle* h, const int32_t* idx, int32_t B, float* I_out) {
+  return forward_impl(h, idx, B, I_out, nullptr);
+}
+
+int fpm_forward_fields(fpm_handle* h, const int32_t* idx, int32_t B, float* I_out, float* psi_out) {
+  if (!h || !I_out || !psi_out) return fail(h, FPM_ERR_ARG, "null argument");
+  if (!is_device_ptr(I_out) || !is_device_ptr(psi_out)) return fail(h, FPM_ERR_ARG, "I_out and psi_out must be device memory");
+  return forward_impl(h, idx, B, I_out, reinterpret_cast<float2*>(psi_out));
+}
+
+int fpm_backward_fields(fpm_handle* h, const int32_t* idx, int32_t B, const float* psi, const float* dL_dI,
+                        float* g_object, float* g_zernike, float* g_defocus, float* g_gamma, float* g_offset) {
+  if (!h || !psi || !dL_dI) return fail(h, FPM_ERR_ARG, "null argument");
+  if (!is_device_ptr(psi) || !is_device_ptr(dL_dI)) return fail(h, FPM_ERR_ARG, "psi and dL_dI must be device memory");
+  return backward_impl(h, idx, B, dL_dI, reinterpret_cast<const float2*>(psi), g_object, g_zernike, g_defocus,
+                       g_gamma, g_offset, nullptr);
+}
+
+int fpm_backward(fpm_handle* h, const int32_t* idx, int32_t B, const float* dL_dI, float* g_object,
+                 float* g_zernike, float* g_defocus, float* g_gamma, float* g_offset, double* loss_out) {
+  return backward_impl(h, idx, B, dL_dI, nullptr, g_object, g_zernike, g_defocus, g_gamma, g_offset, loss_out);
+}
+
+}  // extern "C"
+
+namespace {
+
+int forward_impl(fpm_handle* h, const int32_t* idx, int32_t B, float* I_out, float2* psi_out) {
   if (!h || !I_out) return fail(h, FPM_ERR_ARG, "null argument");
+  if (psi_out && h->hp.precision != FPM_PRECISION_FP32_FFT)
+    return fail(h, FPM_ERR_ARG, "stored fields need the FP32 FFT form");
   int rc = validate_batches(h, idx, 1, B);
   if (rc) return rc;
   if ((rc = ensure_batch(h, B))) return rc;
@@ -740,8 +776,9 @@ int fpm_forward(fpm_handle* h, const int32_t* idx, int32_t B, float* I_out) {
   std::vector<int4> slots(B);
   fill_slots(h, idx, B, slots.data());
   CK(h, cudaMemcpyAsync(h->sched, slots.data(), sizeof(int4) * B, cudaMemcpyHostToDevice, h->st));
-  LedArgs a = led_args(h, h->sched, B, MODE_FORWARD);
+  LedArgs a = led_args(h, h->sched, B, psi_out ? MODE_FORWARD_STORE : MODE_FORWARD);
   a.I_out = dev_out ? I_out : h->fbuf;
+  a.psi = psi_out;
   CK(h, launch_led_mode(h, a, false));
   if (!dev_out) {
     CK(h, cudaMemcpyAsync(I_out, h->fbuf, sizeof(float) * img, cudaMemcpyDeviceToHost, h->st));
@@ -750,9 +787,12 @@ int fpm_forward(fpm_handle* h, const int32_t* idx, int32_t B, float* I_out) {
   return leave(h);
 }
 
-int fpm_backward(fpm_handle* h, const int32_t* idx, int32_t B, const float* dL_dI, float* g_object,
-                 float* g_zernike, float* g_defocus, float* g_gamma, float* g_offset, double* loss_out) {
+int backward_impl(fpm_handle* h, const int32_t* idx, int32_t B, const float* dL_dI, const float2* psi,
+                  float* g_object, float* g_zernike, float* g_defocus, float* g_gamma, float* g_offset,
+                  double* loss_out) {
   if (!h) return FPM_ERR_ARG;
+  if (psi && h->hp.precision != FPM_PRECISION_FP32_FFT)
+    return fail(h, FPM_ERR_ARG, "stored fields need the FP32 FFT form");
   if (!dL_dI && !h->loaded) return fail(h, FPM_ERR_STATE, "no stack loaded");
   int rc = validate_batches(h, idx, 1, B);
   if (rc) return rc;
@@ -767,7 +807,8 @@ int fpm_backward(fpm_handle* h, const int32_t* idx, int32_t B, const float* dL_d
   std::vector<int4> slots(B);
   fill_slots(h, idx, B, slots.data());
   CK(h, cudaMemcpyAsync(h->sched, slots.data(), sizeof(int4) * B, cudaMemcpyHostToDevice, h->st));
-  LedArgs a = led_args(h, h->sched, B, dL_dI ? MODE_UPSTREAM : MODE_LOSS);
+  LedArgs a = led_args(h, h->sched, B, psi ? MODE_UPSTREAM_STORED : dL_dI ? MODE_UPSTREAM : MODE_LOSS);
+  a.psi = const_cast<float2*>(psi);
   if (dL_dI) {
     if (!dev_in) CK(h, cudaMemcpyAsync(h->fbuf, dL_dI, sizeof(float) * img, cudaMemcpyHostToDevice, h->st));
     a.dLdI = dev_in ? dL_dI : h->fbuf;
@@ -793,6 +834,10 @@ int fpm_backward(fpm_handle* h, const int32_t* idx, int32_t B, const float* dL_d
   if (host) CK(h, cudaStreamSynchronize(h->st));
   return leave(h);
 }
+
+}  // namespace
+
+extern "C" {
 
 int fpm_get(fpm_handle* h, float* O, float* zernike, float* defocus, float* gamma, float* offset) {
   if (!h) return FPM_ERR_ARG;

@@ -19,7 +19,9 @@ constexpr int SP_ZERN = 0, SP_DEFOCUS = 14, SP_GAMMA = 15;
 __host__ __device__ inline int sp_offset(int n_leds) { return SP_GAMMA + n_leds; }
 __host__ __device__ inline int sp_size(int n_leds) { return SP_GAMMA + 3 * n_leds; }
 
-enum LedMode : int { MODE_LOSS = 0, MODE_FORWARD = 1, MODE_UPSTREAM = 2 };
+// MODE_FORWARD_STORE: MODE_FORWARD that also writes the fields psi;
+// MODE_UPSTREAM_STORED: MODE_UPSTREAM that reads psi instead of recomputing it.
+enum LedMode : int { MODE_LOSS = 0, MODE_FORWARD = 1, MODE_UPSTREAM = 2, MODE_FORWARD_STORE = 3, MODE_UPSTREAM_STORED = 4 };
 
 // Device error flags (bit set, OR-accumulated).
 enum : int { DERR_INDEX = 1, DERR_NONFINITE = 2, DERR_TIMEOUT = 4 };
@@ -31,6 +33,7 @@ struct LedArgs {
   const float* meas;    // [n_leds][m][m] measured intensities (MODE_LOSS)
   const float* dLdI;    // [B][m][m] upstream gradient of the intensities (MODE_UPSTREAM)
   float* I_out;         // [B][m][m] predicted intensities (MODE_FORWARD)
+  float2* psi;          // [B][m][m] low-res fields (written in MODE_FORWARD_STORE, read in MODE_UPSTREAM_STORED)
   const float* sp;      // scalar parameters, layout above
   const int4* slot;     // [B] batch slots: (LED, crop row offset n_row, crop col offset n_col, 0)
   float2* gbox;         // [B][W][W] per-LED object-gradient boxes, [slot][col][row]

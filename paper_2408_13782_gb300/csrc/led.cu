@@ -139,8 +139,10 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, M == 512 ? 1 : 2) led_kernel(co
   }
   cp_async_commit();  // group 1: O (needed by phase A)
   // group 2: this CTA's image rows (needed by phase B), arriving during phase A
+  const bool fwd_only = a.mode == MODE_FORWARD || a.mode == MODE_FORWARD_STORE;
+  const bool stored = a.mode == MODE_UPSTREAM_STORED;  // psi comes from memory: no inverse transforms
   const float* rows_src = a.mode == MODE_LOSS ? a.meas + ((size_t)led * M + y0) * M
-                        : a.mode == MODE_UPSTREAM ? a.dLdI + ((size_t)k * M + y0) * M : nullptr;
+                        : (a.mode == MODE_UPSTREAM || stored) ? a.dLdI + ((size_t)k * M + y0) * M : nullptr;
   if (rows_src)
     for (int q = tid; q < ROWS * M / 4; q += NT) cp_async16(ms + 4 * q, rows_src + 4 * q);
   cp_async_commit();
@@ -169,7 +171,7 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, M == 512 ? 1 : 2) led_kernel(co
   __syncthreads();     // O slice in shared memory
 
   // ---------------- phase A: column inverse transforms over ky -------------
-  for (int cb = c0; cb < c1; cb += NG) {
+  for (int cb = c0; cb < (stored ? c0 : c1); cb += NG) {
     const int c = cb + grp;
     const bool act = c < c1;
     const float2* Oc = Ob + (size_t)(act ? c - c0 : 0) * W + h;   // index by ky
@@ -201,28 +203,35 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, M == 512 ? 1 : 2) led_kernel(co
     const int rr = rb + grp;
     const bool act = rr < ROWS;
     const int yl = act ? rr : 0, y = y0 + yl;
-    for (int t = h + 1 + j; t < M - h; t += G) buf[bidx<M>(t)] = make_float2(0.f, 0.f);  // outside the box
-    for (int c = j; c < W; c += G) {
-      const int own = c / chunk, lc = c - own * chunk;
-      float2 v = make_float2(0.f, 0.f);
-      if (act) v = cluster.map_shared_rank(T, own)[lc * TS + y];
-      buf[bidx<M>((c - h) & (M - 1))] = v;
+    if (stored) {
+      for (int t = j; t < M; t += G)
+        buf[bidx<M>(t)] = act ? a.psi[((size_t)k * M + y) * M + t] : make_float2(0.f, 0.f);
+    } else {
+      for (int t = h + 1 + j; t < M - h; t += G) buf[bidx<M>(t)] = make_float2(0.f, 0.f);  // outside the box
+      for (int c = j; c < W; c += G) {
+        const int own = c / chunk, lc = c - own * chunk;
+        float2 v = make_float2(0.f, 0.f);
+        if (act) v = cluster.map_shared_rank(T, own)[lc * TS + y];
+        buf[bidx<M>((c - h) & (M - 1))] = v;
+      }
+      __syncwarp();
+      transform<M, +1>(buf, TW, tws, tw2, j);
     }
-    __syncwarp();
-    transform<M, +1>(buf, TW, tws, tw2, j);
     for (int t = j; t < M; t += G) {
-      const float2 psi = cscale(buf[bidx<M>(t)], inv_m2);
+      const float2 psi = stored ? buf[bidx<M>(t)] : cscale(buf[bidx<M>(t)], inv_m2);
       float2 gp = make_float2(0.f, 0.f);
       if (act) {
-        if (a.mode == MODE_FORWARD)
+        if (fwd_only) {
           a.I_out[((size_t)k * M + y) * M + t] = gam * (psi.x * psi.x + psi.y * psi.y);
-        else
+          if (a.mode == MODE_FORWARD_STORE) a.psi[((size_t)k * M + y) * M + t] = psi;
+        } else {
           gp = residual_pixel(psi, ms[yl * M + t], a.mode, a.loss, gam, sg, acc_loss, acc_g);
+        }
       }
       buf[bidx<M>(t)] = gp;
     }
     __syncwarp();
-    if (a.mode != MODE_FORWARD) {
+    if (!fwd_only) {
       transform<M, -1>(buf, TW, tws, tw2, j);
       if (act)
         for (int c = j; c < W; c += G) {
@@ -234,7 +243,7 @@ __global__ void __launch_bounds__(LedCfg<M>::NT, M == 512 ? 1 : 2) led_kernel(co
     }
   }
   cluster.sync();
-  if (a.mode == MODE_FORWARD) return;
+  if (fwd_only) return;
 
   // ---------------- phase C: column transforms over y, box gradients -------
   BoxAcc bacc;

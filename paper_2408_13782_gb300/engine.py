@@ -30,7 +30,8 @@ LOAD_INIT = 1
 
 # every symbol include/fpm.h declares
 EXPORTS = ("fpm_create", "fpm_set_hparams", "fpm_get_hparams", "fpm_load", "fpm_step", "fpm_run",
-           "fpm_epoch_loss", "fpm_profile_run", "fpm_forward", "fpm_backward", "fpm_get", "fpm_set", "fpm_set_object_field",
+           "fpm_epoch_loss", "fpm_profile_run", "fpm_forward", "fpm_backward",
+           "fpm_forward_fields", "fpm_backward_fields", "fpm_get", "fpm_set", "fpm_set_object_field",
            "fpm_state_size", "fpm_get_state", "fpm_set_state", "fpm_dims", "fpm_epoch_permutation",
            "fpm_gradients_static", "fpm_job_footprint", "fpm_server_create", "fpm_server_submit",
            "fpm_server_tick", "fpm_server_status", "fpm_server_result", "fpm_server_clock",
@@ -79,6 +80,8 @@ def lib():
         "fpm_profile_run": ([vp, vp, i32, i32, vp, ctypes.c_int64, vp, vp, vp], i32),
         "fpm_forward": ([vp, vp, i32, f32p], i32),
         "fpm_backward": ([vp, vp, i32, f32p, f32p, f32p, f32p, f32p, f32p, dp], i32),
+        "fpm_forward_fields": ([vp, vp, i32, f32p, f32p], i32),
+        "fpm_backward_fields": ([vp, vp, i32, f32p, f32p, f32p, f32p, f32p, f32p, f32p], i32),
         "fpm_get": ([vp, f32p, f32p, f32p, f32p, f32p], i32),
         "fpm_set": ([vp, f32p, f32p, f32p, f32p, f32p], i32),
         "fpm_set_object_field": ([vp, f32p], i32),

@@ -133,3 +133,26 @@ def test_function_against_central_differences(c3):
         fd = (L(O1, prm) - L(O2, prm)) / (2 * hO)
         ana = got["object"][r, col].real if part == "re" else got["object"][r, col].imag
         assert abs(ana - fd) <= 1e-3 * abs(fd) + 1e-7 * L0 / hO, (part, ana, fd)
+
+
+@pytest.mark.parametrize("m", [128, 512])
+def test_stored_fields_equal_recomputed_bitwise(m):
+    """Keeping psi between the passes gives the recompute path's gradients bit for bit
+    (same kernels up to where psi is formed)."""
+    from paper_2408_13782_gb300.autograd import fpm_intensities
+    from tests.gpu_common import multiparam_problem
+    c, I, g, prm, O = multiparam_problem(m=m, grid=5 if m < 512 else 3, seed=12)
+    dev = torch.device("cuda", 0)
+    eng = engine_for(g)
+    idx = [4, 0, 7, 2] if g.n_leds > 7 else [4, 0, 2]
+    w = torch.tensor(np.random.default_rng(2).normal(size=(len(idx), g.m, g.m)).astype(np.float32), device=dev)
+    out = {}
+    for store in (False, True):
+        leaves = _leaves(O, prm, dev)
+        I_pred = fpm_intensities(eng, idx, *leaves, store_fields=store)
+        (I_pred * w).sum().backward()
+        out[store] = (I_pred.detach().cpu().numpy(), _grads(leaves))
+    assert np.array_equal(out[False][0], out[True][0])
+    for k in ("object", "zernike", "gamma", "offset"):
+        assert np.array_equal(out[False][1][k], out[True][1][k]), k
+    assert out[False][1]["defocus"] == out[True][1]["defocus"]
