@@ -582,7 +582,7 @@ def reference_arm(args):
     print(json.dumps(out), flush=True)
 
 
-def main():
+def parse_args(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3000)
@@ -596,12 +596,17 @@ def main():
     ap.add_argument("--cpu-worker", default=None)
     ap.add_argument("--cpu-leds", type=int, default=16)
     ap.add_argument("--cpu-max-steps", type=int, default=10_000)
-    args = ap.parse_args()
+    args = ap.parse_args(argv)
+    if not args.cpu_worker and args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    return args
+
+
+def main():
+    args = parse_args()
     if args.cpu_worker:
         cpu_worker(args.cpu_worker, args.cpu_sample_s, args.cpu_leds, args.cpu_max_steps)
         return
-    if args.warmup < 3:
-        ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         reference_arm(args)
     else:
