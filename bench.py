@@ -125,14 +125,15 @@ def full_batches(n: int, B: int, n_steps: int, seed: int, first_epoch: int = 0) 
 def kernel_source_hash() -> str:
     import hashlib
     m = hashlib.sha256()
-    for f in ("led.cu", "device.cuh", "internal.h"):
+    for f in ("led.cu", "device.cuh", "pixel.cuh", "internal.h"):
         with open(os.path.join(ROOT, "paper_2408_13782_gb300", "csrc", f), "rb") as fh:
             m.update(fh.read())
     return m.hexdigest()[:16]
 
 
 def led_traffic_from_profile():
-    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged since."""
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged since
+    (led.cu and the headers it includes hash to the recorded value)."""
     path = os.path.join(ROOT, "profiles", "led_kernel_c2_1024_traffic.txt")
     if not os.path.exists(path):
         return None
