@@ -156,10 +156,13 @@ int fpm_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int32_t B, 
 /* Timing variant of fpm_run for profiling: the same steps, launched directly on the
  * engine's stream (not as a graph), with, before every step, a clear of flush_bytes of the device buffer `flush`
  * (nullable: no clear; a buffer larger than the L2 cache evicts the working set so
- * each step starts cold), and CUDA events on the engine's stream around each step
- * and each of its two kernels. Outputs (host, [n_steps] each, nullable): elapsed
- * ms of the per-LED kernel, of the update kernel and of the whole step (excluding
- * the clear). Waits for completion. The state advances exactly as with fpm_run. */
+ * each step starts cold), and CUDA events on the engine's stream. Outputs (host,
+ * [n_steps] each, nullable): elapsed ms of the per-LED kernel, of the update
+ * kernel and of the whole step (excluding the clear). With led_ms or update_ms
+ * given, events also separate the two kernels (so they run back to back); with
+ * both NULL only the step is bracketed and the update kernel starts early by
+ * programmatic dependent launch, as inside fpm_run. Waits for completion. The
+ * state advances exactly as with fpm_run. */
 int fpm_profile_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int32_t B,
                     void* flush, int64_t flush_bytes, float* led_ms, float* update_ms, float* step_ms);
 

@@ -683,6 +683,7 @@ int fpm_profile_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int
       destroy();
       return fail(h, FPM_ERR_CUDA, "event creation failed");
     }
+  const bool per_kernel = led_ms || update_ms;
   // Direct launches (events recorded inside captured graphs cannot be timed);
   // with a flush before every step the host stays ahead of the device, so
   // each timed window holds only device work.
@@ -692,8 +693,8 @@ int fpm_profile_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int
     if (flush) e = cudaMemsetAsync(flush, s & 0xff, (size_t)flush_bytes, h->st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s], h->st);
     if (e == cudaSuccess) e = launch_led_mode(h, led_args(h, idx, B, MODE_LOSS), false);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 1], h->st);
-    if (e == cudaSuccess) e = launch_update(upd_args(h, idx, B, s, h->losses + s, 0), h->st, false);
+    if (e == cudaSuccess && per_kernel) e = cudaEventRecord(ev[3 * s + 1], h->st);
+    if (e == cudaSuccess) e = launch_update(upd_args(h, idx, B, s, h->losses + s, 0), h->st, !per_kernel);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 2], h->st);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
@@ -704,8 +705,12 @@ int fpm_profile_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int
   h->t_host += n_steps;
   for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
     float a = 0.f, b = 0.f;
-    e = cudaEventElapsedTime(&a, ev[3 * s], ev[3 * s + 1]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[3 * s + 1], ev[3 * s + 2]);
+    if (per_kernel) {
+      e = cudaEventElapsedTime(&a, ev[3 * s], ev[3 * s + 1]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&b, ev[3 * s + 1], ev[3 * s + 2]);
+    } else {
+      e = cudaEventElapsedTime(&a, ev[3 * s], ev[3 * s + 2]);
+    }
     if (led_ms) led_ms[s] = a;
     if (update_ms) update_ms[s] = b;
     if (step_ms) step_ms[s] = a + b;

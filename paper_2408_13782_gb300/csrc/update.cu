@@ -33,11 +33,28 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
+// Scalar parameters handled per thread whose state is loaded before the wait
+// on the LED kernel (the rest, for very many LEDs, is loaded after it).
+constexpr int SP_PRE = 4;
+
 __device__ void scalar_update(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc2) {
   extern __shared__ double gsh[];  // [sp_size(n_leds)] gradients, then NPART totals
   const int n = a.n_leds, P = sp_size(n);
   double* tot = gsh + P;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+  // parameter state: written only by earlier update kernels, all complete here
+  float pw[SP_PRE], pm[SP_PRE], pv[SP_PRE];
+#pragma unroll
+  for (int k = 0; k < SP_PRE; ++k) {
+    const int i = tid + k * (int)blockDim.x;
+    pw[k] = pm[k] = pv[k] = 0.f;
+    if (!a.assemble && i < P) {
+      pw[k] = __ldcg(a.sp + i);
+      pm[k] = __ldcg(a.msp + i);
+      pv[k] = __ldcg(a.vsp + i);
+    }
+  }
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");  // partials of the LED kernel
   for (int i = tid; i < P; i += blockDim.x) gsh[i] = 0.0;
   __syncthreads();  // part holds one FP64 set per CTA of each slot's cluster
   // quantities shared by all LEDs (loss, Zernike, defocus): one warp each over
@@ -78,7 +95,7 @@ __device__ void scalar_update(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc
     for (int i = tid; i < P; i += blockDim.x) a.g_sc[i] = (float)gsh[i];
     return;
   }
-  for (int i = tid; i < P; i += blockDim.x) {
+  for (int k = 0, i = tid; i < P; ++k, i += blockDim.x) {
     float lr;
     unsigned bit;
     if (i < SP_DEFOCUS) { lr = a.lr_zern; bit = 1u << 1; }
@@ -86,7 +103,15 @@ __device__ void scalar_update(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc
     else if (i < sp_offset(n)) { lr = a.lr_gam; bit = 1u << 3; }
     else { lr = a.lr_off; bit = 1u << 4; }
     if (!(a.learn & bit)) continue;
-    float w = a.sp[i], m = a.msp[i], v = a.vsp[i];
+    float w, m, v;
+    if (k < SP_PRE) {
+      // a register array indexed by a loop counter: select, not index, to stay in registers
+#pragma unroll
+      for (int u = 0; u < SP_PRE; ++u)
+        if (u == k) { w = pw[u]; m = pm[u]; v = pv[u]; }
+    } else {
+      w = a.sp[i]; m = a.msp[i]; v = a.vsp[i];
+    }
     adam1(w, m, v, (float)gsh[i], lr * inv_bc1, inv_sqrt_bc2, a.b1, a.b2, a.eps);
     if (i >= sp_offset(n)) w = fminf(fmaxf(w, -a.offset_bound), a.offset_bound);
     a.sp[i] = w;
@@ -106,8 +131,7 @@ __global__ void __launch_bounds__(UPD_NT) update_kernel(const UpdArgs a) {
   // update has completed). The gradient boxes and partials come after it.
   const float2 bc = a.coef ? a.coef[a.step_off] : make_float2(1.f, 1.f);
   if (blockIdx.x == 0) {  // first block: the scalar parameters (longest dependency chain)
-    asm volatile("griddepcontrol.wait;\n" ::: "memory");
-    scalar_update(a, bc.x, bc.y);
+    scalar_update(a, bc.x, bc.y);  // waits on the LED kernel inside, after prefetching
     return;
   }
   if (!a.assemble && !(a.learn & 1u)) return;
@@ -150,19 +174,19 @@ __global__ void __launch_bounds__(UPD_NT) update_kernel(const UpdArgs a) {
       }
     }
     // sum of the covering boxes in batch order (adding zeros where a box
-    // does not reach this row), four loads in flight at a time
+    // does not reach this row), eight loads in flight at a time
     float2 g = make_float2(0.f, 0.f);
     int q = 0;
-    for (; q + 4 <= n_l; q += 4) {
-      float2 t[4];
+    for (; q + 8 <= n_l; q += 8) {
+      float2 t[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const int kk = lst[q + u];
         const int ry = y - corner[kk].y, cx = x - corner[kk].x;
         t[u] = (unsigned)ry < (unsigned)W ? a.gbox[((size_t)kk * W + cx) * W + ry] : make_float2(0.f, 0.f);
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) g = cadd(g, t[u]);
+      for (int u = 0; u < 8; ++u) g = cadd(g, t[u]);
     }
     for (; q < n_l; ++q) {
       const int kk = lst[q];

@@ -218,16 +218,20 @@ class Engine:
         self._check(lib().fpm_run(self._h, s.ctypes.data, s.shape[0], s.shape[1], dst))
         return losses if dst else None
 
-    def profile_run(self, schedule, flush=None):
+    def profile_run(self, schedule, flush=None, per_kernel=True):
         """Timed steps (see fpm_profile_run). flush: a CUDA tensor cleared before every
-        step, or None. Returns per-step ms of (per-LED kernel, update kernel, step)."""
+        step, or None. per_kernel=True returns per-step ms of (per-LED kernel, update
+        kernel, step), the kernels run back to back; per_kernel=False times only the
+        step, with the update kernel launched early as inside run(), and returns
+        (None, None, step)."""
         s = np.ascontiguousarray(np.asarray(schedule, np.int32))
         n = s.shape[0]
         led, upd, stp = (np.empty(n, np.float32) for _ in range(3))
         fb = flush.numel() * flush.element_size() if flush is not None else 0
         self._check(lib().fpm_profile_run(self._h, s.ctypes.data, n, s.shape[1], _ptr(flush), fb,
-                                          led.ctypes.data, upd.ctypes.data, stp.ctypes.data))
-        return led, upd, stp
+                                          led.ctypes.data if per_kernel else None,
+                                          upd.ctypes.data if per_kernel else None, stp.ctypes.data))
+        return (led, upd, stp) if per_kernel else (None, None, stp)
 
     def epoch_loss(self, reset=False) -> float:
         out = ctypes.c_double()

@@ -318,3 +318,23 @@ def test_errors_and_edge_cases():
     with pytest.raises(FpmError) as e:
         eng.step([0])
     assert e.value.code == -5
+
+
+def test_profiled_runs_equal_graph_run_bitwise():
+    """Both timing forms of fpm_profile_run advance the state exactly as fpm_run."""
+    c, I, g_t, prm, O = multiparam_problem(m=64, seed=32)
+    hp = orc.Hparams(lr=dict(object=0.5), learn=("object", "zernike", "defocus", "gamma", "offset"))
+    sched = np.stack(S.schedule(g_t.n_leds, 5, 1, seed=6)[:5])
+    outs = []
+    for mode in ("run", "per_kernel", "step"):
+        eng = engine_for(g_t)
+        hparams_to_engine(eng, hp)
+        eng.load(I, init=True)
+        if mode == "run":
+            eng.run(sched)
+        else:
+            led, upd, step = eng.profile_run(sched, per_kernel=(mode == "per_kernel"))
+            assert np.all(step > 0)
+        outs.append(eng.get_state())
+    assert np.array_equal(outs[0], outs[1])
+    assert np.array_equal(outs[0], outs[2])
