@@ -33,11 +33,16 @@ template <> struct LedCfg<64> { static constexpr int NT = 128; };
 template <> struct LedCfg<128> { static constexpr int NT = 256; };
 template <> struct LedCfg<256> { static constexpr int NT = 256; };
 template <> struct LedCfg<512> { static constexpr int NT = 256; };
+// At m = 256 the 16-CTA cluster uses 128-thread CTAs (the threads per LED of
+// the 8-CTA form): small CTAs pack two or three to an SM, so a whole 16-LED
+// batch of clusters is co-resident and no cluster has to share its SMs.
+template <int M, int C>
+constexpr int led_threads() { return (M == 256 && C == 16) ? 128 : LedCfg<M>::NT; }
 
 
 template <int M, int C>
 struct LedLayout {
-  static constexpr int NT = LedCfg<M>::NT;
+  static constexpr int NT = led_threads<M, C>();
   static constexpr int G = FftBuf<M>::G;           // threads per transform
   static constexpr int NG = NT / G;                // transform groups per CTA
   static constexpr int ROWS = M / C;               // image rows per CTA
@@ -82,7 +87,7 @@ __device__ __forceinline__ void transform(float2* buf, const FftTw<(M >= 256) ? 
 }
 
 template <int M, int C>
-__global__ void __launch_bounds__(LedCfg<M>::NT, M == 512 ? 1 : 2) led_kernel(const LedArgs a) {
+__global__ void __launch_bounds__(led_threads<M, C>(), M == 512 ? 1 : 2) led_kernel(const LedArgs a) {
   using L = LedLayout<M, C>;
   constexpr int NT = L::NT, G = L::G, NG = L::NG, ROWS = L::ROWS, TS = L::TS, FS = L::FS;
   constexpr int NW = L::NW;
@@ -298,7 +303,7 @@ template <int M, int C>
 static int max_active_clusters(int W) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(C, 1, 1);
-  cfg.blockDim = dim3(LedCfg<M>::NT, 1, 1);
+  cfg.blockDim = dim3(led_threads<M, C>(), 1, 1);
   cfg.dynamicSmemBytes = LedLayout<M, C>::bytes(W);
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -315,8 +320,8 @@ static int max_active_clusters(int W) {
   return n;
 }
 
-// m = 256: a 16-CTA cluster (a non-portable size) only when the device can
-// hold 16 of them at once (a whole 16-LED batch in one wave), else 8.
+// m = 256: a 16-CTA cluster of 128-thread CTAs (a non-portable size) when the
+// device can hold 16 of them at once (a whole 16-LED batch in one wave), else 8.
 // m = 512 needs 16 (shared memory per CTA); 0 if the device cannot run it.
 int led_choose_cluster(int m, int W) {
   if (m == 512) {

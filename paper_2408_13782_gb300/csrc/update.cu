@@ -8,9 +8,9 @@
 // no-op) gathers the per-LED gradient boxes in batch order - a fixed-order
 // sum, so results are bitwise reproducible - and takes one Adam step on its
 // real and imaginary parts. One CTA per spectrum column of the region.
-// Scalars: the first CTA reduces the per-CTA FP64 partials in a fixed order,
-// forms the gradients of the Zernike coefficients, defocus, intensity factors
-// and LED offsets, and updates all of them (every element, every step).
+// Scalars: 17 CTAs reduce the per-CTA FP64 partials in a fixed order, one per
+// quantity shared by all LEDs and one for the per-LED parameters, and update
+// all of them (every element, every step).
 #include <cmath>
 
 #include "device.cuh"
@@ -33,41 +33,86 @@ __device__ __forceinline__ double warp_sum_d(double v) {
   return v;
 }
 
-// Scalar parameters handled per thread whose state is loaded before the wait
-// on the LED kernel (the rest, for very many LEDs, is loaded after it).
-constexpr int SP_PRE = 4;
+// The scalar parameters are updated by NSC CTAs in parallel: CTA q < 16 owns
+// one quantity shared by all LEDs (q = 0 the loss, 1..14 the Zernike
+// coefficients, 15 the defocus) and sums it over all B x C per-CTA partials
+// with a fixed tree; CTA 16 owns the per-LED intensity factors and offsets,
+// each the sum of its slot's C partials in rank order. Every parameter takes
+// an Adam step every step (zero gradient for LEDs outside the batch).
+constexpr int NSC = 17;
+constexpr int SP_PRE = 4;  // per-LED parameters per thread whose state is loaded before the wait
 
-__device__ void scalar_update(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc2) {
-  extern __shared__ double gsh[];  // [sp_size(n_leds)] gradients, then NPART totals
-  const int n = a.n_leds, P = sp_size(n);
-  double* tot = gsh + P;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-  // parameter state: written only by earlier update kernels, all complete here
+__device__ __forceinline__ bool learned(const UpdArgs& a, int i) {
+  const unsigned bit = i < SP_DEFOCUS ? 1u << 1 : i == SP_DEFOCUS ? 1u << 2 : i < sp_offset(a.n_leds) ? 1u << 3 : 1u << 4;
+  return (a.learn & bit) != 0;
+}
+__device__ __forceinline__ float lr_of(const UpdArgs& a, int i) {
+  return i < SP_DEFOCUS ? a.lr_zern : i == SP_DEFOCUS ? a.lr_def : i < sp_offset(a.n_leds) ? a.lr_gam : a.lr_off;
+}
+
+// Adam on scalar i with FP64 gradient g; offsets are clamped to the box bound.
+__device__ __forceinline__ void scalar_adam(const UpdArgs& a, int i, float w, float m, float v, double g,
+                                            float inv_bc1, float inv_sqrt_bc2) {
+  adam1(w, m, v, (float)g, lr_of(a, i) * inv_bc1, inv_sqrt_bc2, a.b1, a.b2, a.eps);
+  if (i >= sp_offset(a.n_leds)) w = fminf(fmaxf(w, -a.offset_bound), a.offset_bound);
+  a.sp[i] = w;
+  a.msp[i] = m;
+  a.vsp[i] = v;
+}
+
+// CTA q < 16: one shared quantity.
+__device__ void shared_scalar(const UpdArgs& a, int q, float inv_bc1, float inv_sqrt_bc2) {
+  __shared__ double wsum[UPD_NT / 32];
+  const int P = q == 0 ? P_LOSS : q <= 14 ? P_ZERN + q - 1 : P_DEFOCUS;
+  const int i = q == 0 ? -1 : q <= 14 ? SP_ZERN + q - 1 : SP_DEFOCUS;  // parameter index
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float w = 0.f, m = 0.f, v = 0.f;
+  if (tid == 0 && i >= 0 && !a.assemble) {  // written only by earlier update kernels
+    w = __ldcg(a.sp + i);
+    m = __ldcg(a.msp + i);
+    v = __ldcg(a.vsp + i);
+  }
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");  // partials of the LED kernel
+  const int nparts = a.B * a.C;
+  double s = 0.0;
+  for (int e = tid; e < nparts; e += blockDim.x) s += a.part[(size_t)e * NPART + P];
+  s = warp_sum_d(s);
+  if (lane == 0) wsum[warp] = s;
+  __syncthreads();
+  if (tid != 0) return;
+  double tot = 0.0;
+  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += wsum[k];
+  if (q == 0) {
+    *a.loss_slot = tot;
+    if (!a.assemble) *a.epoch_loss += tot;
+    if (!isfinite(tot)) atomicOr(a.err, DERR_NONFINITE);
+    return;
+  }
+  if (a.assemble) {
+    a.g_sc[i] = (float)tot;
+    return;
+  }
+  if (learned(a, i)) scalar_adam(a, i, w, m, v, tot, inv_bc1, inv_sqrt_bc2);
+}
+
+// CTA 16: the per-LED intensity factors and offsets of every LED.
+__device__ void led_scalars(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc2) {
+  extern __shared__ double gl[];  // [3 n_leds]: gamma, then (dy, dx) per LED
+  const int n = a.n_leds, tid = threadIdx.x;
   float pw[SP_PRE], pm[SP_PRE], pv[SP_PRE];
 #pragma unroll
   for (int k = 0; k < SP_PRE; ++k) {
-    const int i = tid + k * (int)blockDim.x;
+    const int i = SP_GAMMA + tid + k * (int)blockDim.x;
     pw[k] = pm[k] = pv[k] = 0.f;
-    if (!a.assemble && i < P) {
+    if (!a.assemble && i < sp_size(n)) {
       pw[k] = __ldcg(a.sp + i);
       pm[k] = __ldcg(a.msp + i);
       pv[k] = __ldcg(a.vsp + i);
     }
   }
-  asm volatile("griddepcontrol.wait;\n" ::: "memory");  // partials of the LED kernel
-  for (int i = tid; i < P; i += blockDim.x) gsh[i] = 0.0;
-  __syncthreads();  // part holds one FP64 set per CTA of each slot's cluster
-  // quantities shared by all LEDs (loss, Zernike, defocus): one warp each over
-  // the B x C per-CTA partials, fixed per-lane order and a fixed shuffle tree
-  const int nparts = a.B * a.C;
-  for (int qi = warp; qi < 16; qi += nwarp) {
-    const int q = qi == 0 ? P_LOSS : (qi <= 14 ? P_ZERN + qi - 1 : P_DEFOCUS);
-    double s = 0.0;
-    for (int e = lane; e < nparts; e += 32) s += a.part[(size_t)e * NPART + q];
-    s = warp_sum_d(s);
-    if (lane == 0) tot[q] = s;
-  }
-  // per-LED quantities: the C ranks of each slot in rank order
+  for (int j = tid; j < 3 * n; j += blockDim.x) gl[j] = 0.0;
+  asm volatile("griddepcontrol.wait;\n" ::: "memory");
+  __syncthreads();
   for (int kk = tid; kk < a.B; kk += blockDim.x) {
     const int led = a.slot[kk].x;
     double sg = 0.0, sy = 0.0, sx = 0.0;
@@ -77,32 +122,18 @@ __device__ void scalar_update(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc
       sy += p[P_DY];
       sx += p[P_DX];
     }
-    gsh[SP_GAMMA + led] = sg;
-    gsh[sp_offset(n) + 2 * led] = sy;
-    gsh[sp_offset(n) + 2 * led + 1] = sx;
+    gl[led] = sg;
+    gl[n + 2 * led] = sy;
+    gl[n + 2 * led + 1] = sx;
   }
   __syncthreads();
-  if (tid < 14) gsh[SP_ZERN + tid] = tot[P_ZERN + tid];
-  if (tid == 14) gsh[SP_DEFOCUS] = tot[P_DEFOCUS];
-  __syncthreads();
-  if (tid == 0) {
-    const double L = tot[P_LOSS];
-    *a.loss_slot = L;
-    if (!a.assemble) *a.epoch_loss += L;
-    if (!isfinite(L)) atomicOr(a.err, DERR_NONFINITE);
-  }
-  if (a.assemble) {
-    for (int i = tid; i < P; i += blockDim.x) a.g_sc[i] = (float)gsh[i];
-    return;
-  }
-  for (int k = 0, i = tid; i < P; ++k, i += blockDim.x) {
-    float lr;
-    unsigned bit;
-    if (i < SP_DEFOCUS) { lr = a.lr_zern; bit = 1u << 1; }
-    else if (i == SP_DEFOCUS) { lr = a.lr_def; bit = 1u << 2; }
-    else if (i < sp_offset(n)) { lr = a.lr_gam; bit = 1u << 3; }
-    else { lr = a.lr_off; bit = 1u << 4; }
-    if (!(a.learn & bit)) continue;
+  for (int k = 0, j = tid; j < 3 * n; ++k, j += blockDim.x) {
+    const int i = SP_GAMMA + j;
+    if (a.assemble) {
+      a.g_sc[i] = (float)gl[j];
+      continue;
+    }
+    if (!learned(a, i)) continue;
     float w, m, v;
     if (k < SP_PRE) {
       // a register array indexed by a loop counter: select, not index, to stay in registers
@@ -112,11 +143,7 @@ __device__ void scalar_update(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc
     } else {
       w = a.sp[i]; m = a.msp[i]; v = a.vsp[i];
     }
-    adam1(w, m, v, (float)gsh[i], lr * inv_bc1, inv_sqrt_bc2, a.b1, a.b2, a.eps);
-    if (i >= sp_offset(n)) w = fminf(fmaxf(w, -a.offset_bound), a.offset_bound);
-    a.sp[i] = w;
-    a.msp[i] = m;
-    a.vsp[i] = v;
+    scalar_adam(a, i, w, m, v, gl[j], inv_bc1, inv_sqrt_bc2);
   }
 }
 
@@ -130,12 +157,13 @@ __global__ void __launch_bounds__(UPD_NT) update_kernel(const UpdArgs a) {
   // kernel only reads O, and lets this kernel start only after the previous
   // update has completed). The gradient boxes and partials come after it.
   const float2 bc = a.coef ? a.coef[a.step_off] : make_float2(1.f, 1.f);
-  if (blockIdx.x == 0) {  // first block: the scalar parameters (longest dependency chain)
-    scalar_update(a, bc.x, bc.y);  // waits on the LED kernel inside, after prefetching
+  if (blockIdx.x < NSC) {  // the scalar parameters (the longest dependency chain)
+    if (blockIdx.x < 16) shared_scalar(a, blockIdx.x, bc.x, bc.y);
+    else led_scalars(a, bc.x, bc.y);
     return;
   }
   if (!a.assemble && !(a.learn & 1u)) return;
-  const int x = a.x_lo + (int)blockIdx.x - 1;
+  const int x = a.x_lo + (int)blockIdx.x - NSC;
   const int W = a.W;
   const int2 span = a.span[x];
   for (int kk = threadIdx.x; kk < a.B; kk += blockDim.x) {
@@ -211,9 +239,9 @@ cudaError_t update_prepare() {
 }
 
 cudaError_t launch_update(const UpdArgs& a, cudaStream_t s, bool pdl) {
-  const size_t smem = sizeof(double) * ((size_t)sp_size(a.n_leds) + NPART);
+  const size_t smem = sizeof(double) * 3 * (size_t)a.n_leds;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(a.n_cols + 1), 1, 1);
+  cfg.gridDim = dim3((unsigned)(a.n_cols + NSC), 1, 1);
   cfg.blockDim = dim3(UPD_NT, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
