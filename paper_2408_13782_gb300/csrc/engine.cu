@@ -45,7 +45,7 @@ struct fpm_handle {
   // device state
   float2 *Ot = nullptr, *mO = nullptr, *vO = nullptr, *tmp = nullptr, *tmp2 = nullptr;
   float2 *tw_m = nullptr, *tw_N = nullptr;
-  float *meas = nullptr, *sp = nullptr, *msp = nullptr, *vsp = nullptr, *gsc = nullptr, *fbuf = nullptr;
+  float *meas = nullptr, *amp = nullptr, *sp = nullptr, *msp = nullptr, *vsp = nullptr, *gsc = nullptr, *fbuf = nullptr;
   int2 *nint = nullptr, *span = nullptr;
   float2* gbox = nullptr;
   double* part = nullptr;
@@ -136,7 +136,7 @@ void free_all(fpm_handle* h) {
   destroy_graphs(h);
   void* dev[] = {h->Ot, h->mO, h->vO, h->tmp, h->tmp2, h->tw_m, h->tw_N, h->meas, h->sp, h->msp, h->vsp,
                  h->gsc, h->fbuf, h->nint, h->span, h->gbox, h->part, h->sched, h->losses, h->epoch,
-                 h->coef, h->err, h->gconst, h->gscr};
+                 h->coef, h->err, h->gconst, h->gscr, h->amp};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (h->h_err) cudaFreeHost(h->h_err);
@@ -260,7 +260,9 @@ void fill_slots(const fpm_handle* h, const int32_t* idx, int count, int4* dst) {
 LedArgs led_args(fpm_handle* h, const int4* slot_dev, int B, int mode) {
   LedArgs a{};
   a.Ot = h->Ot;
-  a.meas = h->meas;
+  // the FFT form's amplitude loss reads the amplitudes computed at load
+  a.meas_is_amp = mode == MODE_LOSS && h->hp.loss == FPM_LOSS_AMPLITUDE && h->hp.precision == FPM_PRECISION_FP32_FFT;
+  a.meas = a.meas_is_amp ? h->amp : h->meas;
   a.sp = h->sp;
   a.slot = slot_dev;
   a.gbox = h->gbox;
@@ -497,6 +499,7 @@ int fpm_create(const fpm_geometry* g, float R, int32_t upsample, void* cuda_stre
             ck(cudaMalloc(&h->tw_m, sizeof(float2) * h->m), "alloc tw") &&
             ck(cudaMalloc(&h->tw_N, sizeof(float2) * h->N), "alloc tw") &&
             ck(cudaMalloc(&h->meas, sizeof(float) * (size_t)h->n * h->m * h->m), "alloc stack") &&
+            ck(cudaMalloc(&h->amp, sizeof(float) * (size_t)h->n * h->m * h->m), "alloc stack") &&
             ck(cudaMalloc(&h->sp, sizeof(float) * P), "alloc params") &&
             ck(cudaMalloc(&h->msp, sizeof(float) * P), "alloc params") &&
             ck(cudaMalloc(&h->vsp, sizeof(float) * P), "alloc params") &&
@@ -601,6 +604,7 @@ int fpm_load(fpm_handle* h, const float* stack, int32_t flags) {
   int rc = enter(h);
   if (rc) return rc;
   CK(h, cudaMemcpyAsync(h->meas, stack, sizeof(float) * (size_t)h->n * h->m * h->m, cudaMemcpyDefault, h->st));
+  CK(h, launch_amplitude(h->meas, h->amp, (size_t)h->n * h->m * h->m, h->st));
   if (flags & FPM_LOAD_INIT) {
     CK(h, launch_upsample_centre(h->meas + (size_t)h->centre * h->m * h->m, h->m, h->s, h->tmp, h->st));
     if ((rc = object_from_field(h))) return rc;

@@ -10,6 +10,8 @@
 #include "device.cuh"
 #include "internal.h"
 
+#include <algorithm>
+
 namespace fpmk {
 
 __global__ void upsample_centre_kernel(const float* __restrict__ I, int m, int s, float2* __restrict__ out) {
@@ -87,6 +89,19 @@ __global__ void transpose_kernel(const float2* __restrict__ in, float2* __restri
     const int x = bx + i, y = by + threadIdx.x;
     if (y < N && x < N) out[(size_t)x * N + y] = tile[threadIdx.x][i];
   }
+}
+
+// Measured amplitude sqrt(max(I, 0)) of the whole stack (the amplitude loss,
+// Section 2.2, compares |psi| with it), computed once per load.
+__global__ void amplitude_kernel(const float* I, float* amp, size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    amp[i] = sqrtf(fmaxf(I[i], 0.f));
+}
+
+cudaError_t launch_amplitude(const float* I, float* amp, size_t n, cudaStream_t st) {
+  const size_t blocks = std::min<size_t>((n + 255) / 256, 152 * 16);
+  amplitude_kernel<<<(unsigned)blocks, 256, 0, st>>>(I, amp, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_upsample_centre(const float* I, int m, int s, float2* out, cudaStream_t st) {

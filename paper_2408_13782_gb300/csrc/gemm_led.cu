@@ -520,7 +520,7 @@ __global__ void __launch_bounds__(GT, 1) gemm_led_kernel(const GemmArgs g) {
   }
 
   if (ok && a.mode != MODE_FORWARD)
-    write_partials(acc_loss, acc_g, bacc, a.mode == MODE_LOSS && a.loss == 0, sg, red, dsum, zmt,
+    write_partials(acc_loss, acc_g, bacc, a.mode == MODE_LOSS && a.loss == 0, sg, red, reinterpret_cast<float*>(dsum), zmt,
                    a.part + (size_t)k * NPART);
   tc::fence_before_sync();
   __syncthreads();

@@ -30,7 +30,7 @@ constexpr int MAX_BATCH = 1024;
 
 struct LedArgs {
   const float2* Ot;     // [N][N] spectrum, column-major: element (row y, col x) at Ot[x * N + y]
-  const float* meas;    // [n_leds][m][m] measured intensities (MODE_LOSS)
+  const float* meas;    // [n_leds][m][m] measured intensities (MODE_LOSS), or amplitudes if meas_is_amp
   const float* dLdI;    // [B][m][m] upstream gradient of the intensities (MODE_UPSTREAM)
   float* I_out;         // [B][m][m] predicted intensities (MODE_FORWARD)
   float2* psi;          // [B][m][m] low-res fields (written in MODE_FORWARD_STORE, read in MODE_UPSTREAM_STORED)
@@ -42,6 +42,7 @@ struct LedArgs {
   int N, n_leds, B, h, W;
   float R, Rinv, inv_lambda, dk2;
   int hard_edge, loss, mode;
+  int meas_is_amp;      // meas holds sqrt(max(I, 0)) (amplitude loss in MODE_LOSS)
   int* err;
 };
 
@@ -117,6 +118,7 @@ cudaError_t launch_led_gemm(const GemmPlan& p, const LedArgs& a, const unsigned 
 cudaError_t update_prepare();
 
 // Field kernels (initialisation, object transforms, layout changes).
+cudaError_t launch_amplitude(const float* I, float* amp, size_t n, cudaStream_t st);
 cudaError_t launch_upsample_centre(const float* I, int m, int s, float2* out_rowmajor, cudaStream_t st);
 cudaError_t launch_fft_rows(float2* data, int N, const float2* twN, int dir, cudaStream_t st);
 cudaError_t launch_fft_cols_centre(const float2* rows, float2* Ot, int N, const float2* twN, float scale,

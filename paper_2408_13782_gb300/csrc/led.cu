@@ -51,10 +51,14 @@ struct LedLayout {
   static constexpr int NW = NT / 32;
   static constexpr int NPOLY = 40;                 // K[15], Dx[10], Dy[10], pad
   static constexpr int NTW2 = M >= 256 ? 15 * 16 : 0;  // second-pass twiddles (M = 256, 512)
+  // Phase A pushes its results into the row owners' staging rows (posted
+  // remote stores) instead of phase B pulling them; m = 512 lacks the room.
+  static constexpr bool PUSH = M <= 256;
   static size_t bytes(int W) {
     const int chunk = (W + C - 1) / C;
     return sizeof(float) * (size_t)ROWS * M +
-           sizeof(float2) * ((size_t)chunk * TS + (size_t)NG * FS + M + NTW2 + (size_t)chunk * W) +
+           sizeof(float2) * ((size_t)chunk * TS + (size_t)NG * FS + M + NTW2 + (size_t)chunk * W +
+                             (PUSH ? (size_t)ROWS * W : 0)) +
            sizeof(float) * (NPOLY + 14 * 15 + 2 + (size_t)NW * NACC) + sizeof(double) * 16;
   }
 };
@@ -107,7 +111,8 @@ __global__ void __launch_bounds__(led_threads<M, C>(), M == 512 ? 1 : 2) led_ker
   float2* tws = fb + NG * FS;                             // [M] twiddle table
   float2* tw2 = tws + M;                                  // [15][16] second-pass twiddles (M = 256)
   float2* Ob = tw2 + L::NTW2;                             // [chunk][W] O on this CTA's box columns
-  float* poly = reinterpret_cast<float*>(Ob + (size_t)chunk * W);  // K[15] Dx[10] Dy[10]
+  float2* Rw = Ob + (size_t)chunk * W;                    // [ROWS][W] this CTA's rows of T (push form)
+  float* poly = reinterpret_cast<float*>(Rw + (L::PUSH ? (size_t)ROWS * W : 0));  // K[15] Dx[10] Dy[10]
   float* zmt = poly + L::NPOLY;                           // [14 * 15] Zernike -> monomial table
   float* red = zmt + 14 * 15 + 2;                         // [NW][NACC]
   double* dsum = reinterpret_cast<double*>(red + NW * NACC);  // [16] (8-byte aligned: float counts are even)
@@ -194,7 +199,12 @@ __global__ void __launch_bounds__(led_threads<M, C>(), M == 512 ? 1 : 2) led_ker
     __syncwarp();
     transform<M, +1>(buf, TW, tws, tw2, j);
     if (act)
-      for (int t = j; t < M; t += G) T[(c - c0) * TS + t] = buf[bidx<M>(t)];
+      for (int t = j; t < M; t += G) {
+        if constexpr (L::PUSH)  // row t of T belongs to CTA t / ROWS
+          cluster.map_shared_rank(Rw, t / ROWS)[(t % ROWS) * W + c] = buf[bidx<M>(t)];
+        else
+          T[(c - c0) * TS + t] = buf[bidx<M>(t)];
+      }
     __syncwarp();
   }
   cp_async_wait<0>();  // image rows
@@ -213,27 +223,62 @@ __global__ void __launch_bounds__(led_threads<M, C>(), M == 512 ? 1 : 2) led_ker
         buf[bidx<M>(t)] = act ? a.psi[((size_t)k * M + y) * M + t] : make_float2(0.f, 0.f);
     } else {
       for (int t = h + 1 + j; t < M - h; t += G) buf[bidx<M>(t)] = make_float2(0.f, 0.f);  // outside the box
-      for (int c = j; c < W; c += G) {
-        const int own = c / chunk, lc = c - own * chunk;
-        float2 v = make_float2(0.f, 0.f);
-        if (act) v = cluster.map_shared_rank(T, own)[lc * TS + y];
-        buf[bidx<M>((c - h) & (M - 1))] = v;
+      if constexpr (L::PUSH) {
+        for (int c = j; c < W; c += G)
+          buf[bidx<M>((c - h) & (M - 1))] = act ? Rw[yl * W + c] : make_float2(0.f, 0.f);
+      } else
+      // remote loads from the owning CTAs, eight in flight before any is stored
+      for (int cb = j; cb < W; cb += 8 * G) {
+        float2 v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int c = cb + u * G;
+          v[u] = make_float2(0.f, 0.f);
+          if (act && c < W) {
+            const int own = c / chunk, lc = c - own * chunk;
+            v[u] = cluster.map_shared_rank(T, own)[lc * TS + y];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int c = cb + u * G;
+          if (c < W) buf[bidx<M>((c - h) & (M - 1))] = v[u];
+        }
       }
       __syncwarp();
       transform<M, +1>(buf, TW, tws, tw2, j);
     }
-    for (int t = j; t < M; t += G) {
-      const float2 psi = stored ? buf[bidx<M>(t)] : cscale(buf[bidx<M>(t)], inv_m2);
-      float2 gp = make_float2(0.f, 0.f);
-      if (act) {
-        if (fwd_only) {
-          a.I_out[((size_t)k * M + y) * M + t] = gam * (psi.x * psi.x + psi.y * psi.y);
-          if (a.mode == MODE_FORWARD_STORE) a.psi[((size_t)k * M + y) * M + t] = psi;
-        } else {
-          gp = residual_pixel(psi, ms[yl * M + t], a.mode, a.loss, gam, sg, acc_loss, acc_g);
-        }
+    // residual per pixel; the loop for each loss form is branch-free so that
+    // the pixels of a thread interleave
+    const float sc = stored ? 1.f : inv_m2;
+    if (!act) {
+      for (int t = j; t < M; t += G) buf[bidx<M>(t)] = make_float2(0.f, 0.f);
+    } else if (fwd_only) {
+      for (int t = j; t < M; t += G) {
+        const float2 psi = cscale(buf[bidx<M>(t)], sc);
+        a.I_out[((size_t)k * M + y) * M + t] = gam * (psi.x * psi.x + psi.y * psi.y);
+        if (a.mode == MODE_FORWARD_STORE) a.psi[((size_t)k * M + y) * M + t] = psi;
+        buf[bidx<M>(t)] = make_float2(0.f, 0.f);
       }
-      buf[bidx<M>(t)] = gp;
+    } else if (a.mode == MODE_LOSS && a.loss == 0 && a.meas_is_amp) {
+#pragma unroll 4
+      for (int t = j; t < M; t += G)
+        buf[bidx<M>(t)] = residual_amp_pixel(cscale(buf[bidx<M>(t)], sc), ms[yl * M + t], sg, acc_loss, acc_g);
+    } else if (a.mode == MODE_LOSS && a.loss == 0) {
+#pragma unroll 4
+      for (int t = j; t < M; t += G)
+        buf[bidx<M>(t)] = residual_pixel(cscale(buf[bidx<M>(t)], sc), ms[yl * M + t], MODE_LOSS, 0, gam, sg,
+                                         acc_loss, acc_g);
+    } else if (a.mode == MODE_LOSS) {
+#pragma unroll 4
+      for (int t = j; t < M; t += G)
+        buf[bidx<M>(t)] = residual_pixel(cscale(buf[bidx<M>(t)], sc), ms[yl * M + t], MODE_LOSS, 1, gam, sg,
+                                         acc_loss, acc_g);
+    } else {
+#pragma unroll 4
+      for (int t = j; t < M; t += G)
+        buf[bidx<M>(t)] = residual_pixel(cscale(buf[bidx<M>(t)], sc), ms[yl * M + t], MODE_UPSTREAM, 0, gam, sg,
+                                         acc_loss, acc_g);
     }
     __syncwarp();
     if (!fwd_only) {
@@ -277,7 +322,7 @@ __global__ void __launch_bounds__(led_threads<M, C>(), M == 512 ? 1 : 2) led_ker
   }
 
   // ---------------- reduction of the scalar partials -----------------------
-  write_partials(acc_loss, acc_g, bacc, a.mode == MODE_LOSS && a.loss == 0, sg, red, dsum, zmt,
+  write_partials(acc_loss, acc_g, bacc, a.mode == MODE_LOSS && a.loss == 0, sg, red, reinterpret_cast<float*>(dsum), zmt,
                  a.part + ((size_t)k * C + rank) * NPART);
 }
 

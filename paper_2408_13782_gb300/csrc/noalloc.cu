@@ -61,8 +61,10 @@ int setup_device(int dev, unsigned char** out) {
     cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess)
       return fail_static(FPM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    // the attributes do not depend on the box width (each launch asks for the
+    // shared memory its box needs; a call whose box does not fit is rejected)
     for (int m : {32, 64, 128, 256}) {
-      e = led_prepare(m, static_cluster(m), m - 1);
+      e = led_prepare(m, static_cluster(m), 1);
       if (e != cudaSuccess)
         return fail_static(FPM_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
     }

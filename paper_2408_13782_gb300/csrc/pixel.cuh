@@ -32,6 +32,18 @@ __device__ __forceinline__ float2 residual_pixel(float2 psi, float v, int mode, 
   return cscale(psi, 2.f * gam * v);
 }
 
+// Amplitude-loss residual with the measured amplitude amp = sqrt(max(I, 0))
+// given (the same arithmetic as residual_pixel's amplitude branch).
+__device__ __forceinline__ float2 residual_amp_pixel(float2 psi, float amp, float sg, float& acc_loss, float& acc_g) {
+  const float mag2 = psi.x * psi.x + psi.y * psi.y;
+  const float rinv = mag2 > 0.f ? rsqrtf(mag2) : 0.f;
+  const float mag = mag2 * rinv;
+  const float res = sg * mag - amp;
+  acc_loss = fmaf(res, res, acc_loss);
+  acc_g = fmaf(res, mag, acc_g);
+  return cscale(psi, 2.f * res * sg * rinv);  // 0 where psi = 0
+}
+
 struct BoxAcc {
   float m[15];  // monomial moments sum t(p) x^a y^b
   float def, dy, dx;
@@ -98,12 +110,14 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 constexpr int NACC = 20;
 enum : int { A_LOSS = 0, A_GAMMA = 1, A_MONO = 2, A_DEF = 17, A_DY = 18, A_DX = 19 };
 
-// Reduce the block's accumulators and write its FP64 partials (NPART values):
-// FP32 within threads and warps, FP64 across warps; the monomial moments become
-// Zernike gradients through the table zmt (row j-2 = Z_j). red: [nwarps][NACC]
-// floats, dsum: [16] doubles of shared memory. Called by every thread.
+// Reduce the block's accumulators and write its partials (NPART values, stored
+// as FP64 for the update kernel's FP64 sums over all CTAs of the batch). The
+// block's own sums (a few thousand pixels) stay in FP32: FP64 arithmetic is
+// slow on this part. The monomial moments become Zernike gradients through
+// the table zmt (row j-2 = Z_j). red: [nwarps][NACC], fsum: [16] floats of
+// shared memory. Called by every thread.
 __device__ __forceinline__ void write_partials(float acc_loss, float acc_g, const BoxAcc& b, bool amp_loss_gamma,
-                                               float sg, float* red, double* dsum, const float* zmt, double* out) {
+                                               float sg, float* red, float* fsum, const float* zmt, double* out) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, nw = blockDim.x >> 5;
   float vals[NACC];
   vals[A_LOSS] = acc_loss;
@@ -119,19 +133,20 @@ __device__ __forceinline__ void write_partials(float acc_loss, float acc_g, cons
     if (lane == 0) red[warp * NACC + q] = s;
   }
   __syncthreads();
-  double tot = 0.0;
+  float tot = 0.f;
   if (tid < NACC)
-    for (int w = 0; w < nw; ++w) tot += (double)red[w * NACC + tid];
-  if (tid >= A_MONO && tid < A_MONO + 15) dsum[tid - A_MONO] = tot;
+    for (int w = 0; w < nw; ++w) tot += red[w * NACC + tid];
+  if (tid >= A_MONO && tid < A_MONO + 15) fsum[tid - A_MONO] = tot;
   __syncthreads();
   if (tid == A_LOSS) out[P_LOSS] = tot;
-  if (tid == A_GAMMA) out[P_GAMMA] = amp_loss_gamma ? tot / (double)sg : tot;
+  if (tid == A_GAMMA) out[P_GAMMA] = amp_loss_gamma ? (double)(tot / sg) : (double)tot;
   if (tid == A_DEF) out[P_DEFOCUS] = tot;
   if (tid == A_DY) out[P_DY] = tot;
   if (tid == A_DX) out[P_DX] = tot;
   if (tid < 14) {  // dL/dc_j = sum_m (Z_j)_m * (sum_p t(p) mo_m(p))
-    double z = 0.0;
-    for (int m = 0; m < 15; ++m) z += (double)zmt[tid * 15 + m] * dsum[m];
+    float z = 0.f;
+#pragma unroll
+    for (int m = 0; m < 15; ++m) z = fmaf(zmt[tid * 15 + m], fsum[m], z);
     out[P_ZERN + tid] = z;
   }
 }

@@ -182,7 +182,7 @@ int64_t fpm_job_footprint(const fpm_job_desc* d) {
   const int64_t W = 2 * h + 1, C = m >= 256 ? 16 : (m == 128 ? 8 : (m == 64 ? 4 : 2));  // upper bound
   const int64_t steps = n / B + 1;
   int64_t bytes = 5 * N * N * 8          // O, Adam m and v, two transform buffers
-                  + n * m * m * 4        // measured stack
+                  + 2 * n * m * m * 4    // measured stack and its amplitudes
                   + (m + N) * 8          // twiddles
                   + 4 * (15 + 3 * n) * 4 // parameters, moments, gradient
                   + n * 8 + N * 8        // LED table, update spans
