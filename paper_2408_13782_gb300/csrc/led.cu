@@ -68,6 +68,10 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
@@ -124,8 +128,10 @@ __global__ void __launch_bounds__(led_threads<M, C>(), M == 512 ? 1 : 2) led_ker
     if (tid == 0 && rank == 0) atomicOr(a.err, DERR_INDEX);
     return;
   }
-  for (int t = tid; t < M; t += NT) tws[t] = a.tw[t];
-  for (int t = tid; t < 14 * 15; t += NT) zmt[t] = zern_mono_table()[t];
+  // constant tables by cp.async (group 0): no stall before the O copies below
+  for (int t = tid; t < M; t += NT) cp_async8(tws + t, a.tw + t);
+  for (int t = tid; t < 14 * 15; t += NT) cp_async4(zmt + t, zern_mono_table() + t);
+  cp_async_commit();
   pdl_wait();  // O and the scalar parameters come from the previous update
   // Only now may the next kernel (this step's update) start: it reads O, m
   // and v before its own wait, which is safe once the previous update, the
@@ -166,6 +172,7 @@ __global__ void __launch_bounds__(led_threads<M, C>(), M == 512 ? 1 : 2) led_ker
   const int grp = tid / G, j = tid % G;
   float2* buf = fb + grp * FS;
   if (tid < 14) red[tid] = zc;   // the aberration coefficients, via the (still unused) reduction area
+  cp_async_wait<2>();  // group 0: the constant tables
   __syncthreads();
   if (tid < 35) poly[tid] = theta_poly_entry_tab(red, zmt, tid);  // aberration phase as monomials of q/R
   FftTw<(M >= 256) ? 128 : M> TW;  // radix-8 path: per-thread twiddles in registers

@@ -113,18 +113,29 @@ __device__ void led_scalars(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc2)
   for (int j = tid; j < 3 * n; j += blockDim.x) gl[j] = 0.0;
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
   __syncthreads();
-  for (int kk = tid; kk < a.B; kk += blockDim.x) {
-    const int led = a.slot[kk].x;
+  // slot kk's C partials sit on C consecutive lanes (C divides 32): all loads
+  // in flight at once, then a fixed xor tree over those lanes
+  const int C = a.C, total = a.B * C;
+  for (int base = 0; base < total; base += blockDim.x) {
+    const int e = base + tid;  // (slot e / C, rank e % C)
     double sg = 0.0, sy = 0.0, sx = 0.0;
-    for (int r = 0; r < a.C; ++r) {
-      const double* p = a.part + ((size_t)kk * a.C + r) * NPART;
-      sg += p[P_GAMMA];
-      sy += p[P_DY];
-      sx += p[P_DX];
+    if (e < total) {
+      const double* p = a.part + (size_t)e * NPART;
+      sg = p[P_GAMMA];
+      sy = p[P_DY];
+      sx = p[P_DX];
     }
-    gl[led] = sg;
-    gl[n + 2 * led] = sy;
-    gl[n + 2 * led + 1] = sx;
+    for (int o = 1; o < C; o <<= 1) {
+      sg += __shfl_xor_sync(0xffffffffu, sg, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+    }
+    if (e < total && (e % C) == 0) {
+      const int led = a.slot[e / C].x;
+      gl[led] = sg;
+      gl[n + 2 * led] = sy;
+      gl[n + 2 * led + 1] = sx;
+    }
   }
   __syncthreads();
   for (int k = 0, j = tid; j < 3 * n; ++k, j += blockDim.x) {
