@@ -40,7 +40,6 @@ __device__ __forceinline__ double warp_sum_d(double v) {
 // each the sum of its slot's C partials in rank order. Every parameter takes
 // an Adam step every step (zero gradient for LEDs outside the batch).
 constexpr int NSC = 17;
-constexpr int SP_PRE = 4;  // per-LED parameters per thread whose state is loaded before the wait
 
 __device__ __forceinline__ bool learned(const UpdArgs& a, int i) {
   const unsigned bit = i < SP_DEFOCUS ? 1u << 1 : i == SP_DEFOCUS ? 1u << 2 : i < sp_offset(a.n_leds) ? 1u << 3 : 1u << 4;
@@ -95,24 +94,41 @@ __device__ void shared_scalar(const UpdArgs& a, int q, float inv_bc1, float inv_
   if (learned(a, i)) scalar_adam(a, i, w, m, v, tot, inv_bc1, inv_sqrt_bc2);
 }
 
-// CTA 16: the per-LED intensity factors and offsets of every LED.
+// CTA 16: the per-LED intensity factors and offsets of every LED. The LEDs
+// outside the batch have zero gradient and are not read by this step's LED
+// kernel, so their Adam steps run before the wait; after it only the batch's
+// 3 B parameters remain.
 __device__ void led_scalars(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc2) {
-  extern __shared__ double gl[];  // [3 n_leds]: gamma, then (dy, dx) per LED
+  extern __shared__ double gl[];  // [3 B]: per batch slot gamma, dy, dx
+  __shared__ unsigned char in_batch[1024];
   const int n = a.n_leds, tid = threadIdx.x;
-  float pw[SP_PRE], pm[SP_PRE], pv[SP_PRE];
-#pragma unroll
-  for (int k = 0; k < SP_PRE; ++k) {
-    const int i = SP_GAMMA + tid + k * (int)blockDim.x;
-    pw[k] = pm[k] = pv[k] = 0.f;
-    if (!a.assemble && i < sp_size(n)) {
-      pw[k] = __ldcg(a.sp + i);
-      pm[k] = __ldcg(a.msp + i);
-      pv[k] = __ldcg(a.vsp + i);
-    }
+  const bool small = n <= 1024;  // else every LED waits (no membership table)
+  if (small) {
+    for (int l = tid; l < n; l += blockDim.x) in_batch[l] = 0;
+    __syncthreads();
+    for (int kk = tid; kk < a.B; kk += blockDim.x) in_batch[a.slot[kk].x] = 1;
+    __syncthreads();
   }
-  for (int j = tid; j < 3 * n; j += blockDim.x) gl[j] = 0.0;
+  auto idx_led = [&](int j) { return j < n ? j : (j - n) >> 1; };  // parameter j of the 3n -> its LED
+  auto batch_param = [&](int q) {  // parameter r = q % 3 (gamma, dy, dx) of batch slot q / 3
+    const int led = a.slot[q / 3].x, r = q % 3;
+    return r == 0 ? SP_GAMMA + led : sp_offset(n) + 2 * led + (r - 1);
+  };
+  // the batch's own parameter state, for the Adam steps after the wait (one per thread)
+  float bw = 0.f, bm = 0.f, bv = 0.f;
+  if (!a.assemble && tid < 3 * a.B) {
+    const int i = batch_param(tid);
+    bw = __ldcg(a.sp + i);
+    bm = __ldcg(a.msp + i);
+    bv = __ldcg(a.vsp + i);
+  }
+  if (!a.assemble)
+    for (int j = tid; j < 3 * n; j += blockDim.x) {
+      const int i = SP_GAMMA + j;
+      if (!small || in_batch[idx_led(j)] || !learned(a, i)) continue;
+      scalar_adam(a, i, __ldcg(a.sp + i), __ldcg(a.msp + i), __ldcg(a.vsp + i), 0.0, inv_bc1, inv_sqrt_bc2);
+    }
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
-  __syncthreads();
   // slot kk's C partials sit on C consecutive lanes (C divides 32): all loads
   // in flight at once, then a fixed xor tree over those lanes
   const int C = a.C, total = a.B * C;
@@ -131,30 +147,39 @@ __device__ void led_scalars(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc2)
       sx += __shfl_xor_sync(0xffffffffu, sx, o);
     }
     if (e < total && (e % C) == 0) {
-      const int led = a.slot[e / C].x;
-      gl[led] = sg;
-      gl[n + 2 * led] = sy;
-      gl[n + 2 * led + 1] = sx;
+      const int kk = e / C;
+      gl[3 * kk] = sg;
+      gl[3 * kk + 1] = sy;
+      gl[3 * kk + 2] = sx;
     }
   }
   __syncthreads();
-  for (int k = 0, j = tid; j < 3 * n; ++k, j += blockDim.x) {
-    const int i = SP_GAMMA + j;
-    if (a.assemble) {
-      a.g_sc[i] = (float)gl[j];
-      continue;
+  if (a.assemble) {  // gradients of every LED: zero outside the batch
+    for (int j = tid; j < 3 * n; j += blockDim.x) a.g_sc[SP_GAMMA + j] = 0.f;
+    __syncthreads();
+    for (int q = tid; q < 3 * a.B; q += blockDim.x) {
+      const int led = a.slot[q / 3].x, r = q % 3;
+      a.g_sc[r == 0 ? SP_GAMMA + led : sp_offset(n) + 2 * led + (r - 1)] = (float)gl[q];
     }
+    return;
+  }
+  if (small) {
+    for (int q = tid; q < 3 * a.B; q += blockDim.x) {
+      const int i = batch_param(q);
+      if (!learned(a, i)) continue;
+      if (q == tid) scalar_adam(a, i, bw, bm, bv, gl[q], inv_bc1, inv_sqrt_bc2);
+      else scalar_adam(a, i, a.sp[i], a.msp[i], a.vsp[i], gl[q], inv_bc1, inv_sqrt_bc2);
+    }
+    return;
+  }
+  // many LEDs: every parameter here, the batch's from the sums
+  for (int j = tid; j < 3 * n; j += blockDim.x) {
+    const int i = SP_GAMMA + j, led = idx_led(j);
     if (!learned(a, i)) continue;
-    float w, m, v;
-    if (k < SP_PRE) {
-      // a register array indexed by a loop counter: select, not index, to stay in registers
-#pragma unroll
-      for (int u = 0; u < SP_PRE; ++u)
-        if (u == k) { w = pw[u]; m = pm[u]; v = pv[u]; }
-    } else {
-      w = a.sp[i]; m = a.msp[i]; v = a.vsp[i];
-    }
-    scalar_adam(a, i, w, m, v, gl[j], inv_bc1, inv_sqrt_bc2);
+    double g = 0.0;
+    for (int kk = 0; kk < a.B; ++kk)
+      if (a.slot[kk].x == led) g = gl[3 * kk + (j < n ? 0 : 1 + ((j - n) & 1))];
+    scalar_adam(a, i, a.sp[i], a.msp[i], a.vsp[i], g, inv_bc1, inv_sqrt_bc2);
   }
 }
 
@@ -181,14 +206,21 @@ __global__ void __launch_bounds__(UPD_NT) update_kernel(const UpdArgs a) {
     const int4 sl = a.slot[kk];
     corner[kk] = make_int2(a.N / 2 + sl.z - a.h, a.N / 2 + sl.y - a.h);
   }
-  // this thread's first element of the column (most columns need one per thread)
-  const int y0 = span.x + (int)threadIdx.x;
-  float2 w0 = make_float2(0.f, 0.f), m0 = w0, v0 = w0;
+  // this thread's first two elements of the column (columns are up to ~2 x
+  // 256 rows tall), loaded before the wait
+  const int y0 = span.x + (int)threadIdx.x, y1 = y0 + (int)blockDim.x;
+  float2 w0 = make_float2(0.f, 0.f), m0 = w0, v0 = w0, w1 = w0, m1 = w0, v1 = w0;
   if (!a.assemble && y0 < span.y) {
     const size_t o = (size_t)x * a.N + y0;
     w0 = __ldcg(a.Ot + o);  // L2 (not L1): written by the previous update kernel
     m0 = __ldcg(a.mO + o);
     v0 = __ldcg(a.vO + o);
+  }
+  if (!a.assemble && y1 < span.y) {
+    const size_t o = (size_t)x * a.N + y1;
+    w1 = __ldcg(a.Ot + o);
+    m1 = __ldcg(a.mO + o);
+    v1 = __ldcg(a.vO + o);
   }
   __syncthreads();
   if (threadIdx.x == 0) {  // batch slots whose box covers this column, in batch order
@@ -208,29 +240,41 @@ __global__ void __launch_bounds__(UPD_NT) update_kernel(const UpdArgs a) {
     if (!a.assemble) {
       if (y == y0) {
         w = w0; m = m0; v = v0;
+      } else if (y == y1) {
+        w = w1; m = m1; v = v1;
       } else {
         w = a.Ot[o]; m = a.mO[o]; v = a.vO[o];
       }
     }
     // sum of the covering boxes in batch order (adding zeros where a box
-    // does not reach this row), eight loads in flight at a time
+    // does not reach this row), sixteen loads in flight at a time
     float2 g = make_float2(0.f, 0.f);
     int q = 0;
-    for (; q + 8 <= n_l; q += 8) {
-      float2 t[8];
+    for (; q + 16 <= n_l; q += 16) {
+      float2 t[16];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 16; ++u) {
         const int kk = lst[q + u];
         const int ry = y - corner[kk].y, cx = x - corner[kk].x;
         t[u] = (unsigned)ry < (unsigned)W ? a.gbox[((size_t)kk * W + cx) * W + ry] : make_float2(0.f, 0.f);
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) g = cadd(g, t[u]);
+      for (int u = 0; u < 16; ++u) g = cadd(g, t[u]);
     }
-    for (; q < n_l; ++q) {
-      const int kk = lst[q];
-      const int ry = y - corner[kk].y, cx = x - corner[kk].x;
-      if ((unsigned)ry < (unsigned)W) g = cadd(g, a.gbox[((size_t)kk * W + cx) * W + ry]);
+    if (q < n_l) {  // the rest (fewer than 16), also all in flight before the sum
+      float2 t[16];
+#pragma unroll
+      for (int u = 0; u < 16; ++u) {
+        t[u] = make_float2(0.f, 0.f);
+        if (q + u < n_l) {
+          const int kk = lst[q + u];
+          const int ry = y - corner[kk].y, cx = x - corner[kk].x;
+          if ((unsigned)ry < (unsigned)W) t[u] = a.gbox[((size_t)kk * W + cx) * W + ry];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u)
+        if (q + u < n_l) g = cadd(g, t[u]);
     }
     if (a.assemble) {
       a.g_obj[o] = g;
@@ -250,7 +294,7 @@ cudaError_t update_prepare() {
 }
 
 cudaError_t launch_update(const UpdArgs& a, cudaStream_t s, bool pdl) {
-  const size_t smem = sizeof(double) * 3 * (size_t)a.n_leds;
+  const size_t smem = sizeof(double) * 3 * (size_t)a.B;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(a.n_cols + NSC), 1, 1);
   cfg.blockDim = dim3(UPD_NT, 1, 1);
