@@ -259,7 +259,15 @@ class Engine:
         return dict(object=None if gO is None else gO[..., 0] + 1j * gO[..., 1].astype(np.float64),
                     zernike=gz, defocus=float(gd[0]), gamma=gg, offset=go, loss=loss.value)
 
-    def get(self, object=True):
+    def get(self, object=True, out=None):
+        """The current state. out (optional): caller-owned host buffers to copy into
+        (e.g. pinned tensors reused across calls), a dict with float32 'object'
+        [N, N, 2], 'zernike' [14], 'defocus' [1], 'gamma' [n_leds], 'offset'
+        [n_leds, 2]; they are returned as they are (no complex conversion)."""
+        if out is not None:
+            self._check(lib().fpm_get(self._h, _ptr(out["object"]) if object else None, _ptr(out["zernike"]),
+                                      _ptr(out["defocus"]), _ptr(out["gamma"]), _ptr(out["offset"])))
+            return out
         O = np.empty((self.N, self.N, 2), np.float32) if object else None
         z = np.empty(14, np.float32)
         d = np.empty(1, np.float32)

@@ -338,3 +338,22 @@ def test_profiled_runs_equal_graph_run_bitwise():
         outs.append(eng.get_state())
     assert np.array_equal(outs[0], outs[1])
     assert np.array_equal(outs[0], outs[2])
+
+
+def test_get_into_caller_buffers_matches_get():
+    torch = pytest.importorskip("torch")
+    c, I, g_t, prm, O = multiparam_problem(m=64, seed=33)
+    eng = engine_for(g_t)
+    push(eng, O, prm)
+    ref = eng.get()
+    out = {"object": torch.empty((g_t.N, g_t.N, 2), dtype=torch.float32).pin_memory(),
+           "zernike": torch.empty(14, dtype=torch.float32).pin_memory(),
+           "defocus": torch.empty(1, dtype=torch.float32).pin_memory(),
+           "gamma": torch.empty(g_t.n_leds, dtype=torch.float32).pin_memory(),
+           "offset": torch.empty((g_t.n_leds, 2), dtype=torch.float32).pin_memory()}
+    got = eng.get(out=out)
+    o = got["object"].numpy()
+    assert np.array_equal(o[..., 0] + 1j * o[..., 1].astype(np.float64), ref["object"])
+    for k in ("zernike", "gamma", "offset"):
+        assert np.array_equal(got[k].numpy(), ref[k])
+    assert float(got["defocus"][0]) == ref["defocus"]
