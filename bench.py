@@ -251,9 +251,10 @@ def run_cpu_child(stack, sample_s: float, leds_per_step: int, max_steps: int):
 # serving: continuous batching of uneven reconstructions vs the same jobs serially
 # --------------------------------------------------------------------------
 
-def serving_jobs(n_jobs: int, rate_hz: float, seed: int):
+def serving_jobs(n_jobs: int, rate_hz: float, seed: int, shape=None):
     """Seeded Poisson arrivals; ROI from {256, 512, 1024, 2048}^2 at upsample 4, grids
-    {7, 11, 15}^2, the 64-px recipe (hard pupil, aberration-free, noise-free) per job."""
+    {7, 11, 15}^2, the 64-px recipe (hard pupil, aberration-free, noise-free) per job.
+    shape=(N, grid): every job of that shape instead (a homogeneous request stream)."""
     from paper_2408_13782_gb300 import Engine
     from paper_2408_13782_gb300 import serve as sv
     from synth import recipes as S
@@ -263,6 +264,8 @@ def serving_jobs(n_jobs: int, rate_hz: float, seed: int):
     for k in range(n_jobs):
         N = int(rng.choice([256, 512, 1024, 2048]))
         grid = int(rng.choice([7, 11, 15]))
+        if shape is not None:
+            N, grid = shape
         c = S.serving_job_config(N, grid, seed * 1000 + k)
         nominal, truth = S.led_grid(c.grid, c.pitch, c.jitter, c.seed)
         eng = Engine(c.m, c.s, truth, c.R, c.lambda_um, c.dk_per_um, c.edge)
@@ -279,13 +282,14 @@ def serving_run(jobs, budget: int, max_active: int):
     from paper_2408_13782_gb300 import serve as sv
     srv = sv.Server(budget, max_active)
     ids, st, wall = sv.run_arrivals(srv, [(d, s, t) for d, s, t, _, _ in jobs])
+    stats = srv.stats()
     srv.close()
     ttc = np.array([x["t_done"] - x["t_submit"] for x in st])
     upd = sum(x["led_updates"] for x in st)
     span = max(x["t_done"] for x in st) - min(x["t_submit"] for x in st)
     return {"p50_ttc_s": float(np.percentile(ttc, 50)), "p99_ttc_s": float(np.percentile(ttc, 99)),
             "led_updates_per_s": upd / span, "jobs_done": int(sum(x["state"] == sv.JOB_DONE for x in st)),
-            "epochs": [int(x["epochs"]) for x in st], "makespan_s": span}
+            "epochs": [int(x["epochs"]) for x in st], "makespan_s": span, "server": stats}
 
 
 def serving_section(n_jobs=16, rate_hz=40.0, seed=5):
@@ -295,12 +299,18 @@ def serving_section(n_jobs=16, rate_hz=40.0, seed=5):
     budget = int(0.6 * free)
     run_serving = serving_run(jobs, budget, max_active=64)
     run_serial = serving_run(jobs, budget, max_active=1)
+    same = serving_jobs(n_jobs, rate_hz, seed + 1, shape=(512, 11))
+    same_serving = serving_run(same, budget, max_active=64)
+    same_serial = serving_run(same, budget, max_active=1)
     return {"what": f"{n_jobs} jobs, Poisson arrivals {rate_hz:g}/s, ROI from {{256,512,1024,2048}}^2 at "
                     "upsample 4, LED grids {7,11,15}^2, stop at relative epoch-loss change < 1e-4 or 40 epochs; "
-                    "continuous batching (jobs admitted by device-memory footprint, overlapping) vs the same "
-                    "jobs one at a time (FCFS) on the same GPU",
+                    "continuous batching (jobs admitted by device-memory footprint, overlapping, same-shape "
+                    "jobs stepped together in one launch per step) vs the same jobs one at a time (FCFS) on "
+                    "the same GPU",
             "mix": [f"{N}^2/{g}x{g}" for _, _, _, N, g in jobs],
-            "hbm_budget_bytes": budget, "continuous": run_serving, "serial": run_serial}
+            "hbm_budget_bytes": budget, "continuous": run_serving, "serial": run_serial,
+            "same_shape": {"what": f"{n_jobs} jobs of 512^2 / 11x11, the same arrivals process",
+                           "continuous": same_serving, "serial": same_serial}}
 
 
 # --------------------------------------------------------------------------

@@ -273,12 +273,17 @@ int fpm_gradients_static(const fpm_geometry* g, float pupil_radius_px, int32_t u
  * a job too large for now does not hold back smaller ones) (the paper picks the
  * batch size from the available GPU memory, Section 2.2; here memory decides
  * which jobs are resident). An admitted job keeps its object spectrum, pupil,
- * defocus, LED parameters and Adam state resident on the device and runs on
- * its own stream, so the epochs of all admitted jobs overlap on the GPU. Each
- * epoch is a fresh random batch order (Eq. 13-14, seed = job seed) as at most
- * two graph launches. A job stops when the relative change of its epoch loss
- * drops below rel_tol, or after max_epochs; its result is then copied to host
- * memory and its device memory freed for the next admissions.
+ * defocus, LED parameters and Adam state resident on the device. Each epoch
+ * is a fresh random batch order (Eq. 13-14, seed = job seed). Resident jobs of
+ * the same low-res size, LED count and batch size (FP32 FFT form) run their
+ * epochs together in rounds: each step of a round is one per-LED launch and
+ * one update launch covering all of them, and a round is one CUDA graph,
+ * captured once per set of jobs. Rounds of different sets run on their own
+ * streams, so all resident jobs overlap on the GPU; each job's arithmetic is
+ * the same alone or in a round, so its result is too (bit for bit). A job
+ * stops when the relative change of its epoch loss drops below rel_tol, or
+ * after max_epochs; its result is then copied to host memory and its device
+ * memory freed for the next admissions.
  * All server calls are made from one host thread. */
 typedef struct fpm_server fpm_server;
 
@@ -314,13 +319,18 @@ int fpm_server_create(int64_t hbm_budget_bytes, int32_t max_active, fpm_server**
  * its footprint exceeds the whole budget. */
 int fpm_server_submit(fpm_server* s, const fpm_job_desc* d, const float* stack, int64_t* job_id);
 /* Make progress without blocking: retire finished epochs, stop converged jobs,
- * admit queued ones. Outputs (nullable): jobs resident, jobs waiting. */
+ * admit queued ones, launch the next rounds. Outputs (nullable): jobs
+ * resident, jobs waiting. */
 int fpm_server_tick(fpm_server* s, int32_t* n_active, int32_t* n_queued);
 int fpm_server_status(const fpm_server* s, int64_t job_id, fpm_job_status* st);
 /* Result of a finished job (host buffers, each nullable; layouts as fpm_get). */
 int fpm_server_result(fpm_server* s, int64_t job_id, float* O, float* zernike, float* defocus,
                       float* gamma, float* offset);
 double fpm_server_clock(const fpm_server* s);      /* seconds since fpm_server_create */
+/* Counters since creation (each nullable): rounds launched, job epochs they
+ * ran, the most jobs in one round, kernel launches of the rounds. */
+int fpm_server_stats(const fpm_server* s, int64_t* rounds, int64_t* round_epochs, int64_t* max_jobs_per_round,
+                     int64_t* launches);
 const char* fpm_server_error(const fpm_server* s);
 void fpm_server_destroy(fpm_server* s);
 

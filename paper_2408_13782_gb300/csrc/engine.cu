@@ -396,6 +396,43 @@ int backward_impl(fpm_handle* h, const int32_t* idx, int32_t B, const float* dL_
                   double* loss_out);
 }  // namespace
 
+int fpmk::engine_round_reserve(fpm_handle* h, int n_steps, int B, EngineRound* out) {
+  if (!h || !out || n_steps < 1 || B < 1) return FPM_ERR_ARG;
+  if (!h->loaded) return fail(h, FPM_ERR_STATE, "no stack loaded");
+  int rc;
+  if ((rc = ensure_batch(h, B))) return rc;
+  if ((rc = grow(h, &h->sched, &h->cap_sched, n_steps * B))) return rc;
+  if ((rc = grow(h, &h->losses, &h->cap_losses, n_steps))) return rc;
+  if ((rc = grow(h, &h->coef, &h->cap_coef, n_steps))) return rc;
+  out->m = h->m;
+  out->C = h->hp.precision != FPM_PRECISION_FP32_FFT ? 1 : h->C;
+  out->W = h->W;
+  out->n_leds = h->n;
+  out->fft = h->hp.precision == FPM_PRECISION_FP32_FFT;
+  out->slots = h->sched;
+  out->coef = h->coef;
+  out->losses = h->losses;
+  out->epoch = h->epoch;
+  return FPM_OK;
+}
+
+void fpmk::engine_round_slots(const fpm_handle* h, const int32_t* idx, int count, int4* dst) {
+  fill_slots(h, idx, count, dst);
+}
+
+void fpmk::engine_round_coef(fpm_handle* h, int n_steps, float2* dst) {
+  fill_coef(h, n_steps, dst);
+  h->t_host += n_steps;
+}
+
+LedArgs fpmk::engine_led_args(fpm_handle* h, const int4* slot_dev, int B) {
+  return led_args(h, slot_dev, B, MODE_LOSS);
+}
+
+UpdArgs fpmk::engine_upd_args(fpm_handle* h, const int4* slot_dev, int B, int step_off, double* loss_slot) {
+  return upd_args(h, slot_dev, B, step_off, loss_slot, 0);
+}
+
 int fpmk::engine_snapshot_loss(fpm_handle* h, double* pinned) {
   int rc = enter(h);
   if (rc) return rc;

@@ -85,6 +85,33 @@ cudaError_t launch_update(const UpdArgs& a, cudaStream_t s, bool pdl);
 // memory, ordered after all earlier work of the handle on its caller stream.
 int engine_snapshot_loss(fpm_handle* h, double* pinned);
 
+// Several jobs in one launch (the serving loop's rounds): cluster q of the
+// per-LED launch takes slot map[q].y of job map[q].x, CTA q of the update
+// launch is CTA map[q].y of job map[q].x's update.
+cudaError_t launch_led_jobs(int m, int C, const LedArgs* jobs, const int2* map, int n_clusters, int W_max,
+                            cudaStream_t s, bool pdl);
+cudaError_t launch_update_jobs(const UpdArgs* jobs, const int2* map, int n_ctas, int B_max, cudaStream_t s,
+                               bool pdl);
+int update_ctas(const UpdArgs& a);  // CTAs of one job's update launch
+
+// A handle as seen by the serving loop.
+struct EngineRound {
+  int m, C, W, n_leds, fft;     // kernel configuration; fft: FP32 FFT form (groupable)
+  int4* slots;                  // device: batch slots of the round's steps
+  float2* coef;                 // device: Adam bias corrections per step
+  double* losses;               // device: batch loss per step
+  double* epoch;                // device: running FP64 loss sum
+};
+// Reserve device room for n_steps steps of at most B slots and describe the handle.
+int engine_round_reserve(fpm_handle* h, int n_steps, int B, EngineRound* out);
+// Host side of one round: slot tables for idx[0..count), and the Adam bias
+// corrections of the next n_steps steps (advancing the handle's step count).
+void engine_round_slots(const fpm_handle* h, const int32_t* idx, int count, int4* dst);
+void engine_round_coef(fpm_handle* h, int n_steps, float2* dst);
+// Launch arguments of one step of the handle (built-in loss, updating).
+LedArgs engine_led_args(fpm_handle* h, const int4* slot_dev, int B);
+UpdArgs engine_upd_args(fpm_handle* h, const int4* slot_dev, int B, int step_off, double* loss_slot);
+
 // Message returned by fpm_last_error(NULL) (calls that have no handle).
 void set_unbound_error(const char* msg);
 

@@ -94,14 +94,15 @@ __device__ __forceinline__ void transform(float2* buf, const FftTw<(M >= 256) ? 
   else fft_group<M, DIR>(buf, TW, j);
 }
 
+// The per-LED step for batch slot k of the job described by a (run by every
+// thread of the slot's cluster).
 template <int M, int C>
-__global__ void __launch_bounds__(led_threads<M, C>(), M == 512 ? 1 : 2) led_kernel(const LedArgs a) {
+__device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
   using L = LedLayout<M, C>;
   constexpr int NT = L::NT, G = L::G, NG = L::NG, ROWS = L::ROWS, TS = L::TS, FS = L::FS;
   constexpr int NW = L::NW;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
-  const int k = blockIdx.x / C;
   const int W = a.W, h = a.h, N = a.N;
   const int chunk = (W + C - 1) / C;
   const int c0 = rank * chunk, c1 = min(W, c0 + chunk);
@@ -333,6 +334,24 @@ __global__ void __launch_bounds__(led_threads<M, C>(), M == 512 ? 1 : 2) led_ker
                  a.part + ((size_t)k * C + rank) * NPART);
 }
 
+// One job: cluster k takes batch slot k.
+template <int M, int C>
+__global__ void __launch_bounds__(led_threads<M, C>(), M == 512 ? 1 : 2) led_kernel(const LedArgs a) {
+  led_body<M, C>(a, (int)(blockIdx.x / C));
+}
+
+// Several jobs in one launch (the serving loop): cluster q takes slot
+// map[q].y of job map[q].x, whose arguments are copied to shared memory.
+template <int M, int C>
+__global__ void __launch_bounds__(led_threads<M, C>(), M == 512 ? 1 : 2)
+    led_kernel_jobs(const LedArgs* __restrict__ jobs, const int2* __restrict__ map) {
+  __shared__ LedArgs sa;
+  const int2 q = map[blockIdx.x / C];
+  if (threadIdx.x == 0) sa = jobs[q.x];
+  __syncthreads();
+  led_body<M, C>(sa, q.y);
+}
+
 // Cluster sizes built for each low-res size (CTAs cooperating on one LED).
 int led_cluster_size(int m) {
   switch (m) {
@@ -410,15 +429,22 @@ static cudaError_t prepare_t(int W) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   if (LedLayout<M, C>::bytes(W) > (size_t)optin) return cudaErrorInvalidValue;
-  if (C > 8) {
-    e = cudaFuncSetAttribute(led_kernel<M, C>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  // both entry points (one job, several jobs); the latter also holds a copy
+  // of its job's arguments in static shared memory
+  const void* fns[2] = {(const void*)led_kernel<M, C>, (const void*)led_kernel_jobs<M, C>};
+  for (int f = 0; f < 2; ++f) {
+    if (C > 8) {
+      e = cudaFuncSetAttribute(fns[f], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e != cudaSuccess) return e;
+    }
+    // the largest shared-memory carveout, so the SM configuration does not flip between kernels
+    e = cudaFuncSetAttribute(fns[f], cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    const int dyn = f == 0 ? optin : optin - (int)sizeof(LedArgs);
+    e = cudaFuncSetAttribute(fns[f], cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return e;
   }
-  // the largest shared-memory carveout, so the SM configuration does not flip between kernels
-  e = cudaFuncSetAttribute(led_kernel<M, C>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                           cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(led_kernel<M, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  return cudaSuccess;
 }
 
 cudaError_t led_prepare(int m, int C, int W) {
@@ -448,6 +474,40 @@ static cudaError_t launch_t(const LedArgs& a, cudaStream_t s, bool pdl) {
   cfg.attrs = attr;
   cfg.numAttrs = pdl ? 2 : 1;
   return cudaLaunchKernelEx(&cfg, led_kernel<M, C>, a);
+}
+
+template <int M, int C>
+static cudaError_t launch_jobs_t(const LedArgs* jobs, const int2* map, int n_clusters, int W_max, cudaStream_t s,
+                                 bool pdl) {
+  using L = LedLayout<M, C>;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n_clusters * C), 1, 1);
+  cfg.blockDim = dim3(L::NT, 1, 1);
+  cfg.dynamicSmemBytes = L::bytes(W_max);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 2 : 1;
+  return cudaLaunchKernelEx(&cfg, led_kernel_jobs<M, C>, jobs, map);
+}
+
+cudaError_t launch_led_jobs(int m, int C, const LedArgs* jobs, const int2* map, int n_clusters, int W_max,
+                            cudaStream_t s, bool pdl) {
+  if (n_clusters < 1) return cudaErrorInvalidValue;
+  if (m == 32) return launch_jobs_t<32, 2>(jobs, map, n_clusters, W_max, s, pdl);
+  if (m == 64) return launch_jobs_t<64, 4>(jobs, map, n_clusters, W_max, s, pdl);
+  if (m == 128) return launch_jobs_t<128, 8>(jobs, map, n_clusters, W_max, s, pdl);
+  if (m == 256)
+    return C == 16 ? launch_jobs_t<256, 16>(jobs, map, n_clusters, W_max, s, pdl)
+                   : launch_jobs_t<256, 8>(jobs, map, n_clusters, W_max, s, pdl);
+  if (m == 512 && C == 16) return launch_jobs_t<512, 16>(jobs, map, n_clusters, W_max, s, pdl);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_led(int m, int C, const LedArgs& a, cudaStream_t s, bool pdl) {

@@ -3,20 +3,30 @@
 // Requests (one reconstruction job each: geometry, stack, hyper-parameters,
 // batch size, stopping rule) are queued on submit and admitted in arrival
 // order, each one as soon as it fits the device-memory budget and a slot is
-// free (first fit). An
-// admitted job owns an engine handle - its object spectrum, pupil, defocus,
-// LED parameters and Adam state stay resident until it finishes - and a
-// private stream, so the epochs of all admitted jobs run concurrently on the
-// GPU. Each epoch (a fresh random permutation chopped into batches, Eq. 13-14)
-// is two graph launches at most (the full batches, then the short one);
-// after it, the running FP64 loss is copied to pinned memory and an event is
-// recorded. fpm_server_tick() never blocks: it retires epochs whose events
-// have fired, applies the stopping rule (relative change of the epoch loss
-// below rel_tol, or max_epochs), copies finished results to host memory and
-// frees their device memory, then admits queued jobs.
+// free (first fit). An admitted job owns an engine handle: its object
+// spectrum, pupil, defocus, LED parameters and Adam state stay resident until
+// it finishes.
+//
+// Work is issued in rounds of one epoch (a fresh random permutation chopped
+// into batches, Eq. 13-14) per job. Jobs with the same kernel configuration
+// and epoch shape (low-res size, cluster, crop box, LED count, batch size;
+// FP32 FFT form) share a round: step s of the round is one per-LED launch and one
+// update launch covering step s of every job in it, the jobs' arguments read
+// from device tables. A round is captured once as a CUDA graph (kept while
+// its jobs are resident) and relaunched every epoch with the new schedules
+// and Adam coefficients copied from pinned staging inside the graph. Rounds
+// of different groups run on their own streams, so all admitted jobs overlap
+// on the GPU. Other jobs (tensor-core forms) run their epochs through fpm_run.
+// After a round, each job's running FP64 loss is in pinned memory.
+// fpm_server_tick() never blocks: it retires rounds whose events have fired,
+// applies the stopping rule (relative change of the epoch loss below
+// rel_tol, or max_epochs), copies finished results to host memory and frees
+// their device memory, admits queued jobs, then launches the next rounds.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
+#include <cstdio>
 #include <cmath>
 #include <cstring>
 #include <deque>
@@ -50,6 +60,21 @@ struct Job {
   int64_t led_updates = 0;
   std::vector<float> O, zern, defocus, gamma, offset;  // results
   std::string error;
+  EngineRound er{};  // device buffers of the handle used by rounds
+  bool fresh = true;  // admitted, its load not yet ordered before a round
+};
+
+// One round: an epoch of each of its jobs (same epoch shape) in lock-step.
+struct Round {
+  std::vector<Job*> jobs;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int steps = 0, B = 0, nfull = 0, rem = 0;
+  std::vector<int4*> h_slots;    // pinned, per job: the epoch's slot table
+  std::vector<float2*> h_coef;   // pinned, per job: Adam bias corrections per step
+  unsigned char* d_tables = nullptr;  // LedArgs / UpdArgs tables and maps of all steps
+  bool in_flight = false;
 };
 
 }  // namespace
@@ -60,6 +85,8 @@ struct fpm_server {
   std::deque<Job*> queue;
   std::vector<Job*> active;
   std::map<int64_t, std::unique_ptr<Job>> jobs;
+  std::map<std::string, std::unique_ptr<Round>> rounds;  // by composition
+  int64_t n_rounds = 0, n_round_epochs = 0, max_round_jobs = 0, n_launches = 0;
   int64_t next_id = 1;
   std::chrono::steady_clock::time_point t0;
   std::string msg;
@@ -76,7 +103,32 @@ int srv_fail(fpm_server* s, int code, const std::string& m) {
   return code;
 }
 
+void destroy_round(Round* r) {
+  if (r->stream) cudaStreamSynchronize(r->stream);
+  if (r->exec) cudaGraphExecDestroy(r->exec);
+  for (auto p : r->h_slots)
+    if (p) cudaFreeHost(p);
+  for (auto p : r->h_coef)
+    if (p) cudaFreeHost(p);
+  if (r->d_tables) cudaFree(r->d_tables);
+  if (r->ev) cudaEventDestroy(r->ev);
+  if (r->stream) cudaStreamDestroy(r->stream);
+}
+
+void forget_rounds_of(fpm_server* s, const Job* j) {
+  for (auto it = s->rounds.begin(); it != s->rounds.end();) {
+    const auto& js = it->second->jobs;
+    if (std::find(js.begin(), js.end(), j) != js.end()) {
+      destroy_round(it->second.get());
+      it = s->rounds.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
 void release(fpm_server* s, Job* j) {
+  forget_rounds_of(s, j);
   if (j->h) fpm_destroy(j->h);
   j->h = nullptr;
   if (j->ev) cudaEventDestroy(j->ev);
@@ -130,9 +182,16 @@ int admit(fpm_server* s, Job* j) {
     return rc;
   }
   std::vector<float>().swap(j->stack);  // the stack now lives on the device
+  const int n = d.geometry.n_leds, B = d.batch;
+  const int steps = n / B + (n % B ? 1 : 0);
+  if ((rc = engine_round_reserve(j->h, steps, B, &j->er))) {
+    j->error = fpm_last_error(j->h);
+    return rc;
+  }
+  if (cudaEventRecord(j->ev, j->stream) != cudaSuccess) return FPM_ERR_CUDA;  // the load, for the first round
   j->state = FPM_JOB_ACTIVE;
   j->t_admit = now(s);
-  return launch_epoch(j);
+  return FPM_OK;
 }
 
 // After an epoch: stop, or queue the next one.
@@ -168,7 +227,153 @@ int retire_epoch(fpm_server* s, Job* j) {
     release(s, j);
     return FPM_OK;
   }
-  return launch_epoch(j);
+  return FPM_OK;  // the next epoch is launched by the tick
+}
+
+// ---------------------------------------------------------------- rounds
+
+std::string group_key(const Job* j) {
+  char b[96];
+  std::snprintf(b, sizeof b, "m%d C%d W%d n%d B%d", j->er.m, j->er.C, j->er.W, j->er.n_leds, j->desc.batch);
+  return b;
+}
+
+bool groupable(const Job* j) { return j->er.fft != 0; }
+
+// Build the round of jobs js (same group): tables, staging, and its graph.
+int build_round(Round* r, const std::vector<Job*>& js) {
+  r->jobs = js;
+  const Job* j0 = js[0];
+  const int n = j0->er.n_leds, B = j0->desc.batch, m = j0->er.m, C = j0->er.C;
+  r->B = B;
+  r->nfull = n / B;
+  r->rem = n - r->nfull * B;
+  r->steps = r->nfull + (r->rem ? 1 : 0);
+  const int J = (int)js.size(), S = r->steps;
+  if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess)
+    return FPM_ERR_CUDA;
+  r->h_slots.assign(J, nullptr);
+  r->h_coef.assign(J, nullptr);
+  for (int q = 0; q < J; ++q)
+    if (cudaMallocHost(&r->h_slots[q], sizeof(int4) * n) != cudaSuccess ||
+        cudaMallocHost(&r->h_coef[q], sizeof(float2) * S) != cudaSuccess)
+      return FPM_ERR_OOM;
+  // per step: J LedArgs, J UpdArgs, the cluster map and the update-CTA map
+  std::vector<LedArgs> led((size_t)S * J);
+  std::vector<UpdArgs> upd((size_t)S * J);
+  std::vector<std::vector<int2>> lmap(S), umap(S);
+  for (int st = 0; st < S; ++st) {
+    const int Bs = st < r->nfull ? B : r->rem;
+    for (int q = 0; q < J; ++q) {
+      Job* j = js[q];
+      const int4* sl = j->er.slots + (size_t)st * B;
+      led[(size_t)st * J + q] = engine_led_args(j->h, sl, Bs);
+      upd[(size_t)st * J + q] = engine_upd_args(j->h, sl, Bs, st, j->er.losses + st);
+      for (int k = 0; k < Bs; ++k) lmap[st].push_back(make_int2(q, k));
+      const int nc = update_ctas(upd[(size_t)st * J + q]);
+      for (int b = 0; b < nc; ++b) umap[st].push_back(make_int2(q, b));
+    }
+  }
+  size_t lm = 0, um = 0;
+  for (int st = 0; st < S; ++st) {
+    lm += lmap[st].size();
+    um += umap[st].size();
+  }
+  const size_t bytes = sizeof(LedArgs) * led.size() + sizeof(UpdArgs) * upd.size() + sizeof(int2) * (lm + um);
+  if (cudaMalloc(&r->d_tables, bytes) != cudaSuccess) return FPM_ERR_OOM;
+  LedArgs* d_led = reinterpret_cast<LedArgs*>(r->d_tables);
+  UpdArgs* d_upd = reinterpret_cast<UpdArgs*>(d_led + led.size());
+  int2* d_map = reinterpret_cast<int2*>(d_upd + upd.size());
+  std::vector<int2> maps;
+  maps.reserve(lm + um);
+  std::vector<size_t> loff(S), uoff(S);
+  for (int st = 0; st < S; ++st) {
+    loff[st] = maps.size();
+    maps.insert(maps.end(), lmap[st].begin(), lmap[st].end());
+    uoff[st] = maps.size();
+    maps.insert(maps.end(), umap[st].begin(), umap[st].end());
+  }
+  if (cudaMemcpy(d_led, led.data(), sizeof(LedArgs) * led.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d_upd, upd.data(), sizeof(UpdArgs) * upd.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(d_map, maps.data(), sizeof(int2) * maps.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return FPM_ERR_CUDA;
+  // the graph: schedules and coefficients in, S steps of two launches, losses out
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(r->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return FPM_ERR_CUDA;
+  cudaError_t e = cudaSuccess;
+  for (int q = 0; q < J && e == cudaSuccess; ++q) {
+    e = cudaMemcpyAsync(js[q]->er.slots, r->h_slots[q], sizeof(int4) * n, cudaMemcpyHostToDevice, r->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(js[q]->er.coef, r->h_coef[q], sizeof(float2) * S, cudaMemcpyHostToDevice, r->stream);
+  }
+  for (int st = 0; st < S && e == cudaSuccess; ++st) {
+    const int Bs = st < r->nfull ? B : r->rem;
+    e = launch_led_jobs(m, C, d_led + (size_t)st * J, d_map + loff[st], (int)lmap[st].size(), j0->er.W, r->stream,
+                        st > 0);
+    if (e == cudaSuccess)
+      e = launch_update_jobs(d_upd + (size_t)st * J, d_map + uoff[st], (int)umap[st].size(), Bs, r->stream, true);
+  }
+  for (int q = 0; q < J && e == cudaSuccess; ++q)
+    e = cudaMemcpyAsync(js[q]->pinned, js[q]->er.epoch, sizeof(double), cudaMemcpyDeviceToHost, r->stream);
+  const cudaError_t e2 = cudaStreamEndCapture(r->stream, &g);
+  if (e == cudaSuccess && e2 == cudaSuccess) e = cudaGraphInstantiate(&r->exec, g, 0);
+  if (g) cudaGraphDestroy(g);
+  return (e == cudaSuccess && e2 == cudaSuccess) ? FPM_OK : FPM_ERR_CUDA;
+}
+
+// Launch one epoch of every job of a group as one round.
+int launch_round(fpm_server* s, const std::vector<Job*>& js) {
+  std::string key = group_key(js[0]);
+  for (const Job* j : js) {
+    char b[32];
+    std::snprintf(b, sizeof b, " %p", (const void*)j);
+    key += b;
+  }
+  auto it = s->rounds.find(key);
+  Round* r;
+  if (it == s->rounds.end()) {
+    if (s->rounds.size() >= 32)  // bound the cache: drop the rounds not in flight
+      for (auto jt = s->rounds.begin(); jt != s->rounds.end();) {
+        if (!jt->second->in_flight) {
+          destroy_round(jt->second.get());
+          jt = s->rounds.erase(jt);
+        } else {
+          ++jt;
+        }
+      }
+    auto nr = std::make_unique<Round>();
+    const int rc = build_round(nr.get(), js);
+    if (rc) {
+      cudaGetLastError();
+      destroy_round(nr.get());
+      return rc;
+    }
+    r = nr.get();
+    s->rounds.emplace(key, std::move(nr));
+  } else {
+    r = it->second.get();
+  }
+  for (size_t q = 0; q < js.size(); ++q) {
+    Job* j = js[q];
+    std::vector<int32_t> perm(j->er.n_leds);
+    fpm_epoch_permutation(j->er.n_leds, j->desc.seed, j->epochs, perm.data());
+    engine_round_slots(j->h, perm.data(), j->er.n_leds, r->h_slots[q]);
+    engine_round_coef(j->h, r->steps, r->h_coef[q]);
+    if (j->fresh) {  // order the job's load before its first round
+      if (cudaStreamWaitEvent(r->stream, j->ev, 0) != cudaSuccess) return FPM_ERR_CUDA;
+      j->fresh = false;
+    }
+  }
+  if (cudaGraphLaunch(r->exec, r->stream) != cudaSuccess || cudaEventRecord(r->ev, r->stream) != cudaSuccess)
+    return FPM_ERR_CUDA;
+  r->in_flight = true;
+  for (Job* j : js) j->in_flight = true;
+  s->n_rounds += 1;
+  s->n_round_epochs += (int64_t)js.size();
+  s->max_round_jobs = std::max<int64_t>(s->max_round_jobs, (int64_t)js.size());
+  s->n_launches += 2 * (int64_t)r->steps;
+  return FPM_OK;
 }
 
 }  // namespace
@@ -204,6 +409,8 @@ int fpm_server_create(int64_t budget, int32_t max_active, fpm_server** out) {
 
 void fpm_server_destroy(fpm_server* s) {
   if (!s) return;
+  for (auto& kv : s->rounds) destroy_round(kv.second.get());  // waits for rounds in flight
+  s->rounds.clear();
   for (Job* j : s->active)
     if (j->stream) cudaStreamSynchronize(j->stream);
   for (auto& kv : s->jobs)
@@ -239,29 +446,43 @@ int fpm_server_submit(fpm_server* s, const fpm_job_desc* d, const float* stack, 
 
 int fpm_server_tick(fpm_server* s, int32_t* n_active, int32_t* n_queued) {
   if (!s) return FPM_ERR_ARG;
-  // retire finished epochs (frees memory of finished jobs)
-  std::vector<Job*> still;
-  for (Job* j : s->active) {
-    if (j->in_flight) {
-      const cudaError_t q = cudaEventQuery(j->ev);
-      if (q == cudaErrorNotReady) {
-        still.push_back(j);
-        continue;
-      }
-      if (q != cudaSuccess) {
-        cudaGetLastError();
-        fail_job(s, j, cudaGetErrorString(q));
-        continue;
-      }
-      const int rc = retire_epoch(s, j);
-      if (rc) fail_job(s, j, fpm_last_error(j->h));
-    }
-    if (j->state == FPM_JOB_ACTIVE) still.push_back(j);
+  // 1. retire the epochs that have finished: rounds whose events fired and
+  //    jobs running their own epochs (retiring may free a job and its rounds,
+  //    so the jobs are collected first)
+  std::vector<std::pair<Job*, cudaError_t>> fin;
+  for (auto& kv : s->rounds) {
+    Round* r = kv.second.get();
+    if (!r->in_flight) continue;
+    const cudaError_t q = cudaEventQuery(r->ev);
+    if (q == cudaErrorNotReady) continue;
+    r->in_flight = false;
+    for (Job* j : r->jobs) fin.emplace_back(j, q);
   }
+  for (Job* j : s->active) {
+    if (!j->in_flight || groupable(j)) continue;
+    const cudaError_t q = cudaEventQuery(j->ev);
+    if (q == cudaErrorNotReady) continue;
+    fin.emplace_back(j, q);
+  }
+  for (auto& f : fin) {
+    Job* j = f.first;
+    if (j->state != FPM_JOB_ACTIVE) continue;
+    if (f.second != cudaSuccess) {
+      cudaGetLastError();
+      j->in_flight = false;
+      fail_job(s, j, cudaGetErrorString(f.second));
+      continue;
+    }
+    const int rc = retire_epoch(s, j);
+    if (rc) fail_job(s, j, fpm_last_error(j->h));
+  }
+  std::vector<Job*> still;
+  for (Job* j : s->active)
+    if (j->state == FPM_JOB_ACTIVE) still.push_back(j);
   s->active.swap(still);
-  // admit queued jobs in arrival order, each one that fits the remaining
-  // memory (first fit: a job too large for now does not hold back smaller
-  // ones behind it), while slots allow
+  // 2. admit queued jobs in arrival order, each one that fits the remaining
+  //    memory (first fit: a job too large for now does not hold back smaller
+  //    ones behind it), while slots allow
   for (auto it = s->queue.begin(); it != s->queue.end() && (int)s->active.size() < s->max_active;) {
     Job* j = *it;
     if (s->used + j->footprint > s->budget) {
@@ -277,8 +498,39 @@ int fpm_server_tick(fpm_server* s, int32_t* n_active, int32_t* n_queued) {
     }
     s->active.push_back(j);
   }
+  // 3. the next epoch of every resident job not in flight: one round per group
+  std::map<std::string, std::vector<Job*>> groups;
+  for (Job* j : s->active) {
+    if (j->in_flight) continue;
+    if (groupable(j)) {
+      groups[group_key(j)].push_back(j);
+    } else if (launch_epoch(j)) {
+      fail_job(s, j, fpm_last_error(j->h));
+    }
+  }
+  for (auto& kv : groups)
+    if (launch_round(s, kv.second))
+      for (Job* j : kv.second)
+        if (j->state == FPM_JOB_ACTIVE) {
+          j->in_flight = false;
+          fail_job(s, j, "round launch failed");
+        }
+  still.clear();
+  for (Job* j : s->active)
+    if (j->state == FPM_JOB_ACTIVE) still.push_back(j);
+  s->active.swap(still);
   if (n_active) *n_active = (int32_t)s->active.size();
   if (n_queued) *n_queued = (int32_t)s->queue.size();
+  return FPM_OK;
+}
+
+int fpm_server_stats(const fpm_server* s, int64_t* rounds, int64_t* round_epochs, int64_t* max_jobs_per_round,
+                     int64_t* launches) {
+  if (!s) return FPM_ERR_ARG;
+  if (rounds) *rounds = s->n_rounds;
+  if (round_epochs) *round_epochs = s->n_round_epochs;
+  if (max_jobs_per_round) *max_jobs_per_round = s->max_round_jobs;
+  if (launches) *launches = s->n_launches;
   return FPM_OK;
 }
 

@@ -183,7 +183,8 @@ __device__ void led_scalars(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc2)
   }
 }
 
-__global__ void __launch_bounds__(UPD_NT) update_kernel(const UpdArgs a) {
+// CTA bid of the update of the job described by a.
+__device__ __forceinline__ void update_body(const UpdArgs& a, const int bid) {
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   __shared__ int2 corner[MAX_BATCH];  // (first column, first row) of each slot's box
   __shared__ int lst[MAX_BATCH];
@@ -193,13 +194,13 @@ __global__ void __launch_bounds__(UPD_NT) update_kernel(const UpdArgs a) {
   // kernel only reads O, and lets this kernel start only after the previous
   // update has completed). The gradient boxes and partials come after it.
   const float2 bc = a.coef ? a.coef[a.step_off] : make_float2(1.f, 1.f);
-  if (blockIdx.x < NSC) {  // the scalar parameters (the longest dependency chain)
-    if (blockIdx.x < 16) shared_scalar(a, blockIdx.x, bc.x, bc.y);
+  if (bid < NSC) {  // the scalar parameters (the longest dependency chain)
+    if (bid < 16) shared_scalar(a, bid, bc.x, bc.y);
     else led_scalars(a, bc.x, bc.y);
     return;
   }
   if (!a.assemble && !(a.learn & 1u)) return;
-  const int x = a.x_lo + (int)blockIdx.x - NSC;
+  const int x = a.x_lo + bid - NSC;
   const int W = a.W;
   const int2 span = a.span[x];
   for (int kk = threadIdx.x; kk < a.B; kk += blockDim.x) {
@@ -288,9 +289,43 @@ __global__ void __launch_bounds__(UPD_NT) update_kernel(const UpdArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(UPD_NT) update_kernel(const UpdArgs a) { update_body(a, (int)blockIdx.x); }
+
+// Several jobs in one launch (the serving loop): CTA q is CTA map[q].y of the
+// update of job map[q].x, whose arguments are copied to shared memory.
+__global__ void __launch_bounds__(UPD_NT) update_kernel_jobs(const UpdArgs* __restrict__ jobs,
+                                                             const int2* __restrict__ map) {
+  __shared__ UpdArgs sa;
+  const int2 q = map[blockIdx.x];
+  if (threadIdx.x == 0) sa = jobs[q.x];
+  __syncthreads();
+  update_body(sa, q.y);
+}
+
+int update_ctas(const UpdArgs& a) { return a.n_cols + NSC; }
+
 cudaError_t update_prepare() {
-  return cudaFuncSetAttribute(update_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+  cudaError_t e = cudaFuncSetAttribute(update_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                       cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(update_kernel_jobs, cudaFuncAttributePreferredSharedMemoryCarveout,
                               cudaSharedmemCarveoutMaxShared);
+}
+
+cudaError_t launch_update_jobs(const UpdArgs* jobs, const int2* map, int n_ctas, int B_max, cudaStream_t s,
+                               bool pdl) {
+  if (n_ctas < 1) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)n_ctas, 1, 1);
+  cfg.blockDim = dim3(UPD_NT, 1, 1);
+  cfg.dynamicSmemBytes = sizeof(double) * 3 * (size_t)B_max;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, update_kernel_jobs, jobs, map);
 }
 
 cudaError_t launch_update(const UpdArgs& a, cudaStream_t s, bool pdl) {

@@ -34,7 +34,7 @@ EXPORTS = ("fpm_create", "fpm_set_hparams", "fpm_get_hparams", "fpm_load", "fpm_
            "fpm_forward_fields", "fpm_backward_fields", "fpm_get", "fpm_set", "fpm_set_object_field",
            "fpm_state_size", "fpm_get_state", "fpm_set_state", "fpm_dims", "fpm_epoch_permutation",
            "fpm_gradients_static", "fpm_job_footprint", "fpm_server_create", "fpm_server_submit",
-           "fpm_server_tick", "fpm_server_status", "fpm_server_result", "fpm_server_clock",
+           "fpm_server_tick", "fpm_server_status", "fpm_server_result", "fpm_server_clock", "fpm_server_stats",
            "fpm_server_error", "fpm_server_destroy", "fpm_destroy", "fpm_last_error")
 
 

@@ -41,6 +41,8 @@ def _declare(L):
         "fpm_server_status": ([vp, i64, ctypes.POINTER(JobStatus)], i32),
         "fpm_server_result": ([vp, i64, vp, vp, vp, vp, vp], i32),
         "fpm_server_clock": ([vp], ctypes.c_double),
+        "fpm_server_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)],
+                             i32),
         "fpm_server_error": ([vp], ctypes.c_char_p),
         "fpm_server_destroy": ([vp], None),
     }
@@ -115,6 +117,13 @@ class Server:
 
     def clock(self) -> float:
         return lib().fpm_server_clock(self._h)
+
+    def stats(self) -> dict:
+        """Rounds launched, job epochs they ran, most jobs in one round, kernel launches."""
+        v = [ctypes.c_int64() for _ in range(4)]
+        self._check(lib().fpm_server_stats(self._h, *[ctypes.byref(x) for x in v]))
+        return dict(rounds=v[0].value, round_epochs=v[1].value, max_jobs_per_round=v[2].value,
+                    launches=v[3].value)
 
     def close(self):
         if getattr(self, "_h", None):

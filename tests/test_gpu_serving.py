@@ -75,3 +75,21 @@ def test_admission_waits_for_memory():
     with pytest.raises(Exception):                    # a job larger than the whole budget is refused
         srv = sv.Server(fp_small, 4)
         srv.submit(big1[1], big1[2])
+
+
+def test_same_shape_jobs_share_rounds_and_match_alone():
+    """Jobs of the same shape run in one round (one launch per step for all of
+    them); each result equals the job served alone, bit for bit."""
+    jobs = [_job(256, 7, 20 + k) for k in range(3)]
+    srv = sv.Server(8 << 30, 16)
+    ids, st, wall = sv.run_arrivals(srv, [(d, s, 0.0) for c, d, s in jobs])
+    stats = srv.stats()
+    res = [srv.result(i, c.N, c.n_leds) for i, (c, d, s) in zip(ids, jobs)]
+    srv.close()
+    assert all(x["state"] == sv.JOB_DONE for x in st)
+    assert stats["max_jobs_per_round"] == 3
+    assert stats["round_epochs"] == sum(x["epochs"] for x in st)
+    for job, r in zip(jobs, res):
+        st1, res1 = _serve([(job, 0.0)])
+        assert np.array_equal(res1[0]["object"], r["object"])
+        assert np.array_equal(res1[0]["gamma"], r["gamma"])
