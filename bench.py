@@ -299,7 +299,7 @@ def serving_section(n_jobs=16, rate_hz=40.0, seed=5):
     budget = int(0.6 * free)
     run_serving = serving_run(jobs, budget, max_active=64)
     run_serial = serving_run(jobs, budget, max_active=1)
-    same = serving_jobs(n_jobs, rate_hz, seed + 1, shape=(512, 11))
+    same = serving_jobs(n_jobs, 1000.0, seed + 1, shape=(512, 11))
     same_serving = serving_run(same, budget, max_active=64)
     same_serial = serving_run(same, budget, max_active=1)
     return {"what": f"{n_jobs} jobs, Poisson arrivals {rate_hz:g}/s, ROI from {{256,512,1024,2048}}^2 at "
@@ -309,7 +309,7 @@ def serving_section(n_jobs=16, rate_hz=40.0, seed=5):
                     "the same GPU",
             "mix": [f"{N}^2/{g}x{g}" for _, _, _, N, g in jobs],
             "hbm_budget_bytes": budget, "continuous": run_serving, "serial": run_serial,
-            "same_shape": {"what": f"{n_jobs} jobs of 512^2 / 11x11, the same arrivals process",
+            "same_shape": {"what": f"{n_jobs} jobs of 512^2 / 11x11 arriving in a burst (Poisson 1000/s)",
                            "continuous": same_serving, "serial": same_serial}}
 
 
