@@ -54,11 +54,14 @@ struct LedLayout {
   // Phase A pushes its results into the row owners' staging rows (posted
   // remote stores) instead of phase B pulling them; m = 512 lacks the room.
   static constexpr bool PUSH = M <= 256;
+  // staging rows are stored by box column, RS row slots per column (even, for
+  // 16-byte stores of row pairs)
+  static constexpr int RS = ROWS + 2;
   static size_t bytes(int W) {
     const int chunk = (W + C - 1) / C;
     return sizeof(float) * (size_t)ROWS * M +
            sizeof(float2) * ((size_t)chunk * TS + (size_t)NG * FS + M + NTW2 + (size_t)chunk * W +
-                             (PUSH ? (size_t)ROWS * W : 0)) +
+                             (PUSH ? (size_t)RS * W + 1 : 0)) +   // + 1: 16-byte alignment of the staging rows
            sizeof(float) * (NPOLY + 14 * 15 + 2 + (size_t)NW * NACC) + sizeof(double) * 16;
   }
 };
@@ -116,8 +119,10 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
   float2* tws = fb + NG * FS;                             // [M] twiddle table
   float2* tw2 = tws + M;                                  // [15][16] second-pass twiddles (M = 256)
   float2* Ob = tw2 + L::NTW2;                             // [chunk][W] O on this CTA's box columns
-  float2* Rw = Ob + (size_t)chunk * W;                    // [ROWS][W] this CTA's rows of T (push form)
-  float* poly = reinterpret_cast<float*>(Rw + (L::PUSH ? (size_t)ROWS * W : 0));  // K[15] Dx[10] Dy[10]
+  // [W][RS] this CTA's rows of T by box column (push form), 16-byte aligned
+  float2* Rw = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(Ob + (size_t)chunk * W) + 15) & ~(uintptr_t)15);
+  float* poly = L::PUSH ? reinterpret_cast<float*>(Rw + (size_t)L::RS * W)      // K[15] Dx[10] Dy[10]
+                        : reinterpret_cast<float*>(Ob + (size_t)chunk * W);
   float* zmt = poly + L::NPOLY;                           // [14 * 15] Zernike -> monomial table
   float* red = zmt + 14 * 15 + 2;                         // [NW][NACC]
   double* dsum = reinterpret_cast<double*>(red + NW * NACC);  // [16] (8-byte aligned: float counts are even)
@@ -206,13 +211,18 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
     }
     __syncwarp();
     transform<M, +1>(buf, TW, tws, tw2, j);
-    if (act)
-      for (int t = j; t < M; t += G) {
-        if constexpr (L::PUSH)  // row t of T belongs to CTA t / ROWS
-          cluster.map_shared_rank(Rw, t / ROWS)[(t % ROWS) * W + c] = buf[bidx<M>(t)];
-        else
-          T[(c - c0) * TS + t] = buf[bidx<M>(t)];
+    if (act) {
+      if constexpr (L::PUSH) {
+        // rows t, t + 1 of T belong to CTA t / ROWS: one 16-byte remote store per pair
+        for (int t = 2 * j; t < M; t += 2 * G) {
+          const float2 u0 = buf[bidx<M>(t)], u1 = buf[bidx<M>(t + 1)];
+          float4* dst = reinterpret_cast<float4*>(cluster.map_shared_rank(Rw, t / ROWS) + (size_t)c * L::RS + t % ROWS);
+          *dst = make_float4(u0.x, u0.y, u1.x, u1.y);
+        }
+      } else {
+        for (int t = j; t < M; t += G) T[(c - c0) * TS + t] = buf[bidx<M>(t)];
       }
+    }
     __syncwarp();
   }
   cp_async_wait<0>();  // image rows
@@ -233,7 +243,7 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
       for (int t = h + 1 + j; t < M - h; t += G) buf[bidx<M>(t)] = make_float2(0.f, 0.f);  // outside the box
       if constexpr (L::PUSH) {
         for (int c = j; c < W; c += G)
-          buf[bidx<M>((c - h) & (M - 1))] = act ? Rw[yl * W + c] : make_float2(0.f, 0.f);
+          buf[bidx<M>((c - h) & (M - 1))] = act ? Rw[(size_t)c * L::RS + yl] : make_float2(0.f, 0.f);
       } else
       // remote loads from the owning CTAs, eight in flight before any is stored
       for (int cb = j; cb < W; cb += 8 * G) {
