@@ -93,3 +93,30 @@ def test_same_shape_jobs_share_rounds_and_match_alone():
         st1, res1 = _serve([(job, 0.0)])
         assert np.array_equal(res1[0]["object"], r["object"])
         assert np.array_equal(res1[0]["gamma"], r["gamma"])
+
+
+def test_tensor_core_form_job_runs_beside_rounds():
+    """A job in a tensor-core DFT form runs its own epochs (outside the rounds)
+    next to same-shape FFT jobs, and equals a direct run of its form."""
+    c, desc_fft, stack = _job(256, 7, 30, max_epochs=3)
+    nominal = S.led_grid(c.grid, c.pitch, c.jitter, c.seed)[0]
+    desc_tc = sv.job_desc(c.m, c.s, nominal, c.R, c.lambda_um, c.dk_per_um, c.edge, batch=c.B, max_epochs=3,
+                          rel_tol=0.0, seed=c.seed, lr=dict(object=0.5), precision="bf16x3")
+    other = _job(256, 7, 31, max_epochs=3)
+    srv = sv.Server(8 << 30, 16)
+    ids, st, wall = sv.run_arrivals(srv, [(desc_tc, stack, 0.0), (desc_fft, stack, 0.0), (other[1], other[2], 0.0)])
+    res = srv.result(ids[0], c.N, c.n_leds)
+    stats = srv.stats()
+    srv.close()
+    assert all(x["state"] == sv.JOB_DONE for x in st)
+    assert stats["max_jobs_per_round"] == 2          # the two FFT jobs; the tensor-core job ran on its own
+    eng = Engine(c.m, c.s, nominal, c.R, c.lambda_um, c.dk_per_um, c.edge)
+    eng.set_hparams(lr=dict(object=0.5), precision="bf16x3")
+    eng.load(stack, init=True)
+    for e in range(3):
+        perm = S.epoch_permutation(c.n_leds, c.seed, e)
+        nfull = c.n_leds // c.B
+        eng.run(perm[:nfull * c.B].reshape(nfull, c.B))
+        if c.n_leds % c.B:
+            eng.step(perm[nfull * c.B:])
+    assert np.array_equal(eng.get()["object"], res["object"])
