@@ -279,9 +279,20 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
         buf[bidx<M>(t)] = make_float2(0.f, 0.f);
       }
     } else if (a.mode == MODE_LOSS && a.loss == 0 && a.meas_is_amp) {
-#pragma unroll 4
-      for (int t = j; t < M; t += G)
-        buf[bidx<M>(t)] = residual_amp_pixel(cscale(buf[bidx<M>(t)], sc), ms[yl * M + t], sg, acc_loss, acc_g);
+      // all of this thread's pixels loaded first: the stores into buf cannot
+      // then hold back the loads (the compiler cannot tell buf and ms apart)
+      constexpr int NU = M / G;
+      float2 pv[NU];
+      float av[NU];
+#pragma unroll
+      for (int u = 0; u < NU; ++u) {
+        pv[u] = buf[bidx<M>(j + G * u)];
+        av[u] = ms[yl * M + j + G * u];
+      }
+#pragma unroll
+      for (int u = 0; u < NU; ++u) pv[u] = residual_amp_pixel(cscale(pv[u], sc), av[u], sg, acc_loss, acc_g);
+#pragma unroll
+      for (int u = 0; u < NU; ++u) buf[bidx<M>(j + G * u)] = pv[u];
     } else if (a.mode == MODE_LOSS && a.loss == 0) {
 #pragma unroll 4
       for (int t = j; t < M; t += G)
