@@ -462,7 +462,27 @@ __device__ __forceinline__ void fft256_group(float2* __restrict__ buf, const flo
     __syncwarp();
   }
 }
+// The same transform with the first pass's inputs (elements j + 16 r) given
+// in registers: buf serves only as the exchange between the two passes and
+// holds the result as fft256_group leaves it. Spares a zero-filled buffer
+// when most inputs are known to be zero.
+template <int DIR>
+__device__ __forceinline__ void fft256_group_in(float2 (&v)[16], float2* __restrict__ buf,
+                                                const float2* __restrict__ tw2, int j) {
+  dft16<DIR>(v);
+  __syncwarp();
+  r16_store(buf, j, 0, v);
+  __syncwarp();
+  r16_load<DIR>(buf, tw2, j, 1, v);
+  __syncwarp();
+  r16_store(buf, j, 1, v);
+  __syncwarp();
+}
 #endif
+
+// Box column (or row) stored at transform index t when a box of half-width h
+// is centred on index 0 (indices t <= h and t >= n - h), else -1.
+FPM_HD int box_index(int t, int n, int h) { return t <= h ? t + h : (t >= n - h ? t - n + h : -1); }
 
 // ---- 512 points: radix 16, radix 16, radix 2 (32 threads x 16 points) ----
 // Second-pass twiddles depend on k = j mod 16 only: tw2[(r-1) * 16 + k] =

@@ -199,7 +199,8 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
     const bool act = c < c1;
     const float2* Oc = Ob + (size_t)(act ? c - c0 : 0) * W + h;   // index by ky
     const float qx = (float)(c - h) - dlx;
-    for (int t = h + 1 + j; t < M - h; t += G) buf[bidx<M>(t)] = make_float2(0.f, 0.f);  // outside the box
+    if constexpr (M != 256)  // (m = 256 reads only the box back below)
+      for (int t = h + 1 + j; t < M - h; t += G) buf[bidx<M>(t)] = make_float2(0.f, 0.f);  // outside the box
     for (int r = j; r < W; r += G) {
       const int ky = r - h;
       float2 v = make_float2(0.f, 0.f);
@@ -210,7 +211,16 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
       buf[bidx<M>(ky & (M - 1))] = v;
     }
     __syncwarp();
-    transform<M, +1>(buf, TW, tws, tw2, j);
+    if constexpr (M == 256) {
+      // first-pass inputs: the box values just written, zeros elsewhere
+      float2 v[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r)
+        v[r] = box_index(j + 16 * r, M, h) >= 0 ? buf[bidx<M>(j + 16 * r)] : make_float2(0.f, 0.f);
+      fft256_group_in<+1>(v, buf, tw2, j);
+    } else {
+      transform<M, +1>(buf, TW, tws, tw2, j);
+    }
     if (act) {
       if constexpr (L::PUSH) {
         // rows t, t + 1 of T belong to CTA t / ROWS: one 16-byte remote store per pair
@@ -239,6 +249,15 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
     if (stored) {
       for (int t = j; t < M; t += G)
         buf[bidx<M>(t)] = act ? a.psi[((size_t)k * M + y) * M + t] : make_float2(0.f, 0.f);
+    } else if constexpr (M == 256 && L::PUSH) {
+      // first-pass inputs straight from the staging rows (zeros outside the box)
+      float2 v[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        const int c = box_index(j + 16 * r, M, h);
+        v[r] = (act && c >= 0) ? Rw[(size_t)c * L::RS + yl] : make_float2(0.f, 0.f);
+      }
+      fft256_group_in<+1>(v, buf, tw2, j);
     } else {
       for (int t = h + 1 + j; t < M - h; t += G) buf[bidx<M>(t)] = make_float2(0.f, 0.f);  // outside the box
       if constexpr (L::PUSH) {
