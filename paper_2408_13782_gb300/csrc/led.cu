@@ -350,9 +350,16 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
   for (int cb = c0; cb < c1; cb += NG) {
     const int c = cb + grp;
     const bool act = c < c1;
-    for (int t = j; t < M; t += G) buf[bidx<M>(t)] = act ? T[(c - c0) * TS + t] : make_float2(0.f, 0.f);
-    __syncwarp();
-    transform<M, -1>(buf, TW, tws, tw2, j);
+    if constexpr (M == 256) {  // first-pass inputs straight from T
+      float2 v[16];
+#pragma unroll
+      for (int r = 0; r < 16; ++r) v[r] = act ? T[(c - c0) * TS + j + 16 * r] : make_float2(0.f, 0.f);
+      fft256_group_in<-1>(v, buf, tw2, j);
+    } else {
+      for (int t = j; t < M; t += G) buf[bidx<M>(t)] = act ? T[(c - c0) * TS + t] : make_float2(0.f, 0.f);
+      __syncwarp();
+      transform<M, -1>(buf, TW, tws, tw2, j);
+    }
     if (act) {
       const float2* Oc = Ob + (size_t)(c - c0) * W + h;
       const float qx = (float)(c - h) - dlx;
