@@ -190,11 +190,37 @@ FPM_HD float pupil_amp(float qy, float qx, const PupilConst& P) {
   return fminf(fmaxf(P.R + 0.5f - r, 0.f), 1.f);
 }
 
+// a / b by the hardware reciprocal on the device (at most 2 ulp for the
+// divisors used here, which are of order 1 / lambda); plain division on the host.
+FPM_HD float fdiv_fast(float a, float b) {
+#ifdef __CUDA_ARCH__
+  return __fdividef(a, b);
+#else
+  return a / b;
+#endif
+}
+
+// sin and cos of a pupil phase (at most tens of radians). On the device the
+// argument is first reduced to [-pi, pi] by the Cody-Waite two-constant scheme
+// (2 pi = C1 + C2 with C1 the float nearest 2 pi and C2 the remainder), so the
+// hardware sine and cosine can be used: their absolute error is documented as
+// 2^-21.41 on that interval. The host calls sincosf.
+FPM_HD void sincos_phase(float x, float* s, float* c) {
+#ifdef __CUDA_ARCH__
+  const float n = rintf(x * 0.15915494309189535f);  // x / (2 pi), rounded
+  float r = fmaf(-n, 6.28318548202514648f, x);
+  r = fmaf(-n, -1.7484556000744883e-07f, r);
+  __sincosf(r, s, c);
+#else
+  sincosf(x, s, c);
+#endif
+}
+
 FPM_HD float defocus_kappa(float r2, const PupilConst& P, float* root_out) {
   const float k2 = r2 * P.dk2;
   const float root = sqrtf(P.inv_lambda * P.inv_lambda - k2);
   *root_out = root;
-  return -6.283185307179586f * k2 / (root + P.inv_lambda);
+  return fdiv_fast(-6.283185307179586f * k2, root + P.inv_lambda);
 }
 
 FPM_HD float2 pupil_value(float qy, float qx, const PupilConst& P,
@@ -209,7 +235,7 @@ FPM_HD float2 pupil_value(float qy, float qx, const PupilConst& P,
   float root;
   const float kap = defocus_kappa(qx * qx + qy * qy, P, &root);
   float sn, cs;
-  sincosf(fmaf(z, kap, th), &sn, &cs);
+  sincos_phase(fmaf(z, kap, th), &sn, &cs);
   return make_float2(A * cs, A * sn);
 }
 
@@ -226,7 +252,7 @@ FPM_HD float2 pupil_value_poly(float qy, float qx, const PupilConst& P, const fl
   float root;
   const float kap = defocus_kappa(qx * qx + qy * qy, P, &root);
   float sn, cs;
-  sincosf(fmaf(z, kap, th), &sn, &cs);
+  sincos_phase(fmaf(z, kap, th), &sn, &cs);
   return make_float2(A * cs, A * sn);
 }
 

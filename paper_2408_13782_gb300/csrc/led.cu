@@ -198,16 +198,18 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
     const int c = cb + grp;
     const bool act = c < c1;
     const float2* Oc = Ob + (size_t)(act ? c - c0 : 0) * W + h;   // index by ky
-    const float qx = (float)(c - h) - dlx;
+    const float qx = (float)(c - h) - dlx, qx2 = qx * qx;
+    ColPoly cp;  // the aberration phase along this column
+    col_poly(qx * P.Rinv, poly, cp);
     if constexpr (M != 256)  // (m = 256 reads only the box back below)
       for (int t = h + 1 + j; t < M - h; t += G) buf[bidx<M>(t)] = make_float2(0.f, 0.f);  // outside the box
     for (int r = j; r < W; r += G) {
       const int ky = r - h;
+      const float qy = (float)ky - dly, r2 = fmaf(qy, qy, qx2);
+      float rad;
+      const float A = act ? pupil_amp_r2(r2, P, rad) : 0.f;
       float2 v = make_float2(0.f, 0.f);
-      if (act) {
-        const float2 Mv = pupil_value_poly((float)ky - dly, qx, P, poly, zdef);
-        if (Mv.x != 0.f || Mv.y != 0.f) v = cmul(Oc[ky], Mv);
-      }
+      if (A > 0.f) v = cmul(Oc[ky], pupil_col(qy, r2, A, P, cp, zdef));
       buf[bidx<M>(ky & (M - 1))] = v;
     }
     __syncwarp();
@@ -362,16 +364,22 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
     }
     if (act) {
       const float2* Oc = Ob + (size_t)(c - c0) * W + h;
-      const float qx = (float)(c - h) - dlx;
+      const float qx = (float)(c - h) - dlx, qx2 = qx * qx;
+      ColPoly cp;  // the aberration phase along this column
+      col_poly(qx * P.Rinv, poly, cp);
+      float S[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // sum t(p) y^b over this thread's pixels of the column
       for (int r = j; r < W; r += G) {
         const int ky = r - h;
-        const float qy = (float)ky - dly;
+        const float qy = (float)ky - dly, r2 = fmaf(qy, qy, qx2);
+        float rad;
+        const float A = pupil_amp_r2(r2, P, rad);
         float2 out = make_float2(0.f, 0.f);
-        const float A = pupil_amp(qy, qx, P);
         if (A > 0.f)
-          out = box_pixel(qy, qx, A, cscale(buf[bidx<M>(ky & (M - 1))], inv_m2), Oc[ky], P, poly, zdef, bacc);
+          out = box_pixel_col(qy, qx, r2, A, rad, cscale(buf[bidx<M>(ky & (M - 1))], inv_m2), Oc[ky], P, cp, zdef, S,
+                              bacc);
         gb[(size_t)c * W + r] = out;
       }
+      col_fold(cp, S, bacc);
     }
     __syncwarp();
   }

@@ -75,7 +75,7 @@ __device__ __forceinline__ float2 box_pixel(float qy, float qx, float A, float2 
   float root;
   const float kap = defocus_kappa(r2, P, &root);
   float sn, cs;
-  sincosf(fmaf(zdef, kap, th), &sn, &cs);
+  sincos_phase(fmaf(zdef, kap, th), &sn, &cs);
   const float2 e = make_float2(cs, sn);
   const float2 Mv = cscale(e, A);
   const float2 gM = cmulc(o, gphi);     // conj(O) gPhi
@@ -84,7 +84,7 @@ __device__ __forceinline__ float2 box_pixel(float qy, float qx, float A, float2 
 #pragma unroll
   for (int q = 0; q < 15; ++q) acc.m[q] = fmaf(tt, mo[q], acc.m[q]);
   acc.def = fmaf(tt, kap, acc.def);
-  const float dk = -6.283185307179586f * P.dk2 / root;  // d kappa / d q = dk * q
+  const float dk = fdiv_fast(-6.283185307179586f * P.dk2, root);  // d kappa / d q = dk * q
   const float dchiy = fmaf(dthy, P.Rinv, zdef * dk * qy);
   const float dchix = fmaf(dthx, P.Rinv, zdef * dk * qx);
   float dAy = 0.f, dAx = 0.f;
@@ -98,6 +98,116 @@ __device__ __forceinline__ float2 box_pixel(float qy, float qx, float A, float2 
   acc.dy -= fmaf(tt, dchiy, ee * dAy);
   acc.dx -= fmaf(tt, dchix, ee * dAx);
   return cmulc(Mv, gphi);               // conj(M) gPhi
+}
+
+// ---- column form (fixed qx, pixels along y) ------------------------------
+// Monomial x^a y^b of the aberration polynomials sits at (a+b)(a+b+1)/2 + b.
+__host__ __device__ constexpr int mono_idx(int a, int b) { return (a + b) * (a + b + 1) / 2 + b; }
+
+// On one box column x = qx / R is fixed, so theta(x, y) = sum_b th[b] y^b and
+// its x / y derivatives are cubic polynomials in y with coefficients that
+// depend on x only: a pixel then costs three Horner steps in y instead of the
+// 15 monomials and 35 products of box_pixel.
+struct ColPoly {
+  float x;
+  float th[5], gx[4], gy[4];
+};
+
+// poly: K[15], Dx[10], Dy[10] (theta and its gradient as monomials of q / R).
+__device__ __forceinline__ void col_poly(float x, const float* poly, ColPoly& cp) {
+  cp.x = x;
+#pragma unroll
+  for (int b = 0; b <= 4; ++b) {
+    float s = poly[mono_idx(4 - b, b)];
+#pragma unroll
+    for (int a = 3 - b; a >= 0; --a) s = fmaf(s, x, poly[mono_idx(a, b)]);
+    cp.th[b] = s;
+  }
+#pragma unroll
+  for (int b = 0; b <= 3; ++b) {
+    float sx = poly[15 + mono_idx(3 - b, b)], sy = poly[25 + mono_idx(3 - b, b)];
+#pragma unroll
+    for (int a = 2 - b; a >= 0; --a) {
+      sx = fmaf(sx, x, poly[15 + mono_idx(a, b)]);
+      sy = fmaf(sy, x, poly[25 + mono_idx(a, b)]);
+    }
+    cp.gx[b] = sx;
+    cp.gy[b] = sy;
+  }
+}
+
+__device__ __forceinline__ float col_theta(const ColPoly& cp, float y) {
+  return fmaf(fmaf(fmaf(fmaf(cp.th[4], y, cp.th[3]), y, cp.th[2]), y, cp.th[1]), y, cp.th[0]);
+}
+
+// Pupil amplitude from r2 = |q|^2; rad = |q| is also returned (anti-aliased
+// edge only: the hard edge needs no square root).
+__device__ __forceinline__ float pupil_amp_r2(float r2, const PupilConst& P, float& rad) {
+  if (P.hard_edge) {
+    rad = 0.f;
+    return r2 <= P.R * P.R ? 1.f : 0.f;
+  }
+  rad = sqrtf(r2);
+  return fminf(fmaxf(P.R + 0.5f - rad, 0.f), 1.f);
+}
+
+// Pupil value M = A exp(i chi) of a pixel of the column (A > 0 given).
+__device__ __forceinline__ float2 pupil_col(float qy, float r2, float A, const PupilConst& P, const ColPoly& cp,
+                                            float zdef) {
+  const float th = col_theta(cp, qy * P.Rinv);
+  float root;
+  const float kap = defocus_kappa(r2, P, &root);
+  float sn, cs;
+  sincos_phase(fmaf(zdef, kap, th), &sn, &cs);
+  return make_float2(A * cs, A * sn);
+}
+
+// box_pixel on a column: the monomial moments are kept as the column sums
+// S[b] = sum t(p) y^b and folded into acc.m by col_fold once per column.
+__device__ __forceinline__ float2 box_pixel_col(float qy, float qx, float r2, float A, float rad, float2 gphi, float2 o,
+                                                const PupilConst& P, const ColPoly& cp, float zdef, float (&S)[5],
+                                                BoxAcc& acc) {
+  const float y = qy * P.Rinv;
+  const float th = col_theta(cp, y);
+  const float dthx = fmaf(fmaf(fmaf(cp.gx[3], y, cp.gx[2]), y, cp.gx[1]), y, cp.gx[0]);
+  const float dthy = fmaf(fmaf(fmaf(cp.gy[3], y, cp.gy[2]), y, cp.gy[1]), y, cp.gy[0]);
+  float root;
+  const float kap = defocus_kappa(r2, P, &root);
+  float sn, cs;
+  sincos_phase(fmaf(zdef, kap, th), &sn, &cs);
+  const float2 e = make_float2(cs, sn);
+  const float2 Mv = cscale(e, A);
+  const float2 gM = cmulc(o, gphi);     // conj(O) gPhi
+  const float tt = -cmulc(gM, Mv).y;    // dL/dchi = Re(conj(gM) i M)
+  const float ee = cmulc(gM, e).x;      // dL/dA   = Re(conj(gM) e^{i chi})
+  const float y2 = y * y;
+  S[0] += tt;
+  S[1] = fmaf(tt, y, S[1]);
+  S[2] = fmaf(tt, y2, S[2]);
+  S[3] = fmaf(tt, y2 * y, S[3]);
+  S[4] = fmaf(tt, y2 * y2, S[4]);
+  acc.def = fmaf(tt, kap, acc.def);
+  const float dk = fdiv_fast(-6.283185307179586f * P.dk2, root);  // d kappa / d q = dk * q
+  const float dchiy = fmaf(dthy, P.Rinv, zdef * dk * qy);
+  const float dchix = fmaf(dthx, P.Rinv, zdef * dk * qx);
+  float dAy = 0.f, dAx = 0.f;
+  if (!P.hard_edge && rad > P.R - 0.5f && rad < P.R + 0.5f) {
+    dAy = -qy / rad;
+    dAx = -qx / rad;
+  }
+  acc.dy -= fmaf(tt, dchiy, ee * dAy);
+  acc.dx -= fmaf(tt, dchix, ee * dAx);
+  return cmulc(Mv, gphi);               // conj(M) gPhi
+}
+
+// acc.m[x^a y^b] += x^a S[b] for the column's x.
+__device__ __forceinline__ void col_fold(const ColPoly& cp, const float (&S)[5], BoxAcc& acc) {
+  const float x = cp.x, x2 = x * x;
+  const float xp[5] = {1.f, x, x2, x2 * x, x2 * x2};
+#pragma unroll
+  for (int b = 0; b <= 4; ++b)
+#pragma unroll
+    for (int a = 0; a + b <= 4; ++a) acc.m[mono_idx(a, b)] = fmaf(xp[a], S[b], acc.m[mono_idx(a, b)]);
 }
 
 __device__ __forceinline__ float warp_sum_f(float v) {
