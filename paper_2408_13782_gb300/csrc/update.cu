@@ -186,8 +186,12 @@ __device__ void led_scalars(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc2)
 // CTA bid of the update of the job described by a.
 __device__ __forceinline__ void update_body(const UpdArgs& a, const int bid) {
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-  __shared__ int2 corner[MAX_BATCH];  // (first column, first row) of each slot's box
-  __shared__ int lst[MAX_BATCH];
+  // the launch's dynamic shared memory (3 B doubles) holds, in the column
+  // CTAs, the first column and row of each slot's box and the list of slots
+  // that cover the column: batch-sized, so the CTA stays small
+  extern __shared__ double dyn_smem[];
+  int2* corner = reinterpret_cast<int2*>(dyn_smem);  // [B]
+  int* lst = reinterpret_cast<int*>(corner + a.B);     // [B]
   __shared__ int nl;
   // Everything read before the wait is untouched by the LED kernel this
   // kernel depends on: step coefficients, LED tables, and O, m, v (the LED
