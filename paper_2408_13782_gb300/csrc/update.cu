@@ -18,7 +18,10 @@
 
 namespace fpmk {
 
-constexpr int UPD_NT = 256;
+// Threads per CTA: enough that a column of the update region is one element
+// per thread (up to 320 rows; 273 on a 15 x 15 grid of pitch 12 at m = 256),
+// so every element's box loads and Adam step are in flight at once.
+constexpr int UPD_NT = 320;
 
 __device__ __forceinline__ void adam1(float& w, float& m, float& v, float g, float lr_bc1, float inv_sqrt_bc2,
                                       float b1, float b2, float eps) {
@@ -211,8 +214,8 @@ __device__ __forceinline__ void update_body(const UpdArgs& a, const int bid) {
     const int4 sl = a.slot[kk];
     corner[kk] = make_int2(a.N / 2 + sl.z - a.h, a.N / 2 + sl.y - a.h);
   }
-  // this thread's first two elements of the column (columns are up to ~2 x
-  // 256 rows tall), loaded before the wait
+  // this thread's first two elements of the column (taller columns at
+  // m = 512 need the second), loaded before the wait
   const int y0 = span.x + (int)threadIdx.x, y1 = y0 + (int)blockDim.x;
   float2 w0 = make_float2(0.f, 0.f), m0 = w0, v0 = w0, w1 = w0, m1 = w0, v1 = w0;
   if (!a.assemble && y0 < span.y) {
