@@ -237,11 +237,24 @@ __device__ __forceinline__ void write_partials(float acc_loss, float acc_g, cons
   vals[A_DEF] = b.def;
   vals[A_DY] = b.dy;
   vals[A_DX] = b.dx;
+  // Warp sums of all NACC values at once by recursive halving: at the step of
+  // distance o every lane keeps the half of its vector selected by bit o of
+  // its lane index and adds the partner's copy of that half; after five steps
+  // lane q holds the warp's total of value q (31 shuffles instead of 5 NACC).
+  float v[32];
 #pragma unroll
-  for (int q = 0; q < NACC; ++q) {
-    const float s = warp_sum_f(vals[q]);
-    if (lane == 0) red[warp * NACC + q] = s;
+  for (int q = 0; q < 32; ++q) v[q] = q < NACC ? vals[q] : 0.f;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float keep = up ? v[i + o] : v[i];
+      const float send = up ? v[i] : v[i + o];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+    }
   }
+  if (lane < NACC) red[warp * NACC + lane] = v[0];
   __syncthreads();
   float tot = 0.f;
   if (tid < NACC)

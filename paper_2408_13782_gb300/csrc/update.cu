@@ -82,8 +82,15 @@ __device__ void shared_scalar(const UpdArgs& a, int q, float inv_bc1, float inv_
   if (lane == 0) wsum[warp] = s;
   __syncthreads();
   if (tid != 0) return;
-  double tot = 0.0;
-  for (int k = 0; k < (int)(blockDim.x >> 5); ++k) tot += wsum[k];
+  // the warps' sums by a fixed pairwise tree (short FP64 dependency chains)
+  double ws[UPD_NT / 32];
+#pragma unroll
+  for (int k = 0; k < UPD_NT / 32; ++k) ws[k] = wsum[k];
+#pragma unroll
+  for (int w = 1; w < UPD_NT / 32; w <<= 1)
+#pragma unroll
+    for (int k = 0; k + w < UPD_NT / 32; k += 2 * w) ws[k] += ws[k + w];
+  const double tot = ws[0];
   if (q == 0) {
     *a.loss_slot = tot;
     if (!a.assemble) *a.epoch_loss += tot;
@@ -119,8 +126,9 @@ __device__ void led_scalars(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc2)
   };
   // the batch's own parameter state, for the Adam steps after the wait (one per thread)
   float bw = 0.f, bm = 0.f, bv = 0.f;
+  const int bi = tid < 3 * a.B ? batch_param(tid) : -1;  // (the slot table is not read again after the wait)
   if (!a.assemble && tid < 3 * a.B) {
-    const int i = batch_param(tid);
+    const int i = bi;
     bw = __ldcg(a.sp + i);
     bm = __ldcg(a.msp + i);
     bv = __ldcg(a.vsp + i);
@@ -132,29 +140,23 @@ __device__ void led_scalars(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc2)
       scalar_adam(a, i, __ldcg(a.sp + i), __ldcg(a.msp + i), __ldcg(a.vsp + i), 0.0, inv_bc1, inv_sqrt_bc2);
     }
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
-  // slot kk's C partials sit on C consecutive lanes (C divides 32): all loads
-  // in flight at once, then a fixed xor tree over those lanes
-  const int C = a.C, total = a.B * C;
-  for (int base = 0; base < total; base += blockDim.x) {
-    const int e = base + tid;  // (slot e / C, rank e % C)
-    double sg = 0.0, sy = 0.0, sx = 0.0;
-    if (e < total) {
-      const double* p = a.part + (size_t)e * NPART;
-      sg = p[P_GAMMA];
-      sy = p[P_DY];
-      sx = p[P_DX];
-    }
-    for (int o = 1; o < C; o <<= 1) {
-      sg += __shfl_xor_sync(0xffffffffu, sg, o);
-      sy += __shfl_xor_sync(0xffffffffu, sy, o);
-      sx += __shfl_xor_sync(0xffffffffu, sx, o);
-    }
-    if (e < total && (e % C) == 0) {
-      const int kk = e / C;
-      gl[3 * kk] = sg;
-      gl[3 * kk + 1] = sy;
-      gl[3 * kk + 2] = sx;
-    }
+  // one thread per (slot, quantity) sums the slot's C partials with a fixed
+  // pairwise tree over the ranks: all loads in flight, four levels of FP64
+  // adds on two warps (FP64 is slow on this part: no long dependent chains
+  // and no shuffle tree over all the CTA's warps)
+  const int C = a.C;
+  for (int q = tid; q < 3 * a.B; q += blockDim.x) {
+    const int kk = q / 3, r = q - 3 * kk;
+    const double* p = a.part + (size_t)kk * C * NPART + (r == 0 ? P_GAMMA : r == 1 ? P_DY : P_DX);
+    double t[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) t[c] = c < C ? p[(size_t)c * NPART] : 0.0;
+#pragma unroll
+    for (int w = 1; w < 16; w <<= 1)
+#pragma unroll
+      for (int c = 0; c + w < 16; c += 2 * w) t[c] += t[c + w];
+    for (int c = 16; c < C; ++c) t[0] += p[(size_t)c * NPART];
+    gl[q] = t[0];
   }
   __syncthreads();
   if (a.assemble) {  // gradients of every LED: zero outside the batch
@@ -168,7 +170,7 @@ __device__ void led_scalars(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc2)
   }
   if (small) {
     for (int q = tid; q < 3 * a.B; q += blockDim.x) {
-      const int i = batch_param(q);
+      const int i = q == tid ? bi : batch_param(q);
       if (!learned(a, i)) continue;
       if (q == tid) scalar_adam(a, i, bw, bm, bv, gl[q], inv_bc1, inv_sqrt_bc2);
       else scalar_adam(a, i, a.sp[i], a.msp[i], a.vsp[i], gl[q], inv_bc1, inv_sqrt_bc2);
