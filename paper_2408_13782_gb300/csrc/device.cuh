@@ -173,6 +173,52 @@ FPM_HD void theta_poly(const float* c, float (&K)[15], float (&Dx)[10], float (&
     }
 }
 
+// ---- column form of the aberration phase (fixed qx, pixels along y) -----
+// Monomial x^a y^b of the aberration polynomials sits at (a+b)(a+b+1)/2 + b.
+FPM_HD constexpr int mono_idx(int a, int b) { return (a + b) * (a + b + 1) / 2 + b; }
+
+// On one box column x = qx / R is fixed, so theta(x, y) = sum_b th[b] y^b and
+// its x / y derivatives are cubic polynomials in y with coefficients that
+// depend on x only: a pixel then costs three Horner steps in y instead of the
+// 15 monomials and 35 products of box_pixel.
+struct ColPoly {
+  float x;
+  float th[5], gx[4], gy[4];
+};
+
+// poly: K[15], Dx[10], Dy[10] (theta and its gradient as monomials of q / R).
+FPM_HD void col_poly(float x, const float* poly, ColPoly& cp) {
+  cp.x = x;
+#pragma unroll
+  for (int b = 0; b <= 4; ++b) {
+    float s = poly[mono_idx(4 - b, b)];
+#pragma unroll
+    for (int a = 3 - b; a >= 0; --a) s = fmaf(s, x, poly[mono_idx(a, b)]);
+    cp.th[b] = s;
+  }
+#pragma unroll
+  for (int b = 0; b <= 3; ++b) {
+    float sx = poly[15 + mono_idx(3 - b, b)], sy = poly[25 + mono_idx(3 - b, b)];
+#pragma unroll
+    for (int a = 2 - b; a >= 0; --a) {
+      sx = fmaf(sx, x, poly[15 + mono_idx(a, b)]);
+      sy = fmaf(sy, x, poly[25 + mono_idx(a, b)]);
+    }
+    cp.gx[b] = sx;
+    cp.gy[b] = sy;
+  }
+}
+
+FPM_HD float col_theta(const ColPoly& cp, float y) {
+  return fmaf(fmaf(fmaf(fmaf(cp.th[4], y, cp.th[3]), y, cp.th[2]), y, cp.th[1]), y, cp.th[0]);
+}
+
+// d theta / dx and d theta / dy on the column (in units of q / R).
+FPM_HD void col_grad(const ColPoly& cp, float y, float& gx, float& gy) {
+  gx = fmaf(fmaf(fmaf(cp.gx[3], y, cp.gx[2]), y, cp.gx[1]), y, cp.gx[0]);
+  gy = fmaf(fmaf(fmaf(cp.gy[3], y, cp.gy[2]), y, cp.gy[1]), y, cp.gy[0]);
+}
+
 // Per-launch pupil constants.
 struct PupilConst {
   float R, Rinv, inv_lambda, dk2;

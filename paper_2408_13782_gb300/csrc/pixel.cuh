@@ -100,46 +100,7 @@ __device__ __forceinline__ float2 box_pixel(float qy, float qx, float A, float2 
   return cmulc(Mv, gphi);               // conj(M) gPhi
 }
 
-// ---- column form (fixed qx, pixels along y) ------------------------------
-// Monomial x^a y^b of the aberration polynomials sits at (a+b)(a+b+1)/2 + b.
-__host__ __device__ constexpr int mono_idx(int a, int b) { return (a + b) * (a + b + 1) / 2 + b; }
-
-// On one box column x = qx / R is fixed, so theta(x, y) = sum_b th[b] y^b and
-// its x / y derivatives are cubic polynomials in y with coefficients that
-// depend on x only: a pixel then costs three Horner steps in y instead of the
-// 15 monomials and 35 products of box_pixel.
-struct ColPoly {
-  float x;
-  float th[5], gx[4], gy[4];
-};
-
-// poly: K[15], Dx[10], Dy[10] (theta and its gradient as monomials of q / R).
-__device__ __forceinline__ void col_poly(float x, const float* poly, ColPoly& cp) {
-  cp.x = x;
-#pragma unroll
-  for (int b = 0; b <= 4; ++b) {
-    float s = poly[mono_idx(4 - b, b)];
-#pragma unroll
-    for (int a = 3 - b; a >= 0; --a) s = fmaf(s, x, poly[mono_idx(a, b)]);
-    cp.th[b] = s;
-  }
-#pragma unroll
-  for (int b = 0; b <= 3; ++b) {
-    float sx = poly[15 + mono_idx(3 - b, b)], sy = poly[25 + mono_idx(3 - b, b)];
-#pragma unroll
-    for (int a = 2 - b; a >= 0; --a) {
-      sx = fmaf(sx, x, poly[15 + mono_idx(a, b)]);
-      sy = fmaf(sy, x, poly[25 + mono_idx(a, b)]);
-    }
-    cp.gx[b] = sx;
-    cp.gy[b] = sy;
-  }
-}
-
-__device__ __forceinline__ float col_theta(const ColPoly& cp, float y) {
-  return fmaf(fmaf(fmaf(fmaf(cp.th[4], y, cp.th[3]), y, cp.th[2]), y, cp.th[1]), y, cp.th[0]);
-}
-
+// ---- column form (fixed qx, pixels along y; ColPoly in device.cuh) --------
 // Pupil amplitude from r2 = |q|^2; rad = |q| is also returned (anti-aliased
 // edge only: the hard edge needs no square root).
 __device__ __forceinline__ float pupil_amp_r2(float r2, const PupilConst& P, float& rad) {
@@ -169,8 +130,8 @@ __device__ __forceinline__ float2 box_pixel_col(float qy, float qx, float r2, fl
                                                 BoxAcc& acc) {
   const float y = qy * P.Rinv;
   const float th = col_theta(cp, y);
-  const float dthx = fmaf(fmaf(fmaf(cp.gx[3], y, cp.gx[2]), y, cp.gx[1]), y, cp.gx[0]);
-  const float dthy = fmaf(fmaf(fmaf(cp.gy[3], y, cp.gy[2]), y, cp.gy[1]), y, cp.gy[0]);
+  float dthx, dthy;
+  col_grad(cp, y, dthx, dthy);
   float root;
   const float kap = defocus_kappa(r2, P, &root);
   float sn, cs;

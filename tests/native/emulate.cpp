@@ -77,6 +77,17 @@ int main() {
       dmax = std::fmax(dmax, std::fabs(theta_poly_entry(c, e) - ref));
     }
     std::printf("polyentry %.9g\n", dmax);
+    // column form: theta and its gradient as polynomials in y on a column of fixed x
+    float poly[35];
+    for (int e = 0; e < 35; ++e) poly[e] = e < 15 ? K[e] : (e < 25 ? Dx[e - 15] : Dy[e - 25]);
+    for (int i = 0; i < 30; ++i) {
+      const float x = (float)std::cos(1.9 * i + 0.3) * 1.05f, y = (float)std::sin(0.83 * i) * 1.05f;
+      ColPoly cp;
+      col_poly(x, poly, cp);
+      float gx, gy;
+      col_grad(cp, y, gx, gy);
+      std::printf("colform %.9g %.9g %.9g %.9g %.9g\n", x, y, col_theta(cp, y), gx, gy);
+    }
     for (int i = 0; i < 30; ++i) {
       const float x = (float)std::sin(2.3 * i) * 1.05f, y = (float)std::cos(0.37 * i + 1.0) * 1.05f;
       float mo[15];

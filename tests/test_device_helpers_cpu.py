@@ -84,5 +84,18 @@ def test_monomial_basis_matches_oracle(emulated):
         np.testing.assert_allclose(zs, [orc.zernike(j, x, y) for j in range(2, 16)], rtol=3e-6, atol=3e-6)
 
 
+def test_column_form_matches_oracle(emulated):
+    """theta, d theta/dx and d theta/dy from the per-column polynomials in y (the form the
+    per-LED kernel evaluates) against the Zernike sums of the oracle."""
+    c = 0.3 * np.cos(1.7 * np.arange(14) + 0.4)
+    rows = emulated["colform"]
+    assert len(rows) == 30
+    for vals in rows:
+        x, y, th, gx, gy = (float(v) for v in vals)
+        ref_th = sum(cj * orc.zernike(j, x, y) for j, cj in zip(range(2, 16), c))
+        ref_g = [sum(cj * orc.zernike_grad(j, x, y)[a] for j, cj in zip(range(2, 16), c)) for a in (0, 1)]
+        np.testing.assert_allclose([th, gx, gy], [ref_th, *ref_g], rtol=3e-6, atol=3e-6)
+
+
 def test_parallel_polynomial_entries_equal_serial(emulated):
     assert float(emulated["polyentry"][0][0]) <= 1e-6
