@@ -16,7 +16,7 @@ What it computes, with the passage each part follows:
 * each image used once per pass (batch order given as input) .. Eq. (14)
 * initial object: bilinear-interpolated centre-LED image ...... Section 2.3
 
-Readings where the paper is silent or garbled (each is listed in the design doc):
+Readings where the paper is silent or garbled:
 
 * defocus kernel: the paper's sqrt(1 - kx^2 - ky^2) mixes units; it is read
   as kappa(k) = 2 pi (sqrt(lambda^-2 - |k|^2) - lambda^-1), the angular
