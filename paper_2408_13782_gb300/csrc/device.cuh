@@ -179,8 +179,8 @@ FPM_HD constexpr int mono_idx(int a, int b) { return (a + b) * (a + b + 1) / 2 +
 
 // On one box column x = qx / R is fixed, so theta(x, y) = sum_b th[b] y^b and
 // its x / y derivatives are cubic polynomials in y with coefficients that
-// depend on x only: a pixel then costs three Horner steps in y instead of the
-// 15 monomials and 35 products of box_pixel.
+// depend on x only: a pixel then costs three Horner steps in y instead of
+// evaluating 15 monomials and 35 products.
 struct ColPoly {
   float x;
   float th[5], gx[4], gy[4];
@@ -278,23 +278,6 @@ FPM_HD float2 pupil_value(float qy, float qx, const PupilConst& P,
   float th = 0.f;
 #pragma unroll
   for (int j = 0; j < 14; ++j) th = fmaf(zc[j], Z.v[j], th);
-  float root;
-  const float kap = defocus_kappa(qx * qx + qy * qy, P, &root);
-  float sn, cs;
-  sincos_phase(fmaf(z, kap, th), &sn, &cs);
-  return make_float2(A * cs, A * sn);
-}
-
-// The same pupil value with the aberration phase taken from its monomial
-// coefficients K = poly[0..14] (see theta_poly).
-FPM_HD float2 pupil_value_poly(float qy, float qx, const PupilConst& P, const float* __restrict__ poly,
-                               float z) {
-  const float A = pupil_amp(qy, qx, P);
-  if (A == 0.f) return make_float2(0.f, 0.f);
-  float mo[15];
-  monomials(qx * P.Rinv, qy * P.Rinv, mo);
-  float th = 0.f;
-  for (int q = 0; q < 15; ++q) th = fmaf(poly[q], mo[q], th);
   float root;
   const float kap = defocus_kappa(qx * qx + qy * qy, P, &root);
   float sn, cs;

@@ -299,14 +299,19 @@ __global__ void __launch_bounds__(GT, 1) gemm_led_kernel(const GemmArgs g) {
   // ---- Phi = O x M on the box, as the B operand of step 1 (rows c, K = [Re r | Im r])
   for (int it = tid; it < Wp * (Wp / 8); it += GT) {
     const int c = it % Wp, r0 = (it / Wp) * 8;
+    const float qx = (float)(c - h) - dlx, qx2 = qx * qx;
+    ColPoly cp;  // the aberration phase along column c
+    col_poly(qx * P.Rinv, poly, cp);
     float re[8], im[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int r = r0 + e;
       float2 v = make_float2(0.f, 0.f);
       if (c < W && r < W) {
-        const float2 Mv = pupil_value_poly((float)(r - h) - dly, (float)(c - h) - dlx, P, poly, zdef);
-        if (Mv.x != 0.f || Mv.y != 0.f) v = cmul(ob[c * W + r], Mv);
+        const float qy = (float)(r - h) - dly, r2 = fmaf(qy, qy, qx2);
+        float rad;
+        const float A = pupil_amp_r2(r2, P, rad);
+        if (A > 0.f) v = cmul(ob[c * W + r], pupil_col(qy, r2, A, P, cp, zdef));
       }
       re[e] = v.x;
       im[e] = v.y;
@@ -503,19 +508,25 @@ __global__ void __launch_bounds__(GT, 1) gemm_led_kernel(const GemmArgs g) {
       }
       if (c >= W) continue;
       const float2* Oc = ob + c * W;
-      const float qx = (float)(c - h) - dlx;
+      const float qx = (float)(c - h) - dlx, qx2 = qx * qx;
+      ColPoly cp;  // the aberration phase along column c
+      col_poly(qx * P.Rinv, poly, cp);
+      float S[5] = {0.f, 0.f, 0.f, 0.f, 0.f};  // sum t(p) y^b over these pixels of the column
       float2* gb = a.gbox + ((size_t)k * W + c) * W;
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int r = r0 + e;
         if (r >= W) continue;
-        const float qy = (float)(r - h) - dly;
+        const float qy = (float)(r - h) - dly, r2 = fmaf(qy, qy, qx2);
         float2 out = make_float2(0.f, 0.f);
-        const float A = pupil_amp(qy, qx, P);
+        float rad;
+        const float A = pupil_amp_r2(r2, P, rad);
         if (A > 0.f)
-          out = box_pixel(qy, qx, A, make_float2(re[e] * inv_m2, im[e] * inv_m2), Oc[r], P, poly, zdef, bacc);
+          out = box_pixel_col(qy, qx, r2, A, rad, make_float2(re[e] * inv_m2, im[e] * inv_m2), Oc[r], P, cp, zdef,
+                              S, bacc);
         gb[r] = out;
       }
+      col_fold(cp, S, bacc);
     }
   }
 

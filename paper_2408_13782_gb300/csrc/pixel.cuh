@@ -55,51 +55,6 @@ __device__ __forceinline__ void box_acc_zero(BoxAcc& b) {
   b.def = b.dy = b.dx = 0.f;
 }
 
-// One pixel of an LED's support box at q = (qy, qx) = p - delta with the
-// spectrum gradient gphi and the object value o there: returns the object
-// gradient conj(M) gphi and accumulates the pupil-parameter gradient terms.
-// poly: K[15], Dx[10], Dy[10] of the aberration phase. Caller checks A > 0.
-__device__ __forceinline__ float2 box_pixel(float qy, float qx, float A, float2 gphi, float2 o, const PupilConst& P,
-                                            const float* poly, float zdef, BoxAcc& acc) {
-  float mo[15];
-  monomials(qx * P.Rinv, qy * P.Rinv, mo);
-  float th = 0.f, dthx = 0.f, dthy = 0.f;
-#pragma unroll
-  for (int q = 0; q < 15; ++q) th = fmaf(poly[q], mo[q], th);
-#pragma unroll
-  for (int q = 0; q < 10; ++q) {
-    dthx = fmaf(poly[15 + q], mo[q], dthx);
-    dthy = fmaf(poly[25 + q], mo[q], dthy);
-  }
-  const float r2 = qx * qx + qy * qy;
-  float root;
-  const float kap = defocus_kappa(r2, P, &root);
-  float sn, cs;
-  sincos_phase(fmaf(zdef, kap, th), &sn, &cs);
-  const float2 e = make_float2(cs, sn);
-  const float2 Mv = cscale(e, A);
-  const float2 gM = cmulc(o, gphi);     // conj(O) gPhi
-  const float tt = -cmulc(gM, Mv).y;    // dL/dchi = Re(conj(gM) i M)
-  const float ee = cmulc(gM, e).x;      // dL/dA   = Re(conj(gM) e^{i chi})
-#pragma unroll
-  for (int q = 0; q < 15; ++q) acc.m[q] = fmaf(tt, mo[q], acc.m[q]);
-  acc.def = fmaf(tt, kap, acc.def);
-  const float dk = fdiv_fast(-6.283185307179586f * P.dk2, root);  // d kappa / d q = dk * q
-  const float dchiy = fmaf(dthy, P.Rinv, zdef * dk * qy);
-  const float dchix = fmaf(dthx, P.Rinv, zdef * dk * qx);
-  float dAy = 0.f, dAx = 0.f;
-  if (!P.hard_edge) {
-    const float rad = sqrtf(r2);
-    if (rad > P.R - 0.5f && rad < P.R + 0.5f) {
-      dAy = -qy / rad;
-      dAx = -qx / rad;
-    }
-  }
-  acc.dy -= fmaf(tt, dchiy, ee * dAy);
-  acc.dx -= fmaf(tt, dchix, ee * dAx);
-  return cmulc(Mv, gphi);               // conj(M) gPhi
-}
-
 // ---- column form (fixed qx, pixels along y; ColPoly in device.cuh) --------
 // Pupil amplitude from r2 = |q|^2; rad = |q| is also returned (anti-aliased
 // edge only: the hard edge needs no square root).
@@ -123,8 +78,13 @@ __device__ __forceinline__ float2 pupil_col(float qy, float r2, float A, const P
   return make_float2(A * cs, A * sn);
 }
 
-// box_pixel on a column: the monomial moments are kept as the column sums
-// S[b] = sum t(p) y^b and folded into acc.m by col_fold once per column.
+// One pixel of an LED's support box at q = (qy, qx) = p - delta (A > 0, r2 =
+// |q|^2, rad = |q| for the anti-aliased edge) with the spectrum gradient gphi
+// and the object value o there: returns the object gradient conj(M) gphi and
+// accumulates the pupil-parameter gradient terms. The aberration phase comes
+// from the column's polynomials (ColPoly); the monomial moments sum t x^a y^b
+// are kept as the column sums S[b] = sum t y^b and folded into acc.m by
+// col_fold once per column.
 __device__ __forceinline__ float2 box_pixel_col(float qy, float qx, float r2, float A, float rad, float2 gphi, float2 o,
                                                 const PupilConst& P, const ColPoly& cp, float zdef, float (&S)[5],
                                                 BoxAcc& acc) {
