@@ -26,4 +26,8 @@ from .fpm import (  # noqa: F401
     forward,
     loss_and_grad,
     adam_update,
+    adamw_update,
+    nadam_mu,
+    nadam_update,
+    rmsprop_update,
 )

@@ -35,14 +35,15 @@ Readings where the paper is silent or garbled:
   pixel r on high-res pixel s*r and a periodic boundary, zero phase;
   gamma = 1, aberrations = 0, z = 0, delta = fractional part of the nominal
   LED offsets;
-* Adam (Kingma & Ba 2015, bias-corrected) on every real component of every
+* Adam (Kingma & Ba 2015, bias-corrected; or AdamW, NAdam, RMSprop, the other
+  members of the Adam family) on every real component of every
   learnable tensor, every step; sub-pixel offsets clamped to +-offset_bound
   after each update.
 
 Parity pins (tests/test_oracle_*.py): brute-force DFT, Parseval, closed forms
 (constant object, cosine grating, global phase), central finite differences
 on every gradient, zero loss/gradient at the truth, the gamma optimum,
-torch.optim.Adam and its first-step closed form, Noll's table, scipy's
+torch.optim.Adam, AdamW, NAdam and RMSprop and their first-step closed forms, Noll's table, scipy's
 periodic linear interpolation. Reconstruction quality against the paper's Fig. 4 is
 "parity unpinned": the figure's values are not in the text.
 """
@@ -190,6 +191,9 @@ class Hparams:
     loss: str = "amplitude"    # 'amplitude' | 'intensity' | 'linear'
     learn: tuple = ("object",)
     offset_bound: float = 1.0
+    optimizer: str = "adam"    # 'adam' | 'adamw' | 'nadam' | 'rmsprop' (the Adam family of Section 2.2)
+    weight_decay: float = 0.0  # AdamW's decoupled decay
+    momentum_decay: float = 0.004  # NAdam's momentum schedule
 
 
 # --------------------------------------------------------------------------
@@ -364,6 +368,40 @@ def adam_update(w, g, m, v, t: int, lr: float, b1: float, b2: float, eps: float)
     w -= lr * mhat / (np.sqrt(vhat) + eps)
 
 
+def adamw_update(w, g, m, v, t: int, lr: float, b1: float, b2: float, eps: float, wd: float):
+    """AdamW (Loshchilov & Hutter 2019): the weights first decay by lr * wd, decoupled
+    from the gradient, then take the Adam step."""
+    w *= 1 - lr * wd
+    adam_update(w, g, m, v, t, lr, b1, b2, eps)
+
+
+def nadam_mu(t: int, b1: float, psi: float) -> float:
+    """NAdam's momentum coefficient of step t: b1 (1 - 0.96^(t psi) / 2) (Dozat 2016, with
+    the warming schedule of Sutskever et al. 2013)."""
+    return b1 * (1.0 - 0.5 * 0.96 ** (t * psi))
+
+
+def nadam_update(w, g, m, v, t: int, lr: float, b1: float, b2: float, eps: float,
+                 prod_t: float, prod_next: float, psi: float):
+    """One NAdam step (Dozat 2016): Adam's moments, but the step looks one momentum update
+    ahead. prod_t = mu_1 ... mu_t and prod_next = prod_t mu_(t+1)."""
+    mu, mu_next = nadam_mu(t, b1, psi), nadam_mu(t + 1, b1, psi)
+    m *= b1
+    m += (1 - b1) * g
+    v *= b2
+    v += (1 - b2) * g * g
+    denom = np.sqrt(v / (1 - b2 ** t)) + eps
+    w -= lr * (1 - mu) / (1 - prod_t) * g / denom
+    w -= lr * mu_next / (1 - prod_next) * m / denom
+
+
+def rmsprop_update(w, g, v, lr: float, alpha: float, eps: float):
+    """RMSprop (Tieleman & Hinton 2012): a running mean of g^2 scales the step."""
+    v *= alpha
+    v += (1 - alpha) * g * g
+    w -= lr * g / (np.sqrt(v) + eps)
+
+
 # --------------------------------------------------------------------------
 # reconstruction loop (Eq. 13-14)
 # --------------------------------------------------------------------------
@@ -383,33 +421,50 @@ class Reconstruction:
         self.t = 0
         self.epoch_loss = 0.0
         self._state = {}
+        self._mu_prod = 1.0  # NAdam: product of the momentum coefficients so far
 
     def _moments(self, name, shape):
         if name not in self._state:
             self._state[name] = (np.zeros(shape), np.zeros(shape))
         return self._state[name]
 
+    def _update(self, w, g, mm, vv, lr):
+        """One step of the chosen optimiser on a real array, in place."""
+        hp, t = self.hp, self.t
+        if hp.optimizer == "adam":
+            adam_update(w, g, mm, vv, t, lr, hp.beta1, hp.beta2, hp.eps)
+        elif hp.optimizer == "adamw":
+            adamw_update(w, g, mm, vv, t, lr, hp.beta1, hp.beta2, hp.eps, hp.weight_decay)
+        elif hp.optimizer == "nadam":
+            nadam_update(w, g, mm, vv, t, lr, hp.beta1, hp.beta2, hp.eps, self._mu_prod,
+                         self._mu_prod * nadam_mu(t + 1, hp.beta1, hp.momentum_decay), hp.momentum_decay)
+        elif hp.optimizer == "rmsprop":
+            rmsprop_update(w, g, vv, lr, hp.beta2, hp.eps)
+        else:
+            raise ValueError(hp.optimizer)
+
     def step(self, idx) -> float:
         hp = self.hp
         L, g, _ = loss_and_grad(self.O, self.prm, self.geom, idx, self.I, hp.loss)
         self.t += 1
         t = self.t
+        if hp.optimizer == "nadam":  # mu_1 ... mu_t, shared by every parameter
+            self._mu_prod *= nadam_mu(t, hp.beta1, hp.momentum_decay)
         if "object" in hp.learn:
             w = np.stack([self.O.real, self.O.imag], axis=-1)
             gw = np.stack([g["object"].real, g["object"].imag], axis=-1)
             mm, vv = self._moments("object", w.shape)
-            adam_update(w, gw, mm, vv, t, hp.lr["object"], hp.beta1, hp.beta2, hp.eps)
+            self._update(w, gw, mm, vv, hp.lr["object"])
             self.O = w[..., 0] + 1j * w[..., 1]
         for name, attr in (("zernike", "zernike"), ("gamma", "gamma"), ("offset", "offset")):
             if name in hp.learn:
                 w = getattr(self.prm, attr)
                 mm, vv = self._moments(name, w.shape)
-                adam_update(w, g[name], mm, vv, t, hp.lr[name], hp.beta1, hp.beta2, hp.eps)
+                self._update(w, g[name], mm, vv, hp.lr[name])
         if "defocus" in hp.learn:
             w = np.array([self.prm.defocus])
             mm, vv = self._moments("defocus", (1,))
-            adam_update(w, np.array([g["defocus"]]), mm, vv, t, hp.lr["defocus"],
-                        hp.beta1, hp.beta2, hp.eps)
+            self._update(w, np.array([g["defocus"]]), mm, vv, hp.lr["defocus"])
             self.prm.defocus = float(w[0])
         if "offset" in hp.learn:
             np.clip(self.prm.offset, -hp.offset_bound, hp.offset_bound, out=self.prm.offset)

@@ -37,6 +37,68 @@ def test_adam_matches_torch_on_complex_and_real():
     np.testing.assert_allclose(w[..., 0] + 1j * w[..., 1], tw.detach().numpy(), rtol=1e-13, atol=1e-15)
 
 
+def _torch_steps(opt, w0, grads):
+    # FP64 default dtype: NAdam keeps its running momentum product as a scalar of that type
+    old = torch.get_default_dtype()
+    torch.set_default_dtype(torch.float64)
+    try:
+        tw = torch.tensor(w0, dtype=torch.float64, requires_grad=True)
+        o = opt([tw])
+        for g in grads:
+            o.zero_grad()
+            tw.grad = torch.tensor(g, dtype=torch.float64)
+            o.step()
+    finally:
+        torch.set_default_dtype(old)
+    return tw.detach().numpy()
+
+
+@pytest.mark.parametrize("name", ["adamw", "nadam", "rmsprop"])
+def test_adam_family_matches_torch(name):
+    """AdamW, NAdam and RMSprop of the oracle against torch.optim's implementations, on
+    the (Re, Im) components, seven steps including one with zero gradient on some rows."""
+    rng = np.random.default_rng(2)
+    w0 = rng.normal(size=(6, 5, 2))
+    grads = [rng.normal(size=(6, 5, 2)) * 10.0 ** rng.uniform(-3, 2) for _ in range(7)]
+    grads[3][:2] = 0.0
+    lr, b1, b2, eps, wd, psi = 0.05, 0.9, 0.999, 1e-8, 0.01, 0.004
+    w, m, v, prod = w0.copy(), np.zeros_like(w0), np.zeros_like(w0), 1.0
+    for t, g in enumerate(grads, start=1):
+        if name == "adamw":
+            orc.adamw_update(w, g, m, v, t, lr, b1, b2, eps, wd)
+        elif name == "nadam":
+            prod *= orc.nadam_mu(t, b1, psi)
+            orc.nadam_update(w, g, m, v, t, lr, b1, b2, eps, prod, prod * orc.nadam_mu(t + 1, b1, psi), psi)
+        else:
+            orc.rmsprop_update(w, g, v, lr, b2, eps)
+    opt = {"adamw": lambda p: torch.optim.AdamW(p, lr=lr, betas=(b1, b2), eps=eps, weight_decay=wd),
+           "nadam": lambda p: torch.optim.NAdam(p, lr=lr, betas=(b1, b2), eps=eps, momentum_decay=psi),
+           "rmsprop": lambda p: torch.optim.RMSprop(p, lr=lr, alpha=b2, eps=eps)}[name]
+    np.testing.assert_allclose(w, _torch_steps(opt, w0, grads), rtol=1e-12, atol=1e-14)
+
+
+def test_rmsprop_first_step_closed_form():
+    # From a zero running mean the first step is lr * g / (sqrt(1 - alpha) |g| + eps).
+    rng = np.random.default_rng(3)
+    g = rng.normal(size=50) * 10.0 ** rng.uniform(-6, 3, 50)
+    w = np.zeros(50)
+    orc.rmsprop_update(w, g, np.zeros(50), 0.1, 0.99, 1e-8)
+    np.testing.assert_allclose(w, -0.1 * g / (np.sqrt(0.01) * np.abs(g) + 1e-8), rtol=1e-12)
+
+
+def test_nadam_schedule_and_first_step():
+    # mu_t = b1 (1 - 0.96^(t psi) / 2); from zero moments the first step is
+    # lr ((1 - mu_1) / (1 - mu_1) + mu_2 (1 - b1) / (1 - mu_1 mu_2)) g / (|g| + eps)
+    b1, psi = 0.9, 0.004
+    assert orc.nadam_mu(1, b1, psi) == pytest.approx(b1 * (1 - 0.5 * 0.96 ** psi), rel=1e-15)
+    mu1, mu2 = orc.nadam_mu(1, b1, psi), orc.nadam_mu(2, b1, psi)
+    g = np.array([2.0, -0.5, 1e-3])
+    w = np.zeros(3)
+    orc.nadam_update(w, g, np.zeros(3), np.zeros(3), 1, 0.1, b1, 0.999, 0.0, mu1, mu1 * mu2, psi)
+    coef = 1.0 + mu2 * (1 - b1) / (1 - mu1 * mu2)
+    np.testing.assert_allclose(w, -0.1 * coef * np.sign(g), rtol=1e-12)
+
+
 def test_adam_zero_state_zero_gradient_is_noop():
     w = np.ones(4)
     orc.adam_update(w, np.zeros(4), np.zeros(4), np.zeros(4), 3, 0.1, 0.9, 0.999, 1e-8)
