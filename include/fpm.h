@@ -110,6 +110,23 @@ typedef struct fpm_geometry {
   int32_t pupil_edge;       /* FPM_EDGE_AA or FPM_EDGE_HARD */
 } fpm_geometry;
 
+/* Optimisers of the Adam family (Section 2.2 leaves the choice open). Each takes one
+ * step per batch on every real component of every learnable tensor, with the
+ * group's learning rate lr and the gradient g of the batch loss:
+ *   ADAM     m <- b1 m + (1 - b1) g, v <- b2 v + (1 - b2) g^2,
+ *            w <- w - lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps)   (Kingma & Ba)
+ *   ADAMW    w <- w (1 - lr weight_decay), then the ADAM step (decoupled decay,
+ *            Loshchilov & Hutter)
+ *   NADAM    the ADAM moments; with mu_t = b1 (1 - 0.96^(0.004 t) / 2) and
+ *            P_t = mu_1 ... mu_t: w <- w - lr (mu_(t+1) m / (1 - P_(t+1))
+ *            + (1 - mu_t) g / (1 - P_t)) / (sqrt(v / (1 - b2^t)) + eps)   (Dozat)
+ *   RMSPROP  v <- b2 v + (1 - b2) g^2, w <- w - lr g / (sqrt(v) + eps)
+ *            (Tieleman & Hinton; beta2 is the smoothing constant, beta1 unused) */
+#define FPM_OPT_ADAM 0
+#define FPM_OPT_ADAMW 1
+#define FPM_OPT_NADAM 2
+#define FPM_OPT_RMSPROP 3
+
 /* Optimiser and loss settings (Section 2.2: Adam-family optimiser, free loss choice). */
 typedef struct fpm_hparams {
   float lr_object, lr_zernike, lr_defocus, lr_gamma, lr_offset;
@@ -117,6 +134,8 @@ typedef struct fpm_hparams {
   int32_t loss;             /* FPM_LOSS_AMPLITUDE or FPM_LOSS_INTENSITY */
   uint32_t learn_mask;      /* FPM_LEARN_* bits; cleared groups are held fixed */
   int32_t precision;        /* FPM_PRECISION_*: FP32 FFTs (default) or a tensor-core DFT form */
+  int32_t optimizer;        /* FPM_OPT_*; default FPM_OPT_ADAM */
+  float weight_decay;       /* FPM_OPT_ADAMW's decay rate (>= 0), applied to every learnable group */
 } fpm_hparams;
 
 /* Create an engine for N = m * upsample, pupil radius R (spectral px).
@@ -124,7 +143,7 @@ typedef struct fpm_hparams {
  * to lie inside the N x N spectrum and inside the m x m window.
  * cuda_stream: a cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream); NULL = default.
  * Default hyper-parameters: lr 0.1 / 0.01 / 0.1 / 0.01 / 0.01, betas 0.9 / 0.999,
- * eps 1e-8, amplitude loss, learn object only. On success *out owns device memory
+ * eps 1e-8, amplitude loss, learn object only, Adam, no weight decay. On success *out owns device memory
  * until fpm_destroy. */
 int fpm_create(const fpm_geometry* g, float pupil_radius_px, int32_t upsample,
                void* cuda_stream, fpm_handle** out);

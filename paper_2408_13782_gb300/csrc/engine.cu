@@ -56,12 +56,16 @@ struct fpm_handle {
   int cap_losses = 0;
   size_t cap_fbuf = 0;
   double* epoch = nullptr;
-  float2* coef = nullptr;  // per-step Adam bias corrections of the current run
+  float4* coef = nullptr;  // per-step optimiser coefficients of the current run
   int cap_coef = 0;
   int* err = nullptr;
   // pinned staging of handle-free copies
   int* h_err = nullptr;
   long long t_host = 0;
+  // NAdam's product of momentum coefficients P_t for t = nadam_t (with beta1 = nadam_b1)
+  long long nadam_t = 0;
+  double nadam_prod = 1.0;
+  float nadam_b1 = -1.f;
   bool loaded = false;
   // One captured graph per (n_steps, B), each with its own pinned staging for
   // the batch slots and Adam coefficients its first nodes copy, and an event
@@ -70,7 +74,7 @@ struct fpm_handle {
   struct Graph {
     cudaGraphExec_t exec = nullptr;
     int4* h_slots = nullptr;
-    float2* h_coef = nullptr;
+    float4* h_coef = nullptr;
     cudaEvent_t done = nullptr;
   };
   std::map<std::pair<int, int>, Graph> graphs;
@@ -207,13 +211,36 @@ int grow(fpm_handle* h, T** p, int* cap, int need) {
   return FPM_OK;
 }
 
-// Adam bias corrections (1/(1 - b1^t), 1/sqrt(1 - b2^t)) for steps
-// t = t_host + 1 .. t_host + n_steps, in FP64, into dst (host).
-void fill_coef(const fpm_handle* h, int n_steps, float2* dst) {
+// The optimiser's per-step coefficients for steps t = t_host + 1 .. t_host +
+// n_steps, in FP64, into dst (host); the layout per optimiser is UpdArgs::coef's.
+// NAdam's momentum coefficient mu_t = b1 (1 - 0.96^(0.004 t) / 2) and the running
+// product P_t = mu_1 ... mu_t (kept on the handle, rebuilt when the step count
+// moves back or beta1 changes).
+void fill_coef(fpm_handle* h, int n_steps, float4* dst) {
   const double b1 = h->hp.beta1, b2 = h->hp.beta2;
+  const int opt = h->hp.optimizer;
+  auto mu = [b1](double t) { return b1 * (1.0 - 0.5 * std::pow(0.96, 0.004 * t)); };
+  if (opt == FPM_OPT_NADAM) {
+    if (h->nadam_t > h->t_host || h->nadam_b1 != h->hp.beta1) {
+      h->nadam_t = 0;
+      h->nadam_prod = 1.0;
+      h->nadam_b1 = h->hp.beta1;
+    }
+    while (h->nadam_t < h->t_host) h->nadam_prod *= mu((double)++h->nadam_t);
+  }
+  double prod = h->nadam_prod;  // P at t_host (NAdam)
   for (int s = 0; s < n_steps; ++s) {
     const double t = (double)(h->t_host + s + 1);
-    dst[s] = make_float2((float)(1.0 / (1.0 - std::pow(b1, t))), (float)(1.0 / std::sqrt(1.0 - std::pow(b2, t))));
+    const float inv_sqrt_bc2 = (float)(1.0 / std::sqrt(1.0 - std::pow(b2, t)));
+    if (opt == FPM_OPT_NADAM) {
+      const double mt = mu(t), pt = prod * mt, pn = pt * mu(t + 1);
+      dst[s] = make_float4((float)(mu(t + 1) / (1.0 - pn)), inv_sqrt_bc2, (float)((1.0 - mt) / (1.0 - pt)), 0.f);
+      prod = pt;
+    } else if (opt == FPM_OPT_RMSPROP) {
+      dst[s] = make_float4(0.f, 1.f, 0.f, 0.f);
+    } else {
+      dst[s] = make_float4((float)(1.0 / (1.0 - std::pow(b1, t))), inv_sqrt_bc2, 0.f, 0.f);
+    }
   }
 }
 
@@ -318,6 +345,8 @@ UpdArgs upd_args(fpm_handle* h, const int4* slot_dev, int B, int step_off, doubl
   u.b1 = h->hp.beta1;
   u.b2 = h->hp.beta2;
   u.eps = h->hp.eps;
+  u.opt = h->hp.optimizer;
+  u.wd = h->hp.weight_decay;
   u.offset_bound = FPM_OFFSET_BOUND_PX;
   u.coef = assemble ? nullptr : h->coef;
   u.step_off = step_off;
@@ -360,14 +389,14 @@ int copy_out(fpm_handle* h, void* dst, const void* src, size_t bytes, bool* host
 
 int build_graph(fpm_handle* h, int n_steps, int B, fpm_handle::Graph* gr) {
   CK(h, cudaMallocHost(&gr->h_slots, sizeof(int4) * (size_t)n_steps * B));
-  CK(h, cudaMallocHost(&gr->h_coef, sizeof(float2) * (size_t)n_steps));
+  CK(h, cudaMallocHost(&gr->h_coef, sizeof(float4) * (size_t)n_steps));
   CK(h, cudaEventCreateWithFlags(&gr->done, cudaEventDisableTiming));
   cudaGraph_t g = nullptr;
   CK(h, cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaMemcpyAsync(h->sched, gr->h_slots, sizeof(int4) * (size_t)n_steps * B,
                                   cudaMemcpyHostToDevice, h->st);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(h->coef, gr->h_coef, sizeof(float2) * n_steps, cudaMemcpyHostToDevice, h->st);
+    e = cudaMemcpyAsync(h->coef, gr->h_coef, sizeof(float4) * n_steps, cudaMemcpyHostToDevice, h->st);
   // kernels after the first may start early (programmatic dependent launch)
   // and wait in-kernel for their predecessor's results
   for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
@@ -420,7 +449,7 @@ void fpmk::engine_round_slots(const fpm_handle* h, const int32_t* idx, int count
   fill_slots(h, idx, count, dst);
 }
 
-void fpmk::engine_round_coef(fpm_handle* h, int n_steps, float2* dst) {
+void fpmk::engine_round_coef(fpm_handle* h, int n_steps, float4* dst) {
   fill_coef(h, n_steps, dst);
   h->t_host += n_steps;
 }
@@ -517,6 +546,8 @@ int fpm_create(const fpm_geometry* g, float R, int32_t upsample, void* cuda_stre
   h->hp.loss = FPM_LOSS_AMPLITUDE;
   h->hp.learn_mask = FPM_LEARN_OBJECT;
   h->hp.precision = FPM_PRECISION_FP32_FFT;
+  h->hp.optimizer = FPM_OPT_ADAM;
+  h->hp.weight_decay = 0.f;
 
   auto ck = [&](cudaError_t e, const char* what) {
     if (e == cudaSuccess) return true;
@@ -587,6 +618,9 @@ int fpm_set_hparams(fpm_handle* h, const fpm_hparams* hp) {
     return fail(h, FPM_ERR_ARG, "unknown precision mode");
   if (!(hp->beta1 >= 0.f && hp->beta1 < 1.f && hp->beta2 >= 0.f && hp->beta2 < 1.f && hp->eps > 0.f))
     return fail(h, FPM_ERR_ARG, "betas must lie in [0, 1) and eps be positive");
+  if (hp->optimizer < FPM_OPT_ADAM || hp->optimizer > FPM_OPT_RMSPROP) return fail(h, FPM_ERR_ARG, "unknown optimiser");
+  if (!(std::isfinite(hp->weight_decay) && hp->weight_decay >= 0.f))
+    return fail(h, FPM_ERR_ARG, "weight decay must be finite and non-negative");
   const bool lr_ok = std::isfinite(hp->lr_object) && std::isfinite(hp->lr_zernike) &&
                      std::isfinite(hp->lr_defocus) && std::isfinite(hp->lr_gamma) && std::isfinite(hp->lr_offset);
   if (!lr_ok) return fail(h, FPM_ERR_ARG, "non-finite learning rate");
@@ -711,9 +745,9 @@ int fpm_profile_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int
   std::vector<int4> slots((size_t)n_steps * B);
   fill_slots(h, schedule, n_steps * B, slots.data());
   CK(h, cudaMemcpyAsync(h->sched, slots.data(), sizeof(int4) * slots.size(), cudaMemcpyHostToDevice, h->st));
-  std::vector<float2> coef(n_steps);
+  std::vector<float4> coef(n_steps);
   fill_coef(h, n_steps, coef.data());
-  CK(h, cudaMemcpyAsync(h->coef, coef.data(), sizeof(float2) * n_steps, cudaMemcpyHostToDevice, h->st));
+  CK(h, cudaMemcpyAsync(h->coef, coef.data(), sizeof(float4) * n_steps, cudaMemcpyHostToDevice, h->st));
   std::vector<cudaEvent_t> ev((size_t)3 * n_steps, nullptr);
   auto destroy = [&]() {
     for (auto e : ev)

@@ -61,7 +61,13 @@ struct UpdArgs {
   int N, n_leds, B, C, h, W;
   float lr_obj, lr_zern, lr_def, lr_gam, lr_off, b1, b2, eps;
   float offset_bound;
-  const float2* coef;       // per step of the sequence: (1/(1-b1^t), 1/sqrt(1-b2^t)); nullable
+  // per step of the sequence, by optimiser (nullable: (1, 1, 0, 0)):
+  //   Adam, AdamW: (1/(1-b1^t), 1/sqrt(1-b2^t), 0, 0)
+  //   NAdam: (mu_(t+1)/(1-P_(t+1)), 1/sqrt(1-b2^t), (1-mu_t)/(1-P_t), 0)
+  //   RMSprop: (0, 1, 0, 0)
+  const float4* coef;
+  int opt;                  // FPM_OPT_*
+  float wd;                 // AdamW weight decay
   int step_off;             // this step's position in the sequence
   unsigned learn;
   double* loss_slot;        // batch loss of this step
@@ -98,7 +104,7 @@ int update_ctas(const UpdArgs& a);  // CTAs of one job's update launch
 struct EngineRound {
   int m, C, W, n_leds, fft;     // kernel configuration; fft: FP32 FFT form (groupable)
   int4* slots;                  // device: batch slots of the round's steps
-  float2* coef;                 // device: Adam bias corrections per step
+  float4* coef;                 // device: optimiser coefficients per step (see UpdArgs)
   double* losses;               // device: batch loss per step
   double* epoch;                // device: running FP64 loss sum
 };
@@ -107,7 +113,7 @@ int engine_round_reserve(fpm_handle* h, int n_steps, int B, EngineRound* out);
 // Host side of one round: slot tables for idx[0..count), and the Adam bias
 // corrections of the next n_steps steps (advancing the handle's step count).
 void engine_round_slots(const fpm_handle* h, const int32_t* idx, int count, int4* dst);
-void engine_round_coef(fpm_handle* h, int n_steps, float2* dst);
+void engine_round_coef(fpm_handle* h, int n_steps, float4* dst);
 // Launch arguments of one step of the handle (built-in loss, updating).
 LedArgs engine_led_args(fpm_handle* h, const int4* slot_dev, int B);
 UpdArgs engine_upd_args(fpm_handle* h, const int4* slot_dev, int B, int step_off, double* loss_slot);

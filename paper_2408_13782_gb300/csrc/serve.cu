@@ -72,7 +72,7 @@ struct Round {
   cudaGraphExec_t exec = nullptr;
   int steps = 0, B = 0, nfull = 0, rem = 0;
   std::vector<int4*> h_slots;    // pinned, per job: the epoch's slot table
-  std::vector<float2*> h_coef;   // pinned, per job: Adam bias corrections per step
+  std::vector<float4*> h_coef;   // pinned, per job: optimiser coefficients per step
   unsigned char* d_tables = nullptr;  // LedArgs / UpdArgs tables and maps of all steps
   bool in_flight = false;
 };
@@ -257,7 +257,7 @@ int build_round(Round* r, const std::vector<Job*>& js) {
   r->h_coef.assign(J, nullptr);
   for (int q = 0; q < J; ++q)
     if (cudaMallocHost(&r->h_slots[q], sizeof(int4) * n) != cudaSuccess ||
-        cudaMallocHost(&r->h_coef[q], sizeof(float2) * S) != cudaSuccess)
+        cudaMallocHost(&r->h_coef[q], sizeof(float4) * S) != cudaSuccess)
       return FPM_ERR_OOM;
   // per step: J LedArgs, J UpdArgs, the cluster map and the update-CTA map
   std::vector<LedArgs> led((size_t)S * J);
@@ -305,7 +305,7 @@ int build_round(Round* r, const std::vector<Job*>& js) {
   for (int q = 0; q < J && e == cudaSuccess; ++q) {
     e = cudaMemcpyAsync(js[q]->er.slots, r->h_slots[q], sizeof(int4) * n, cudaMemcpyHostToDevice, r->stream);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(js[q]->er.coef, r->h_coef[q], sizeof(float2) * S, cudaMemcpyHostToDevice, r->stream);
+      e = cudaMemcpyAsync(js[q]->er.coef, r->h_coef[q], sizeof(float4) * S, cudaMemcpyHostToDevice, r->stream);
   }
   for (int st = 0; st < S && e == cudaSuccess; ++st) {
     const int Bs = st < r->nfull ? B : r->rem;
@@ -393,7 +393,7 @@ int64_t fpm_job_footprint(const fpm_job_desc* d) {
                   + n * 8 + N * 8        // LED table, update spans
                   + B * W * W * 8        // per-LED gradient boxes
                   + B * C * NPART * 8    // FP64 partials
-                  + steps * B * 16 + steps * (8 + 8);  // batch slots, losses, coefficients
+                  + steps * B * 16 + steps * (8 + 16);  // batch slots, losses, coefficients
   return bytes + (1 << 20);              // allocator granularity and small buffers
 }
 

@@ -1,7 +1,8 @@
-// Random-batch update (Section 2.3, Eq. 13) with Adam (Kingma & Ba 2015).
-// The bias corrections 1/(1 - b1^t) and 1/sqrt(1 - b2^t) of each step are
-// computed on the host in FP64 and passed in per step (no FP64 math here
-// apart from the fixed-order reduction of the FP64 partials).
+// Random-batch update (Section 2.3, Eq. 13) with an optimiser of the Adam
+// family (Adam, AdamW, NAdam, RMSprop; the rules are in fpm.h). The per-step
+// coefficients (bias corrections, NAdam's momentum schedule) are computed on
+// the host in FP64 and passed in per step (no FP64 math here apart from the
+// fixed-order reduction of the FP64 partials).
 //
 // Object: every element of the update region (the union of all LEDs' crop
 // boxes; outside it the gradient has always been zero and Adam is an exact
@@ -13,6 +14,7 @@
 // all of them (every element, every step).
 #include <cmath>
 
+#include "../../include/fpm.h"
 #include "device.cuh"
 #include "internal.h"
 
@@ -28,6 +30,29 @@ __device__ __forceinline__ void adam1(float& w, float& m, float& v, float g, flo
   m = fmaf(b1, m, (1.f - b1) * g);
   v = fmaf(b2, v, (1.f - b2) * g * g);
   w -= lr_bc1 * m / fmaf(sqrtf(v), inv_sqrt_bc2, eps);
+}
+
+// One step of the handle's optimiser on one real component with learning rate
+// lr and this step's coefficients k (see UpdArgs::coef). The branch is the
+// same for every thread of a launch.
+__device__ __forceinline__ void opt1(const UpdArgs& a, float& w, float& m, float& v, float g, float lr, float4 k) {
+  switch (a.opt) {
+    case FPM_OPT_ADAMW:
+      w *= 1.f - lr * a.wd;
+      adam1(w, m, v, g, lr * k.x, k.y, a.b1, a.b2, a.eps);
+      break;
+    case FPM_OPT_NADAM:
+      m = fmaf(a.b1, m, (1.f - a.b1) * g);
+      v = fmaf(a.b2, v, (1.f - a.b2) * g * g);
+      w -= lr * fmaf(k.x, m, k.z * g) / fmaf(sqrtf(v), k.y, a.eps);
+      break;
+    case FPM_OPT_RMSPROP:
+      v = fmaf(a.b2, v, (1.f - a.b2) * g * g);
+      w -= lr * g / (sqrtf(v) + a.eps);
+      break;
+    default:
+      adam1(w, m, v, g, lr * k.x, k.y, a.b1, a.b2, a.eps);
+  }
 }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -52,10 +77,10 @@ __device__ __forceinline__ float lr_of(const UpdArgs& a, int i) {
   return i < SP_DEFOCUS ? a.lr_zern : i == SP_DEFOCUS ? a.lr_def : i < sp_offset(a.n_leds) ? a.lr_gam : a.lr_off;
 }
 
-// Adam on scalar i with FP64 gradient g; offsets are clamped to the box bound.
-__device__ __forceinline__ void scalar_adam(const UpdArgs& a, int i, float w, float m, float v, double g,
-                                            float inv_bc1, float inv_sqrt_bc2) {
-  adam1(w, m, v, (float)g, lr_of(a, i) * inv_bc1, inv_sqrt_bc2, a.b1, a.b2, a.eps);
+// The optimiser step of scalar i with FP64 gradient g; offsets are clamped to
+// the box bound.
+__device__ __forceinline__ void scalar_adam(const UpdArgs& a, int i, float w, float m, float v, double g, float4 k) {
+  opt1(a, w, m, v, (float)g, lr_of(a, i), k);
   if (i >= sp_offset(a.n_leds)) w = fminf(fmaxf(w, -a.offset_bound), a.offset_bound);
   a.sp[i] = w;
   a.msp[i] = m;
@@ -63,7 +88,7 @@ __device__ __forceinline__ void scalar_adam(const UpdArgs& a, int i, float w, fl
 }
 
 // CTA q < 16: one shared quantity.
-__device__ void shared_scalar(const UpdArgs& a, int q, float inv_bc1, float inv_sqrt_bc2) {
+__device__ void shared_scalar(const UpdArgs& a, int q, float4 k) {
   __shared__ double wsum[UPD_NT / 32];
   const int P = q == 0 ? P_LOSS : q <= 14 ? P_ZERN + q - 1 : P_DEFOCUS;
   const int i = q == 0 ? -1 : q <= 14 ? SP_ZERN + q - 1 : SP_DEFOCUS;  // parameter index
@@ -101,14 +126,14 @@ __device__ void shared_scalar(const UpdArgs& a, int q, float inv_bc1, float inv_
     a.g_sc[i] = (float)tot;
     return;
   }
-  if (learned(a, i)) scalar_adam(a, i, w, m, v, tot, inv_bc1, inv_sqrt_bc2);
+  if (learned(a, i)) scalar_adam(a, i, w, m, v, tot, k);
 }
 
 // CTA 16: the per-LED intensity factors and offsets of every LED. The LEDs
 // outside the batch have zero gradient and are not read by this step's LED
 // kernel, so their Adam steps run before the wait; after it only the batch's
 // 3 B parameters remain.
-__device__ void led_scalars(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc2) {
+__device__ void led_scalars(const UpdArgs& a, float4 k) {
   extern __shared__ double gl[];  // [3 B]: per batch slot gamma, dy, dx
   __shared__ unsigned char in_batch[1024];
   const int n = a.n_leds, tid = threadIdx.x;
@@ -137,7 +162,7 @@ __device__ void led_scalars(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc2)
     for (int j = tid; j < 3 * n; j += blockDim.x) {
       const int i = SP_GAMMA + j;
       if (!small || in_batch[idx_led(j)] || !learned(a, i)) continue;
-      scalar_adam(a, i, __ldcg(a.sp + i), __ldcg(a.msp + i), __ldcg(a.vsp + i), 0.0, inv_bc1, inv_sqrt_bc2);
+      scalar_adam(a, i, __ldcg(a.sp + i), __ldcg(a.msp + i), __ldcg(a.vsp + i), 0.0, k);
     }
   asm volatile("griddepcontrol.wait;\n" ::: "memory");
   // one thread per (slot, quantity) sums the slot's C partials with a fixed
@@ -172,8 +197,8 @@ __device__ void led_scalars(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc2)
     for (int q = tid; q < 3 * a.B; q += blockDim.x) {
       const int i = q == tid ? bi : batch_param(q);
       if (!learned(a, i)) continue;
-      if (q == tid) scalar_adam(a, i, bw, bm, bv, gl[q], inv_bc1, inv_sqrt_bc2);
-      else scalar_adam(a, i, a.sp[i], a.msp[i], a.vsp[i], gl[q], inv_bc1, inv_sqrt_bc2);
+      if (q == tid) scalar_adam(a, i, bw, bm, bv, gl[q], k);
+      else scalar_adam(a, i, a.sp[i], a.msp[i], a.vsp[i], gl[q], k);
     }
     return;
   }
@@ -184,7 +209,30 @@ __device__ void led_scalars(const UpdArgs& a, float inv_bc1, float inv_sqrt_bc2)
     double g = 0.0;
     for (int kk = 0; kk < a.B; ++kk)
       if (a.slot[kk].x == led) g = gl[3 * kk + (j < n ? 0 : 1 + ((j - n) & 1))];
-    scalar_adam(a, i, a.sp[i], a.msp[i], a.vsp[i], g, inv_bc1, inv_sqrt_bc2);
+    scalar_adam(a, i, a.sp[i], a.msp[i], a.vsp[i], g, k);
+  }
+}
+
+// AdamW's decoupled decay reaches every element of the object spectrum, also
+// those outside the update region, whose gradient is always zero (there every
+// other rule of the family is an exact no-op). NDECAY extra CTAs take the
+// columns q, q + NDECAY, ... and scale the rows outside the region. No
+// per-LED kernel reads those elements (every crop box lies inside the
+// region), so this runs before the grid-dependency wait.
+constexpr int NDECAY = 64;
+
+__device__ void decay_outside(const UpdArgs& a, int q) {
+  const float f = 1.f - a.lr_obj * a.wd;
+  for (int x = q; x < a.N; x += NDECAY) {
+    const int2 sp = a.span[x];  // rows [sp.x, sp.y) of the region (empty: (N, 0))
+    float2* col = a.Ot + (size_t)x * a.N;
+    for (int y = threadIdx.x; y < a.N; y += blockDim.x)
+      if (y < sp.x || y >= sp.y) {
+        float2 w = col[y];
+        w.x *= f;
+        w.y *= f;
+        col[y] = w;
+      }
   }
 }
 
@@ -202,10 +250,14 @@ __device__ __forceinline__ void update_body(const UpdArgs& a, const int bid) {
   // kernel depends on: step coefficients, LED tables, and O, m, v (the LED
   // kernel only reads O, and lets this kernel start only after the previous
   // update has completed). The gradient boxes and partials come after it.
-  const float2 bc = a.coef ? a.coef[a.step_off] : make_float2(1.f, 1.f);
+  const float4 bc = a.coef ? a.coef[a.step_off] : make_float4(1.f, 1.f, 0.f, 0.f);
   if (bid < NSC) {  // the scalar parameters (the longest dependency chain)
-    if (bid < 16) shared_scalar(a, bid, bc.x, bc.y);
-    else led_scalars(a, bc.x, bc.y);
+    if (bid < 16) shared_scalar(a, bid, bc);
+    else led_scalars(a, bc);
+    return;
+  }
+  if (bid >= NSC + a.n_cols) {  // AdamW only (see update_ctas)
+    decay_outside(a, bid - NSC - a.n_cols);
     return;
   }
   if (!a.assemble && !(a.learn & 1u)) return;
@@ -241,8 +293,6 @@ __device__ __forceinline__ void update_body(const UpdArgs& a, const int bid) {
   }
   asm volatile("griddepcontrol.wait;\n" ::: "memory");  // gradient boxes of the LED kernel
   __syncthreads();
-  const float lr_bc1 = a.lr_obj * bc.x;
-  const float inv_sqrt_bc2 = bc.y;
   const int n_l = nl;
   for (int y = y0; y < span.y; y += blockDim.x) {
     const size_t o = (size_t)x * a.N + y;
@@ -290,8 +340,8 @@ __device__ __forceinline__ void update_body(const UpdArgs& a, const int bid) {
       a.g_obj[o] = g;
       continue;
     }
-    adam1(w.x, m.x, v.x, g.x, lr_bc1, inv_sqrt_bc2, a.b1, a.b2, a.eps);
-    adam1(w.y, m.y, v.y, g.y, lr_bc1, inv_sqrt_bc2, a.b1, a.b2, a.eps);
+    opt1(a, w.x, m.x, v.x, g.x, a.lr_obj, bc);
+    opt1(a, w.y, m.y, v.y, g.y, a.lr_obj, bc);
     a.Ot[o] = w;
     a.mO[o] = m;
     a.vO[o] = v;
@@ -311,7 +361,10 @@ __global__ void __launch_bounds__(UPD_NT) update_kernel_jobs(const UpdArgs* __re
   update_body(sa, q.y);
 }
 
-int update_ctas(const UpdArgs& a) { return a.n_cols + NSC; }
+int update_ctas(const UpdArgs& a) {
+  const bool decay = a.opt == FPM_OPT_ADAMW && a.wd > 0.f && !a.assemble && (a.learn & 1u);
+  return a.n_cols + NSC + (decay ? NDECAY : 0);
+}
 
 cudaError_t update_prepare() {
   cudaError_t e = cudaFuncSetAttribute(update_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -340,7 +393,7 @@ cudaError_t launch_update_jobs(const UpdArgs* jobs, const int2* map, int n_ctas,
 cudaError_t launch_update(const UpdArgs& a, cudaStream_t s, bool pdl) {
   const size_t smem = sizeof(double) * 3 * (size_t)a.B;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(a.n_cols + NSC), 1, 1);
+  cfg.gridDim = dim3((unsigned)update_ctas(a), 1, 1);
   cfg.blockDim = dim3(UPD_NT, 1, 1);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;

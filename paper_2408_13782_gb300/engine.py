@@ -26,6 +26,7 @@ LEARN = {"object": 1, "zernike": 2, "defocus": 4, "gamma": 8, "offset": 16}
 # transform arithmetic: FP32 shared-memory FFTs, or the DFT as tensor-core
 # contractions with BF16 / TF32 operands (x3: hi + lo split, three products)
 PRECISION = {"fp32_fft": 0, "bf16": 1, "bf16x3": 2, "tf32": 3, "tf32x3": 4}
+OPTIMIZER = {"adam": 0, "adamw": 1, "nadam": 2, "rmsprop": 3}
 LOAD_INIT = 1
 
 # every symbol include/fpm.h declares
@@ -53,7 +54,8 @@ class Hparams(ctypes.Structure):
     _fields_ = [("lr_object", ctypes.c_float), ("lr_zernike", ctypes.c_float), ("lr_defocus", ctypes.c_float),
                 ("lr_gamma", ctypes.c_float), ("lr_offset", ctypes.c_float), ("beta1", ctypes.c_float),
                 ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("loss", ctypes.c_int32),
-                ("learn_mask", ctypes.c_uint32), ("precision", ctypes.c_int32)]
+                ("learn_mask", ctypes.c_uint32), ("precision", ctypes.c_int32), ("optimizer", ctypes.c_int32),
+                ("weight_decay", ctypes.c_float)]
 
 
 _lib = None
@@ -184,7 +186,7 @@ class Engine:
 
     # -- API ---------------------------------------------------------------
     def set_hparams(self, lr=None, betas=(0.9, 0.999), eps=1e-8, loss="amplitude", learn=("object",),
-                    precision="fp32_fft"):
+                    precision="fp32_fft", optimizer="adam", weight_decay=0.0):
         rates = dict(object=0.1, zernike=0.01, defocus=0.1, gamma=0.01, offset=0.01)
         rates.update(lr or {})
         lr = rates
@@ -192,7 +194,8 @@ class Engine:
         for k in learn:
             mask |= LEARN[k]
         hp = Hparams(lr["object"], lr["zernike"], lr["defocus"], lr["gamma"], lr["offset"],
-                     betas[0], betas[1], eps, LOSS[loss], mask, PRECISION[precision])
+                     betas[0], betas[1], eps, LOSS[loss], mask, PRECISION[precision], OPTIMIZER[optimizer],
+                     weight_decay)
         self._check(lib().fpm_set_hparams(self._h, ctypes.byref(hp)))
 
     def load(self, stack, init: bool = True):

@@ -12,7 +12,7 @@ import time
 
 import numpy as np
 
-from .engine import EDGE, LEARN, LOSS, PRECISION, FpmError, Geometry, Hparams, lib
+from .engine import EDGE, LEARN, LOSS, OPTIMIZER, PRECISION, FpmError, Geometry, Hparams, lib
 
 JOB_QUEUED, JOB_ACTIVE, JOB_DONE, JOB_FAILED = 0, 1, 2, 3
 
@@ -54,7 +54,8 @@ def _declare(L):
 
 
 def job_desc(m, upsample, led_offset, pupil_radius, lambda_um, dk_per_um, edge="aa", batch=8, max_epochs=40,
-             rel_tol=1e-4, seed=0, lr=None, learn=("object",), loss="amplitude", precision="fp32_fft"):
+             rel_tol=1e-4, seed=0, lr=None, learn=("object",), loss="amplitude", precision="fp32_fft",
+             optimizer="adam", weight_decay=0.0):
     """A job description; keep the returned tuple alive until it has been submitted."""
     off = np.ascontiguousarray(np.asarray(led_offset, np.float32).reshape(-1, 2))
     rates = dict(object=0.1, zernike=0.01, defocus=0.1, gamma=0.01, offset=0.01)
@@ -63,7 +64,7 @@ def job_desc(m, upsample, led_offset, pupil_radius, lambda_um, dk_per_um, edge="
     for k in learn:
         mask |= LEARN[k]
     hp = Hparams(rates["object"], rates["zernike"], rates["defocus"], rates["gamma"], rates["offset"],
-                 0.9, 0.999, 1e-8, LOSS[loss], mask, PRECISION[precision])
+                 0.9, 0.999, 1e-8, LOSS[loss], mask, PRECISION[precision], OPTIMIZER[optimizer], weight_decay)
     g = Geometry(m, off.shape[0], off.ctypes.data, lambda_um, dk_per_um, EDGE[edge])
     return JobDesc(g, pupil_radius, upsample, hp, batch, max_epochs, rel_tol, seed & ((1 << 64) - 1)), off
 

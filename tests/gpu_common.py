@@ -33,7 +33,8 @@ def push(eng: Engine, O, prm: orc.Params):
 
 
 def hparams_to_engine(eng: Engine, hp: orc.Hparams):
-    eng.set_hparams(lr=dict(hp.lr), betas=(hp.beta1, hp.beta2), eps=hp.eps, loss=hp.loss, learn=hp.learn)
+    eng.set_hparams(lr=dict(hp.lr), betas=(hp.beta1, hp.beta2), eps=hp.eps, loss=hp.loss, learn=hp.learn,
+                    optimizer=hp.optimizer, weight_decay=hp.weight_decay)
 
 
 def multiparam_problem(m=64, s=4, grid=5, pitch=None, R=None, edge="aa", seed=5, z=3.0):

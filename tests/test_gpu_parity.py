@@ -5,11 +5,14 @@ gradient, <= 1e-3 on the object after a fixed number of epochs (FP32 path).
 Each measured error is recorded for the parity report.
 """
 
+import ctypes
+
 import numpy as np
 import pytest
 
 import oracle as orc
 from paper_2408_13782_gb300 import FpmError
+from paper_2408_13782_gb300.engine import Hparams, lib
 from synth import recipes as S
 from tests.gpu_common import (engine_for, hparams_to_engine, multiparam_problem, push, record, rel_l2,
                               simulate)
@@ -168,6 +171,36 @@ def test_steps_multiparam_all_learnable():
         assert eo <= 1e-4, (k, eo)
         for name, ref in (("zernike", rec.prm.zernike), ("gamma", rec.prm.gamma), ("offset", rec.prm.offset)):
             assert rel_l2(st[name], ref) <= 1e-4, (k, name)
+        assert abs(st["defocus"] - rec.prm.defocus) <= 1e-4 * max(1.0, abs(rec.prm.defocus))
+
+
+@pytest.mark.parametrize("opt", ["adamw", "nadam", "rmsprop"])
+def test_steps_other_optimisers(opt):
+    """AdamW, NAdam and RMSprop steps on every parameter group against the oracle."""
+    c, I, g_t, prm, O = multiparam_problem(m=64, seed=21)
+    g = orc.Geometry(c.N, c.m, S.led_grid(c.grid, c.pitch, c.jitter, c.seed)[0], c.R, c.edge,
+                     c.lambda_um, c.dk_per_um)
+    learn = ("object", "zernike", "defocus", "gamma", "offset")
+    if opt == "rmsprop":  # no bias correction: the first steps are ~ lr / sqrt(1 - beta2) long
+        hp = orc.Hparams(lr=dict(object=0.02, zernike=0.001, defocus=0.005, gamma=0.001, offset=0.001),
+                         beta2=0.99, learn=learn, optimizer=opt)
+    else:
+        hp = orc.Hparams(lr=dict(object=0.5, zernike=0.01, defocus=0.1, gamma=0.01, offset=0.01),
+                         learn=learn, optimizer=opt, weight_decay=0.01 if opt == "adamw" else 0.0)
+    rec, eng = _oracle_and_engine(c, I, g, hp)
+    sched = S.schedule(g.n_leds, 4, 2, seed=3)
+    for k, b in enumerate(sched[:6]):
+        L_ref = rec.step(b)
+        L_got = eng.step(b)
+        assert abs(L_got - L_ref) <= 1e-5 * L_ref + 1e-12, (k, L_got, L_ref)
+        st = eng.get()
+        eo = rel_l2(st["object"], rec.O)
+        record(f"steps.{opt}.k{k}.object", eo)
+        assert eo <= 1e-4, (k, eo)
+        for name, ref in (("zernike", rec.prm.zernike), ("gamma", rec.prm.gamma), ("offset", rec.prm.offset)):
+            e = rel_l2(st[name], ref)
+            record(f"steps.{opt}.k{k}.{name}", e)
+            assert e <= 1e-4, (k, name, e)
         assert abs(st["defocus"] - rec.prm.defocus) <= 1e-4 * max(1.0, abs(rec.prm.defocus))
 
 
@@ -347,6 +380,12 @@ def test_errors_and_edge_cases():
         assert e.value.code == code, bad
     with pytest.raises(FpmError):
         eng.set(offset=np.full((g.n_leds, 2), 3.0))
+    # an unknown optimiser or a negative weight decay is refused; the handle keeps its settings
+    with pytest.raises(FpmError) as e:
+        eng.set_hparams(weight_decay=-0.1, optimizer="adamw")
+    assert e.value.code == -1
+    hp = Hparams(0.1, 0.01, 0.1, 0.01, 0.01, 0.9, 0.999, 1e-8, 0, 1, 0, 7, 0.0)
+    assert lib().fpm_set_hparams(eng.handle, ctypes.byref(hp)) == -1
     # ragged batch sizes back to back, B = 1 and B = n_leds
     for b in ([4], [0, 1, 2, 3, 4, 5, 6, 7, 8], [8, 2]):
         assert np.isfinite(eng.step(b))
