@@ -358,6 +358,58 @@ def tensor_forms_section(c, nominal, stack, flush, n_steps=40):
     return out
 
 
+def amplitude_psnr(O, o_true, s: int) -> float:
+    """PSNR (dB, peak 1) of the reconstructed amplitude against the true one, after the best
+    complex scale (the reconstruction is defined up to a global phase, and the intensity
+    factors can trade a global scale with the object). O: centred spectrum, 1/s^2 scaled."""
+    o = np.fft.ifft2(np.fft.ifftshift(np.asarray(O, np.complex128))) * (s * s)
+    a = np.vdot(o, o_true) / np.vdot(o, o)
+    err = np.abs(a * o) - np.abs(o_true)
+    return float(10.0 * np.log10(1.0 / np.mean(err * err)))
+
+
+def batch_sweep_section(c, nominal, stack, epochs=20, every=4, batches=(1, 4, 16, 64, 225)):
+    """Reconstruction quality against time for several batch sizes on the same noisy stack
+    (Fig. 4-style): B = 1 is the sequential mode (Eq. 7), B = n_leds the global one (Eq. 6).
+    Each epoch is one pass in a fresh random order (Eq. 14), its full batches as one CUDA
+    graph and the short tail batch on its own; wall-clock time with the device synchronised."""
+    import torch
+
+    from paper_2408_13782_gb300 import Engine
+    from synth import recipes as S
+    o_true = S.make_object(c.N, c.seed)
+    out = {"what": f"{epochs} epochs per batch size, Adam as in the headline workload, amplitude PSNR "
+                   "(peak 1) of the reconstructed object against the synthetic truth after the best "
+                   "complex scale, every " + str(every) + " epochs; wall-clock seconds of the epochs",
+           "runs": {}}
+    for B in batches:
+        eng = Engine(c.m, c.s, nominal, c.R, c.lambda_um, c.dk_per_um, c.edge)
+        eng.set_hparams(lr=dict(c.lr), learn=c.learn)
+        eng.load(stack, init=True)
+        sched = S.schedule(c.n_leds, B, epochs, c.seed)
+        nb = -(-c.n_leds // B)
+        t_run, curve = 0.0, [(0, 0.0, amplitude_psnr(eng.get()["object"], o_true, c.s))]
+        for e in range(epochs):
+            ep = sched[e * nb:(e + 1) * nb]
+            full = [b for b in ep if len(b) == B]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if full:
+                eng.run(np.stack(full), losses=False)
+            for b in ep:
+                if len(b) != B:
+                    eng.step(b, loss=False)
+            torch.cuda.synchronize()
+            t_run += time.perf_counter() - t0
+            if (e + 1) % every == 0:
+                curve.append((e + 1, t_run, amplitude_psnr(eng.get()["object"], o_true, c.s)))
+        eng.close()
+        out["runs"][str(B)] = {"epoch_s_psnr_db": [[k, round(t, 6), round(p, 3)] for k, t, p in curve],
+                               "steps_per_epoch": nb, "final_psnr_db": round(curve[-1][2], 3),
+                               "seconds": round(t_run, 6)}
+    return out
+
+
 def autograd_section(dev, reps=3):
     """Recompute-in-backward vs stored fields through the torch.autograd.Function
     on the 2048^2 / 512^2, 15 x 15-LED instance at batch 64: device memory held
@@ -554,6 +606,8 @@ def engine_arm(args):
     if rank == 0 and world == 1 and not args.no_variants:
         result["tensor_core_forms"] = tensor_forms_section(c, nominal, stack, flush)
         result["autograd_memory"] = autograd_section(dev)
+    if rank == 0 and world == 1 and not args.no_sweep:
+        result["batch_sweep"] = batch_sweep_section(c, nominal, stack)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         r = run_cpu_child(stack, args.cpu_sample_s, B, 10_000)
         result["cpu_baseline"] = {"value": r["updates"] / r["seconds"], "unit": UNIT, "cores": 1,
@@ -616,6 +670,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-variants", action="store_true",
                     help="skip the tensor-core DFT forms and the autograd memory study")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the reconstruction-quality sweep over batch sizes")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--cpu-worker", default=None)
     ap.add_argument("--cpu-leds", type=int, default=16)
