@@ -110,8 +110,8 @@ struct EngineRound {
 };
 // Reserve device room for n_steps steps of at most B slots and describe the handle.
 int engine_round_reserve(fpm_handle* h, int n_steps, int B, EngineRound* out);
-// Host side of one round: slot tables for idx[0..count), and the Adam bias
-// corrections of the next n_steps steps (advancing the handle's step count).
+// Host side of one round: slot tables for idx[0..count), and the optimiser
+// coefficients of the next n_steps steps (advancing the handle's step count).
 void engine_round_slots(const fpm_handle* h, const int32_t* idx, int count, int4* dst);
 void engine_round_coef(fpm_handle* h, int n_steps, float4* dst);
 // Launch arguments of one step of the handle (built-in loss, updating).
