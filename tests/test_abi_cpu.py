@@ -50,3 +50,38 @@ def test_create_rejects_bad_shapes_without_gpu(L):
     with pytest.raises(fpm.FpmError) as e:
         fpm.Engine(64, 4, np.array([[200.0, 0.0]]), 10.0, 0.532, 0.05)  # crop leaves the spectrum
     assert e.value.code == -2
+
+
+def test_ctypes_structures_match_the_header(tmp_path):
+    """Size and field offsets of every structure the Python binding mirrors, as the C
+    compiler lays them out from include/fpm.h."""
+    import ctypes
+    import shutil
+    import subprocess
+
+    from paper_2408_13782_gb300.engine import Geometry, Hparams
+    from paper_2408_13782_gb300.serve import JobDesc, JobStatus
+
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    mirrors = {"fpm_geometry": Geometry, "fpm_hparams": Hparams, "fpm_job_desc": JobDesc,
+               "fpm_job_status": JobStatus}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "fpm.h"', "int main(void) {"]
+    for cname, py in mirrors.items():
+        lines.append(f'  printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'  printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        cname, field, value = line.split()
+        got[(cname, field)] = int(value)
+    for cname, py in mirrors.items():
+        assert got[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
