@@ -21,6 +21,7 @@
 
 #include "../../include/fpm.h"
 #include "internal.h"
+#include "optcoef.h"
 
 using namespace fpmk;
 
@@ -219,28 +220,20 @@ int grow(fpm_handle* h, T** p, int* cap, int need) {
 void fill_coef(fpm_handle* h, int n_steps, float4* dst) {
   const double b1 = h->hp.beta1, b2 = h->hp.beta2;
   const int opt = h->hp.optimizer;
-  auto mu = [b1](double t) { return b1 * (1.0 - 0.5 * std::pow(0.96, 0.004 * t)); };
   if (opt == FPM_OPT_NADAM) {
     if (h->nadam_t > h->t_host || h->nadam_b1 != h->hp.beta1) {
       h->nadam_t = 0;
       h->nadam_prod = 1.0;
       h->nadam_b1 = h->hp.beta1;
     }
-    while (h->nadam_t < h->t_host) h->nadam_prod *= mu((double)++h->nadam_t);
+    h->nadam_prod = nadam_advance(b1, h->nadam_t, h->nadam_prod, h->t_host);
+    h->nadam_t = h->t_host;
   }
   double prod = h->nadam_prod;  // P at t_host (NAdam)
   for (int s = 0; s < n_steps; ++s) {
-    const double t = (double)(h->t_host + s + 1);
-    const float inv_sqrt_bc2 = (float)(1.0 / std::sqrt(1.0 - std::pow(b2, t)));
-    if (opt == FPM_OPT_NADAM) {
-      const double mt = mu(t), pt = prod * mt, pn = pt * mu(t + 1);
-      dst[s] = make_float4((float)(mu(t + 1) / (1.0 - pn)), inv_sqrt_bc2, (float)((1.0 - mt) / (1.0 - pt)), 0.f);
-      prod = pt;
-    } else if (opt == FPM_OPT_RMSPROP) {
-      dst[s] = make_float4(0.f, 1.f, 0.f, 0.f);
-    } else {
-      dst[s] = make_float4((float)(1.0 / (1.0 - std::pow(b1, t))), inv_sqrt_bc2, 0.f, 0.f);
-    }
+    float k[4];
+    prod = opt_coefficients(opt, b1, b2, h->t_host + s + 1, prod, k);
+    dst[s] = make_float4(k[0], k[1], k[2], k[3]);
   }
 }
 

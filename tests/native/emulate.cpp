@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "device.cuh"
+#include "optcoef.h"
 
 using namespace fpmk;
 
@@ -104,6 +105,16 @@ int main() {
       std::printf("\n");
     }
   }
+  // the optimisers' per-step coefficients (b1 = 0.9, b2 = 0.999), steps 1..12
+  for (int opt = 0; opt < 4; ++opt) {
+    double prod = 1.0;
+    for (int t = 1; t <= 12; ++t) {
+      float k[4];
+      prod = opt_coefficients(opt, 0.9, 0.999, t, prod, k);
+      std::printf("coef %d %d %.9g %.9g %.9g %.9g %.17g\n", opt, t, k[0], k[1], k[2], k[3], prod);
+    }
+  }
+  std::printf("nadam_advance %.17g\n", nadam_advance(0.9, 3, nadam_advance(0.9, 0, 1.0, 3), 12));
   // pupil value on a few q for fixed coefficients
   float zc[14];
   for (int j = 0; j < 14; ++j) zc[j] = 0.3f * (float)std::sin(2.1 * j + 0.3);

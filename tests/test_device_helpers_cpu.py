@@ -97,5 +97,26 @@ def test_column_form_matches_oracle(emulated):
         np.testing.assert_allclose([th, gx, gy], [ref_th, *ref_g], rtol=3e-6, atol=3e-6)
 
 
+def test_optimiser_coefficients_match_oracle(emulated):
+    """The host's per-step coefficients (handed to the update kernel) against the oracle's
+    definitions: Adam's bias corrections and NAdam's momentum schedule and running product."""
+    b1, b2, psi = 0.9, 0.999, 0.004
+    prod = 1.0
+    rows = {(int(v[0]), int(v[1])): [float(x) for x in v[2:]] for v in emulated["coef"]}
+    assert len(rows) == 48
+    for t in range(1, 13):
+        bc2 = 1.0 / np.sqrt(1 - b2 ** t)
+        for opt in (0, 1):   # Adam, AdamW
+            np.testing.assert_allclose(rows[(opt, t)][:4], [1 / (1 - b1 ** t), bc2, 0, 0], rtol=1e-7)
+        mu, mu_next = orc.nadam_mu(t, b1, psi), orc.nadam_mu(t + 1, b1, psi)
+        prod *= mu
+        got = rows[(2, t)]
+        np.testing.assert_allclose(got[:4], [mu_next / (1 - prod * mu_next), bc2, (1 - mu) / (1 - prod), 0],
+                                   rtol=1e-7)
+        assert got[4] == pytest.approx(prod, rel=1e-15)
+        assert rows[(3, t)][:4] == [0.0, 1.0, 0.0, 0.0]
+    assert float(emulated["nadam_advance"][0][0]) == pytest.approx(prod, rel=1e-15)
+
+
 def test_parallel_polynomial_entries_equal_serial(emulated):
     assert float(emulated["polyentry"][0][0]) <= 1e-6
