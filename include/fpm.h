@@ -227,7 +227,9 @@ int fpm_set_object_field(fpm_handle* h, const float* o);
 int64_t fpm_state_size(const fpm_handle* h);
 /* Layout: O, m_O, v_O ([N][N][2] each), then params, m_params, v_params
  * ([15 + 3 n_leds] each: zernike, z, gamma, delta), then {step count, epoch loss}
- * stored as two float64 in the last four floats. */
+ * stored as two float64 in the last four floats. The layout is the same for every
+ * optimiser: RMSprop leaves the m arrays at zero, and NAdam's product of momentum
+ * coefficients is rebuilt from the step count. */
 int fpm_get_state(fpm_handle* h, float* state);
 int fpm_set_state(fpm_handle* h, const float* state);
 
