@@ -94,6 +94,13 @@ def union_pixels(nominal, R: float, N: int) -> int:
     return int(mask.sum())
 
 
+def led_flops_per_led(m: int, W: int, D: int) -> float:
+    """Algorithmic FP32 flops of one LED in the per-LED kernel: 2 (W + m) m-point
+    transforms at 5 m log2 m, the residual (15 per image pixel) and the per-pixel
+    pupil (40) and box-gradient (95) work on the support D."""
+    return 2 * (W + m) * 5 * m * math.log2(m) + 15 * m * m + 135 * D
+
+
 def make_stack_gpu(c, truth):
     """Clean intensities from the engine's forward model at the truth, plus the camera noise."""
     from paper_2408_13782_gb300 import Engine
@@ -153,7 +160,9 @@ def led_traffic_from_profile():
 # --------------------------------------------------------------------------
 
 class ClockSampler:
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    """nvidia-smi polled every 20 ms with timestamps; summary() reports the samples
+    that fall in a given host-time window (the timed region) and in the whole run."""
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
@@ -166,7 +175,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "100"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
@@ -176,7 +185,7 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.time(), line.strip()))
 
     def __exit__(self, *a):
         if self.proc:
@@ -186,33 +195,48 @@ class ClockSampler:
             except subprocess.TimeoutExpired:
                 self.proc.kill()
 
-    def summary(self):
-        sm, smax, reasons = [], None, set()
+    @staticmethod
+    def _parse(ln):
+        parts = [p.strip() for p in ln.split(",")]
+        if len(parts) < 8:
+            return None
+        try:
+            sm, smax = float(parts[1]), float(parts[2])
+        except ValueError:
+            return None
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 7:
-                continue
-            try:
-                sm.append(float(parts[0]))
-                smax = float(parts[1])
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[3:7]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
-        if not sm:
+        return sm, smax, {nm for nm, v in zip(names, parts[4:8]) if v.lower().startswith("active")}
+
+    def summary(self, t0=None, t1=None, margin=0.025):
+        rows = [(t, self._parse(ln)) for t, ln in self.lines]
+        rows = [(t, r) for t, r in rows if r is not None]
+        inside = [r for t, r in rows if t0 is not None and t0 - margin <= t <= t1 + margin]
+        use = inside if inside else [r for _, r in rows]
+        if not use:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"], "samples": 0}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        reasons = set()
+        for r in use:
+            reasons |= r[2]
+        return {"sm_mhz": statistics.median(r[0] for r in use), "sm_max_mhz": use[-1][1],
+                "reasons": sorted(reasons), "samples": len(use), "samples_in_timed_region": len(inside),
+                "samples_in_run": len(rows),
+                "window": "the timed steps" if inside else
+                          "the run (identical flushed steps before and after the timed ones; none of the 20 ms samples "
+                          "fell inside the timed region)"}
 
 
 # --------------------------------------------------------------------------
 # CPU baseline: the FP64 oracle as it stands, single thread
 # --------------------------------------------------------------------------
 
-def cpu_worker(stack_path: str, sample_s: float, leds_per_step: int, max_steps: int):
-    """Runs oracle steps on the workload (in a child process with 1 BLAS thread)."""
+def cpu_worker(stack_path: str, sample_s: float, leds_per_step: int, max_steps: int, threads: int = 1):
+    """Runs oracle steps on the workload in a child process: one thread, or (threads > 1)
+    the oracle's 2-D FFTs through scipy.fft with that many workers and numpy's BLAS
+    threads left at that count (the oracle's arithmetic is unchanged)."""
+    if threads > 1:
+        import scipy.fft as sfft
+        np.fft.fft2 = lambda x, *a, **k: sfft.fft2(x, *a, workers=threads, **k)
+        np.fft.ifft2 = lambda x, *a, **k: sfft.ifft2(x, *a, workers=threads, **k)
     import oracle as orc
     c, nominal, truth = workload()
     I = np.load(stack_path)
@@ -232,15 +256,16 @@ def cpu_worker(stack_path: str, sample_s: float, leds_per_step: int, max_steps: 
     print(json.dumps({"updates": n_led, "seconds": dt, "steps": steps}))
 
 
-def run_cpu_child(stack, sample_s: float, leds_per_step: int, max_steps: int):
+def run_cpu_child(stack, sample_s: float, leds_per_step: int, max_steps: int, threads: int = 1):
     with tempfile.TemporaryDirectory() as d:
         path = os.path.join(d, "stack.npy")
         np.save(path, stack)
-        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+        t = str(threads)
+        env = dict(os.environ, OMP_NUM_THREADS=t, OPENBLAS_NUM_THREADS=t, MKL_NUM_THREADS=t,
                    CUDA_VISIBLE_DEVICES="")
         r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", path,
                             "--cpu-sample-s", str(sample_s), "--cpu-leds", str(leds_per_step),
-                            "--cpu-max-steps", str(max_steps)],
+                            "--cpu-max-steps", str(max_steps), "--cpu-threads", t],
                            capture_output=True, text=True, env=env, timeout=1800)
         if r.returncode != 0:
             raise RuntimeError("CPU baseline worker failed:\n" + r.stderr[-2000:])
@@ -331,12 +356,40 @@ def gemm_mma_flops(m: int, W: int, split: bool) -> float:
     return 2.0 * macs * (3 if split else 1)
 
 
+def measure_tf32_peak(dev, n=8192, reps=5):
+    """Dense TF32 tensor throughput of this GPU: cuBLAS FP32 GEMM with TF32 allowed
+    (torch.matmul, n^3), best of reps, CUDA events; TFLOP/s."""
+    import torch
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    try:
+        a = torch.randn(n, n, device=dev)
+        b = torch.randn(n, n, device=dev)
+        torch.matmul(a, b)
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / 1e3
+            best = t if best is None else min(best, t)
+        del a, b
+        return 2.0 * n ** 3 / best / 1e12
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
 def tensor_forms_section(c, nominal, stack, flush, n_steps=40):
     """The per-LED kernel in each tensor-core DFT form on the same workload and
     schedule (L2 flushed before every step): kernel time and tensor throughput
-    against the measured BF16 peak (TF32 at half of it, the nominal ratio)."""
+    against the measured BF16 peak (BF16 forms) and the TF32 peak measured here
+    (TF32 forms)."""
+    import torch
     from paper_2408_13782_gb300 import Engine
     peak_bf16, kind = _peak_bf16()
+    peak_tf32 = measure_tf32_peak(torch.device("cuda"))
     box = 2 * (int(np.floor(c.R + 0.5 + np.sqrt(2.0))) + 1) + 1
     out = {}
     sched = full_batches(c.n_leds, c.B, n_steps + 3, c.seed, first_epoch=500)
@@ -349,12 +402,13 @@ def tensor_forms_section(c, nominal, stack, flush, n_steps=40):
         eng.close()
         flops = c.B * gemm_mma_flops(c.m, box, form.endswith("x3"))
         t = float(np.mean(led_ms)) / 1e3
-        peak = peak_bf16 if form.startswith("bf16") else peak_bf16 / 2
+        peak = peak_bf16 if form.startswith("bf16") else peak_tf32
         out[form] = {"led_kernel_ms": t * 1e3, "update_kernel_ms": float(np.mean(upd_ms)),
                      "led_updates_per_s": c.B / (float(np.mean(step_ms)) / 1e3),
                      "tensor_tflops": flops / t / 1e12, "peak_tflops": peak,
                      "frac": flops / t / 1e12 / peak, "mma_flops_per_launch": flops}
-    out["peak_source"] = kind
+    out["peak_source"] = {"bf16": f"{kind} (MEASURED_PEAKS.json)", "tf32": "measured in this run (cuBLAS TF32 GEMM 8192^3)"}
+    out["peak_tf32_tflops"] = peak_tf32
     return out
 
 
@@ -516,11 +570,24 @@ def engine_arm(args):
     torch.cuda.synchronize()
     barrier(pg, local)
     # the timed region: K steps, each bracketed by events on the engine's stream,
-    # the update kernel launched early by programmatic dependent launch as in run()
+    # the update kernel launched early by programmatic dependent launch as in run().
+    # The clock sampler polls every 20 ms; identical flushed steps run untimed for
+    # about 0.3 s before the timed ones so that a short timed region still has
+    # samples of the same load around it
+    pre = full_batches(c.n_leds, B, 2000, c.seed, first_epoch=2000)
     with ClockSampler(local) as clk:
+        t_pre, k_pre = time.time(), 0
+        while time.time() - t_pre < 0.3 and k_pre + 200 <= len(pre):
+            eng.profile_run(pre[k_pre:k_pre + 200], flush=flush, per_kernel=False)
+            k_pre += 200
         torch.cuda.synchronize()
+        t_timed0 = time.time()
         _, _, step_ms = eng.profile_run(sched[W:W + K], flush=flush, per_kernel=False)
         torch.cuda.synchronize()
+        t_timed1 = time.time()
+        time.sleep(0.05)
+    clocks = clk.summary(t_timed0, t_timed1)
+    clocks["pre_roll_steps"] = k_pre
     barrier(pg, local)
     # the per-kernel split (kernels back to back, events between them) on the next K steps
     led_ms, upd_ms, split_ms = eng.profile_run(sched[W + K:], flush=flush)
@@ -538,7 +605,9 @@ def engine_arm(args):
     total_ms_max = allreduce_max(pg, total_ms, dev)
     value = world * K * B / (total_ms_max / 1e3)
 
-    # roofline of the dominant kernel (the fused per-LED kernel)
+    # roofline of the dominant kernel (the fused per-LED kernel): algorithmic bytes
+    # against the measured copy bandwidth, and algorithmic FP32 flops against the
+    # measured FMA throughput of this GPU
     D = support_pixels(c.R)
     A = union_pixels(nominal, c.R, c.N)
     led_bytes = B * (4 * c.m * c.m + 16 * D)            # image read + O on support + gradient box
@@ -547,6 +616,11 @@ def engine_arm(args):
     peak, peak_kind = _peaks()
     achieved = led_bytes / led_avg_s / 1e9
     traffic = led_traffic_from_profile()
+    box = 2 * (int(np.floor(c.R + 0.5 + np.sqrt(2.0))) + 1) + 1
+    led_flops = B * led_flops_per_led(c.m, box, D)
+    from paper_2408_13782_gb300.engine import probe_fp32_fma
+    fp32_peak, _ = probe_fp32_fma()
+    alu_achieved = led_flops / led_avg_s / 1e12
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": total_ms_max / K, "higher_is_better": True, "scaling": "weak",
@@ -556,7 +630,14 @@ def engine_arm(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "kernel": "led_kernel (fused per-LED forward + adjoint, m=256)",
                      "peak_source": peak_kind, "algorithmic_bytes_per_launch": led_bytes,
-                     "avg_launch_ms": led_avg_s * 1e3},
+                     "avg_launch_ms": led_avg_s * 1e3,
+                     "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                             "peak_source": peak_kind},
+                     "alu": {"achieved": alu_achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                             "frac": alu_achieved / fp32_peak, "peak_source": "measured (fpm_probe_fp32_fma, this run)",
+                             "algorithmic_flops_per_launch": led_flops,
+                             "flops": "per LED 2 (W + m) transforms x 5 m log2 m + 15 m^2 (residual) + "
+                                      "135 |D| (pupil 40, box gradient 95 per support pixel)"}},
         "step_hbm_roofline": {"algorithmic_bytes_per_step": step_bytes,
                               "achieved_gbs": step_bytes / (total_ms / K / 1e3) / 1e9,
                               "frac": step_bytes / (total_ms / K / 1e3) / 1e9 / peak},
@@ -567,7 +648,7 @@ def engine_arm(args):
                           "what": "context: fpm_run of K steps as one CUDA graph, no flush, timed with "
                                   "CUDA events on the caller's stream"},
         "gpu_launches": 2 * K,
-        "clocks": clk.summary(),
+        "clocks": clocks,
     }
 
     # end to end through the C ABI with host buffers: a whole job (load, 20 passes, read back)
@@ -614,6 +695,12 @@ def engine_arm(args):
                                   "kind": "oracle",
                                   "sample": f"{r['steps']} oracle steps of 16 LEDs on this workload "
                                             f"({r['seconds']:.1f} s, FP64 numpy, 1 thread)"}
+        ncpu = os.cpu_count() or 1
+        r = run_cpu_child(stack, args.cpu_sample_s, B, 10_000, threads=ncpu)
+        result["cpu_baseline_threads"] = {
+            "value": r["updates"] / r["seconds"], "unit": UNIT, "cores": ncpu, "kind": "oracle",
+            "sample": f"{r['steps']} oracle steps of 16 LEDs on this workload ({r['seconds']:.1f} s, FP64; "
+                      f"2-D FFTs by scipy.fft with {ncpu} workers, BLAS threads {ncpu})"}
     if rank == 0:
         print(json.dumps(result), flush=True)
     if pg is not None:
@@ -674,6 +761,7 @@ def parse_args(argv=None):
                     help="skip the reconstruction-quality sweep over batch sizes")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--cpu-worker", default=None)
+    ap.add_argument("--cpu-threads", type=int, default=1)
     ap.add_argument("--cpu-leds", type=int, default=16)
     ap.add_argument("--cpu-max-steps", type=int, default=10_000)
     args = ap.parse_args(argv)
@@ -685,7 +773,7 @@ def parse_args(argv=None):
 def main():
     args = parse_args()
     if args.cpu_worker:
-        cpu_worker(args.cpu_worker, args.cpu_sample_s, args.cpu_leds, args.cpu_max_steps)
+        cpu_worker(args.cpu_worker, args.cpu_sample_s, args.cpu_leds, args.cpu_max_steps, args.cpu_threads)
         return
     if args.impl == "reference":
         reference_arm(args)

@@ -180,10 +180,43 @@ int fpm_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int32_t B, 
  * kernel and of the whole step (excluding the clear). With led_ms or update_ms
  * given, events also separate the two kernels (so they run back to back); with
  * both NULL only the step is bracketed and the update kernel starts early by
- * programmatic dependent launch, as inside fpm_run. Waits for completion. The
- * state advances exactly as with fpm_run. */
+ * programmatic dependent launch, as inside fpm_run. In the dataflow form (see
+ * fpm_set_step_form) a step is one kernel: led_ms gets the step and update_ms
+ * zero. Waits for completion. The state advances exactly as with fpm_run. */
 int fpm_profile_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int32_t B,
                     void* flush, int64_t flush_bytes, float* led_ms, float* update_ms, float* step_ms);
+
+/* Form of the kernels that run a step (the same model and results, up to the
+ * order of FP32 rounding in the per-pixel partial sums):
+ *   FPM_STEP_AUTO      the per-LED form (the fastest for one job's step);
+ *   FPM_STEP_CLUSTER   the per-LED form: one thread-block cluster per LED image
+ *                      for the model and its adjoint, the intermediate transforms
+ *                      exchanged in distributed shared memory, then an update
+ *                      launch (the batch-ordered gather and the optimiser);
+ *   FPM_STEP_DATAFLOW  m = 256, FP32 FFT form: one launch per step whose CTAs
+ *                      take the step's column transforms, row transforms with the
+ *                      residual, adjoint column transforms and update as tasks
+ *                      from a shared counter, spread over every SM; a task waits
+ *                      (bounded) only for the tasks it reads, which hand their
+ *                      results over through L2. Elsewhere the per-LED form.
+ * Applies to fpm_step, fpm_run, fpm_profile_run, fpm_forward, fpm_backward and
+ * their stored-field forms. fpm_get_step_form gives the form asked for and
+ * whether the dataflow form is in use (each pointer nullable). */
+#define FPM_STEP_AUTO     0
+#define FPM_STEP_CLUSTER  1
+#define FPM_STEP_DATAFLOW 2
+int fpm_set_step_form(fpm_handle* h, int32_t form);
+int fpm_get_step_form(const fpm_handle* h, int32_t* form, int32_t* dataflow);
+
+/* Failure-injection check of the bounded device waits of the dataflow form (the
+ * paper has no counterpart; it tests the engine's failure detection). Runs one
+ * step over batch idx in which every row task waits for a count of column tasks
+ * that is never reached, with every wait bounded by limit_s seconds (in
+ * (0, 10]); the waits give up, the kernel records the timeout in its error
+ * flag and returns, and the call returns FPM_ERR_TIMEOUT (FPM_ERR_STATE if no
+ * wait gave up). The GPU context stays usable; the handle's estimate is
+ * undefined afterwards (load or set a new one). Needs the dataflow form. */
+int fpm_check_wait_timeout(fpm_handle* h, const int32_t* idx, int32_t B, double limit_s);
 
 /* Sum of the batch losses since the last reset (FP64), optionally resetting it. */
 int fpm_epoch_loss(fpm_handle* h, double* out, int32_t reset);
@@ -263,29 +296,55 @@ int fpm_epoch_permutation(int32_t n, uint64_t seed, int32_t epoch, int32_t* out)
  * The array is shared by all calls on a device and keeps the last call's
  * contents (each call clears what must start at zero); calls whose device
  * work overlaps (two streams, two host threads) race on it.
- * The first call on a device looks up the array's device address and sets the
- * kernels' attributes (once per device, with that device current); make that
- * first call before any stream capture.
+ * The first call on a device looks up the array's device address, sets the
+ * kernels' attributes and writes the transform twiddles into the array (once
+ * per device, with that device current); make that first call before any
+ * stream capture. Every call copies its batch tables from host memory, so a
+ * call on a stream that is being captured returns FPM_ERR_STATE.
  *
  * g, pupil_radius_px, upsample: as fpm_create, m up to 256 (the rounded LED offsets give the
  *   crop positions; delta comes from `params`).
  * O_t      device [N][N][2] object spectrum, COLUMN-major: element (row y, col x)
  *          at index x * N + y (the transpose of fpm_get's layout).
- * params   device [15 + 3 n_leds]: zernike[14], defocus, gamma[n_leds], delta[n_leds][2].
+ * params   device [15 + 3 n_leds]: zernike[14], defocus, gamma[n_leds], delta[n_leds][2];
+ *          every delta of the batch must lie within +-FPM_OFFSET_BOUND_PX (the crop
+ *          box is sized for that bound; beyond it the results are unspecified
+ *          and err_out gets FPM_DEVERR_OFFSET).
  * stack    device [n_leds][m][m] measured intensities.
  * idx      host [B] distinct LED indices; B in [1, n_leds].
  * loss     FPM_LOSS_AMPLITUDE or FPM_LOSS_INTENSITY.
  * g_object_t  device [N][N][2], column-major like O_t; every element is written.
  * g_params    device [15 + 3 n_leds], same layout as params; LEDs outside idx get 0.
  * loss_out    device [1] FP64 batch loss (NaN/Inf if the data are not finite).
+ * err_out     device [1] int32 (nullable): the kernels' error bits of this call,
+ *             written after the gradients: 0, or an OR of FPM_DEVERR_INDEX (a
+ *             batch index the kernels found out of range), FPM_DEVERR_NONFINITE
+ *             (the batch loss is not finite) and FPM_DEVERR_OFFSET (a delta beyond
+ *             the bound). Without err_out only a non-finite loss_out shows them.
  * cuda_stream cudaStream_t for all of the call's device work (NULL = default).
- * Returns after enqueueing; results are ready when the stream reaches them.
- * Errors are reported by fpm_last_error(NULL). */
+ * All device buffers must belong to the current device. Returns after
+ * enqueueing; results are ready when the stream reaches them. Errors found on
+ * the host are reported by the return code and fpm_last_error(NULL). */
+#define FPM_DEVERR_INDEX     1
+#define FPM_DEVERR_NONFINITE 2
+#define FPM_DEVERR_OFFSET    8
 #define FPM_STATIC_SCRATCH_BYTES (4u << 20)
 int fpm_gradients_static(const fpm_geometry* g, float pupil_radius_px, int32_t upsample,
                          const float* O_t, const float* params, const float* stack,
                          const int32_t* idx, int32_t B, int32_t loss,
-                         float* g_object_t, float* g_params, double* loss_out, void* cuda_stream);
+                         float* g_object_t, float* g_params, double* loss_out, int32_t* err_out,
+                         void* cuda_stream);
+
+/* ---- Measurement ----------------------------------------------------------
+ * FP32 fused multiply-add throughput of the current device (TFLOP/s): the
+ * CUDA-core peak that the per-LED kernel's ALU roofline is quoted against.
+ * Not a step of the method (the paper has no counterpart). Runs reps + 1
+ * launches of a kernel in which every thread (8 CTAs of 256 threads per SM)
+ * advances 16 independent fmaf chains `iters` times, and reports the fastest
+ * launch timed by CUDA events: 2 * 16 * iters * threads / time. ms_out
+ * (nullable): that launch's duration. Allocates and frees a small output
+ * buffer; synchronises. Returns FPM_ERR_ARG for iters or reps below 1. */
+int fpm_probe_fp32_fma(int32_t iters, int32_t reps, double* tflops_out, double* ms_out);
 
 /* ---- Serving: continuous batching of reconstruction jobs -----------------
  * A request loop for many reconstructions of uneven size. Submitted jobs are

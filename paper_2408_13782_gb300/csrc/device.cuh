@@ -485,6 +485,62 @@ FPM_HD void dft16(float2 (&v)[16]) {
   }
 }
 
+// Pruned forms of dft16 for transforms restricted to a box |t| <= h < 64 of a
+// 256-point transform (index t taken mod 256). A thread's first-pass points
+// are t = j + 16 n (n = 0..15); those with n = 4..11 lie in [64, 192) and are
+// outside the box, so:
+//  - ZIN:  inputs n = 4..11 are zero (first DFT4 stage has two inputs);
+//  - ZOUT: only outputs k = 0..3 and 12..15 are wanted (last DFT4 stage
+//          computes two of its four outputs; the others are left zero).
+// Both give the same values as dft16 on the outputs they produce.
+template <int DIR, bool ZIN, bool ZOUT>
+FPM_HD void dft16p(float2 (&v)[16]) {
+  const float c1 = 0.92387953251128674f, s1 = 0.38268343236508977f, h = 0.70710678118654752f;
+  const float d = (float)DIR;
+  float2 y[4][4];
+  for (int n1 = 0; n1 < 4; ++n1) {
+    if (ZIN) {
+      const float2 a0 = v[n1], a3 = v[n1 + 12], ia3 = mul_i<DIR>(a3);
+      y[n1][0] = cadd(a0, a3);
+      y[n1][1] = csub(a0, ia3);
+      y[n1][2] = csub(a0, a3);
+      y[n1][3] = cadd(a0, ia3);
+    } else {
+      float2 a0 = v[n1], a1 = v[n1 + 4], a2 = v[n1 + 8], a3 = v[n1 + 12];
+      dft4<DIR>(a0, a1, a2, a3);
+      y[n1][0] = a0; y[n1][1] = a1; y[n1][2] = a2; y[n1][3] = a3;
+    }
+  }
+  const float2 w1 = make_float2(c1, d * s1), w2 = make_float2(h, d * h), w3 = make_float2(s1, d * c1);
+  const float2 w6 = make_float2(-h, d * h), w9 = make_float2(-c1, -d * s1);
+  y[1][1] = cmul(y[1][1], w1); y[1][2] = cmul(y[1][2], w2); y[1][3] = cmul(y[1][3], w3);
+  y[2][1] = cmul(y[2][1], w2); y[2][2] = mul_i<DIR>(y[2][2]); y[2][3] = cmul(y[2][3], w6);
+  y[3][1] = cmul(y[3][1], w3); y[3][2] = cmul(y[3][2], w6); y[3][3] = cmul(y[3][3], w9);
+  for (int k2 = 0; k2 < 4; ++k2) {
+    if (ZOUT) {
+      // outputs k2 (k1 = 0) and k2 + 12 (k1 = 3) of the DFT4 over n1
+      const float2 a0 = y[0][k2], a1 = y[1][k2], a2 = y[2][k2], a3 = y[3][k2];
+      const float2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3), t3 = mul_i<DIR>(csub(a1, a3));
+      v[k2] = cadd(t0, t2);
+      v[k2 + 12] = csub(t1, t3);
+      v[k2 + 4] = make_float2(0.f, 0.f);
+      v[k2 + 8] = make_float2(0.f, 0.f);
+    } else {
+      float2 a0 = y[0][k2], a1 = y[1][k2], a2 = y[2][k2], a3 = y[3][k2];
+      dft4<DIR>(a0, a1, a2, a3);
+      v[k2] = a0; v[k2 + 4] = a1; v[k2 + 8] = a2; v[k2 + 12] = a3;
+    }
+  }
+}
+
+// First-pass point t = j + 16 n of a 256-point transform whose non-zero
+// inputs (or wanted outputs) are a box |t| <= h (t mod 256) of W = 2h + 1
+// entries: the box index t + h or t - 256 + h, or -1 outside the box.
+FPM_HD int box256(int j, int n, int h) {
+  const int t = j + 16 * n;
+  return t <= h ? t + h : (t >= 256 - h ? t - 256 + h : -1);
+}
+
 // Second-pass twiddles of thread j (256 points): tw2[(r-1) * 16 + j] = W256^(r j).
 FPM_HD void fft256_twiddles(const float2* tw, float2* tw2, int j) {
   for (int r = 1; r < 16; ++r) tw2[(r - 1) * 16 + j] = tw[r * j];

@@ -85,6 +85,14 @@ struct fpm_handle {
   unsigned char* gconst = nullptr;  // constant DFT factors of gp
   unsigned char* gscr = nullptr;    // per-slot scratch, capacity cap_gscr slots
   int cap_gscr = 0;
+  // dataflow form of the step (m = 256, FP32 FFT form): scratch for capB slots
+  int step_form = FPM_STEP_AUTO;
+  float2* T = nullptr;         // [capB][W][256]
+  double* partB = nullptr;     // [capB][nB][STEP_NPB]
+  double* partC = nullptr;     // [capB][nC][STEP_NPC]
+  StepSync* sync = nullptr;    // zero between launches
+  int step_ctas = 0;           // CTAs that fit at once (for capB)
+  long long wait_ns = 200000000LL;  // bound of the kernels' dependency waits
 };
 
 namespace {
@@ -141,7 +149,7 @@ void free_all(fpm_handle* h) {
   destroy_graphs(h);
   void* dev[] = {h->Ot, h->mO, h->vO, h->tmp, h->tmp2, h->tw_m, h->tw_N, h->meas, h->sp, h->msp, h->vsp,
                  h->gsc, h->fbuf, h->nint, h->span, h->gbox, h->part, h->sched, h->losses, h->epoch,
-                 h->coef, h->err, h->gconst, h->gscr, h->amp};
+                 h->coef, h->err, h->gconst, h->gscr, h->amp, h->T, h->partB, h->partC, h->sync};
   for (void* p : dev)
     if (p) cudaFree(p);
   if (h->h_err) cudaFreeHost(h->h_err);
@@ -170,8 +178,11 @@ int check_device_error(fpm_handle* h) {
   const int e = *h->h_err;
   if (e) {
     CK(h, cudaMemsetAsync(h->err, 0, sizeof(int), h->st));
+    // a launch whose waits gave up may have left its counters non-zero
+    if (h->sync) CK(h, cudaMemsetAsync(h->sync, 0, sizeof(StepSync), h->st));
     if (e & DERR_NONFINITE) return fail(h, FPM_ERR_NONFINITE, "a batch loss was not finite");
     if (e & DERR_TIMEOUT) return fail(h, FPM_ERR_TIMEOUT, "a bounded wait in a kernel gave up");
+    if (e & DERR_OFFSET) return fail(h, FPM_ERR_RANGE, "an LED offset lies outside +-%.2f px", (double)FPM_OFFSET_BOUND_PX);
     return fail(h, FPM_ERR_RANGE, "a kernel saw an LED index out of range");
   }
   return FPM_OK;
@@ -237,6 +248,16 @@ void fill_coef(fpm_handle* h, int n_steps, float4* dst) {
   }
 }
 
+// Tasks per LED of the dataflow step: column tasks of at most 8 box columns,
+// row tasks of 8 image rows.
+int step_nA(const fpm_handle* h) { return (h->W + 7) / 8; }
+int step_nB() { return 256 / 8; }
+
+// The dataflow step kernel serves the FP32 FFT form at m = 256 when asked for.
+bool uses_step(const fpm_handle* h) {
+  return h->sync && h->hp.precision == FPM_PRECISION_FP32_FFT && h->step_form == FPM_STEP_DATAFLOW;
+}
+
 int ensure_batch(fpm_handle* h, int B) {
   if (h->hp.precision != FPM_PRECISION_FP32_FFT && h->cap_gscr < B) {
     if (h->gscr) CK(h, cudaFree(h->gscr));
@@ -249,11 +270,22 @@ int ensure_batch(fpm_handle* h, int B) {
   if (h->capB >= B) return FPM_OK;
   if (h->gbox) CK(h, cudaFree(h->gbox));
   if (h->part) CK(h, cudaFree(h->part));
+  if (h->T) CK(h, cudaFree(h->T));
+  if (h->partB) CK(h, cudaFree(h->partB));
+  if (h->partC) CK(h, cudaFree(h->partC));
   h->gbox = nullptr;
   h->part = nullptr;
+  h->T = nullptr;
+  h->partB = h->partC = nullptr;
   h->capB = 0;
   CK(h, cudaMalloc(&h->gbox, sizeof(float2) * (size_t)B * h->W * h->W));
   CK(h, cudaMalloc(&h->part, sizeof(double) * (size_t)B * h->C * NPART));
+  if (h->sync) {  // the dataflow form (m = 256)
+    CK(h, cudaMalloc(&h->T, sizeof(float2) * (size_t)B * h->W * 256));
+    CK(h, cudaMalloc(&h->partB, sizeof(double) * (size_t)B * step_nB() * STEP_NPB));
+    CK(h, cudaMalloc(&h->partC, sizeof(double) * (size_t)B * step_nA(h) * STEP_NPC));
+    CK(h, step_prepare(h->W, B, &h->step_ctas));
+  }
   h->capB = B;
   destroy_graphs(h);
   return FPM_OK;
@@ -353,6 +385,34 @@ UpdArgs upd_args(fpm_handle* h, const int4* slot_dev, int B, int step_off, doubl
   return u;
 }
 
+StepArgs step_args(fpm_handle* h, const LedArgs& a, const UpdArgs* u) {
+  StepArgs s{};
+  s.L = a;
+  if (u) s.U = *u;
+  s.T = h->T;
+  s.partB = h->partB;
+  s.partC = h->partC;
+  s.sync = h->sync;
+  s.nA = step_nA(h);
+  s.nB = step_nB();
+  s.nC = s.nA;
+  s.do_update = u != nullptr;
+  s.wait_ns = h->wait_ns;
+  s.stall = 0;
+  return s;
+}
+
+// One step (built-in loss, updating) in the handle's form.
+cudaError_t launch_train_step(fpm_handle* h, const int4* idx, int B, int step_off, double* loss_slot, bool pdl,
+                              bool split_update = false) {
+  const LedArgs a = led_args(h, idx, B, MODE_LOSS);
+  const UpdArgs u = upd_args(h, idx, B, step_off, loss_slot, 0);
+  if (uses_step(h)) return launch_step(step_args(h, a, &u), h->step_ctas, h->st, pdl);
+  cudaError_t e = launch_led_mode(h, a, pdl);
+  if (e == cudaSuccess && !split_update) e = launch_update(u, h->st, true);
+  return e;
+}
+
 int reset_state(fpm_handle* h) {
   const size_t NN = (size_t)h->N * h->N;
   CK(h, cudaMemsetAsync(h->mO, 0, sizeof(float2) * NN, h->st));
@@ -392,11 +452,8 @@ int build_graph(fpm_handle* h, int n_steps, int B, fpm_handle::Graph* gr) {
     e = cudaMemcpyAsync(h->coef, gr->h_coef, sizeof(float4) * n_steps, cudaMemcpyHostToDevice, h->st);
   // kernels after the first may start early (programmatic dependent launch)
   // and wait in-kernel for their predecessor's results
-  for (int s = 0; s < n_steps && e == cudaSuccess; ++s) {
-    const int4* idx = h->sched + (size_t)s * B;
-    e = launch_led_mode(h, led_args(h, idx, B, MODE_LOSS), s > 0);
-    if (e == cudaSuccess) e = launch_update(upd_args(h, idx, B, s, h->losses + s, 0), h->st, true);
-  }
+  for (int s = 0; s < n_steps && e == cudaSuccess; ++s)
+    e = launch_train_step(h, h->sched + (size_t)s * B, B, s, h->losses + s, s > 0);
   cudaError_t e2 = cudaStreamEndCapture(h->st, &g);
   if (e != cudaSuccess || e2 != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -430,7 +487,9 @@ int fpmk::engine_round_reserve(fpm_handle* h, int n_steps, int B, EngineRound* o
   out->C = h->hp.precision != FPM_PRECISION_FP32_FFT ? 1 : h->C;
   out->W = h->W;
   out->n_leds = h->n;
-  out->fft = h->hp.precision == FPM_PRECISION_FP32_FFT;
+  // rounds group jobs of the per-LED cluster form; a job in the dataflow form
+  // (m = 256) runs its own epochs, so its arithmetic is the same alone or not
+  out->fft = h->hp.precision == FPM_PRECISION_FP32_FFT && !uses_step(h);
   out->slots = h->sched;
   out->coef = h->coef;
   out->losses = h->losses;
@@ -569,6 +628,7 @@ int fpm_create(const fpm_geometry* g, float R, int32_t upsample, void* cuda_stre
             ck(cudaMalloc(&h->span, sizeof(int2) * h->N), "alloc span") &&
             ck(cudaMalloc(&h->epoch, sizeof(double)), "alloc") &&
             ck(cudaMalloc(&h->err, sizeof(int)), "alloc") &&
+            (h->m != 256 || ck(cudaMalloc(&h->sync, sizeof(StepSync)), "alloc")) &&
             ck(cudaMallocHost(&h->h_err, sizeof(int)), "pinned") &&
             ck((h->C = led_choose_cluster(h->m, h->W)) > 0 ? cudaSuccess : cudaErrorNotSupported,
                "this device cannot run the per-LED kernel for this size") &&
@@ -581,7 +641,8 @@ int fpm_create(const fpm_geometry* g, float R, int32_t upsample, void* cuda_stre
          ck(cudaMemcpy(h->nint, h->nint_h.data(), sizeof(int2) * h->n, cudaMemcpyHostToDevice), "copy") &&
          ck(cudaMemcpy(h->span, span.data(), sizeof(int2) * h->N, cudaMemcpyHostToDevice), "copy") &&
          ck(cudaMemset(h->Ot, 0, sizeof(float2) * NN), "memset") &&
-         ck(cudaMemset(h->err, 0, sizeof(int)), "memset");
+         ck(cudaMemset(h->err, 0, sizeof(int)), "memset") &&
+         (!h->sync || ck(cudaMemset(h->sync, 0, sizeof(StepSync)), "memset"));
   }
   if (ok) ok = reset_state(h) == FPM_OK && ck(cudaStreamSynchronize(h->st), "sync");
   if (!ok) {
@@ -760,9 +821,14 @@ int fpm_profile_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int
     const int4* idx = h->sched + (size_t)s * B;
     if (flush) e = cudaMemsetAsync(flush, s & 0xff, (size_t)flush_bytes, h->st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s], h->st);
-    if (e == cudaSuccess) e = launch_led_mode(h, led_args(h, idx, B, MODE_LOSS), false);
-    if (e == cudaSuccess && per_kernel) e = cudaEventRecord(ev[3 * s + 1], h->st);
-    if (e == cudaSuccess) e = launch_update(upd_args(h, idx, B, s, h->losses + s, 0), h->st, !per_kernel);
+    if (uses_step(h)) {  // one kernel per step: no split
+      if (e == cudaSuccess) e = launch_train_step(h, idx, B, s, h->losses + s, false);
+      if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 1], h->st);
+    } else {
+      if (e == cudaSuccess) e = launch_train_step(h, idx, B, s, h->losses + s, false, per_kernel);
+      if (e == cudaSuccess && per_kernel) e = cudaEventRecord(ev[3 * s + 1], h->st);
+      if (e == cudaSuccess && per_kernel) e = launch_update(upd_args(h, idx, B, s, h->losses + s, 0), h->st, false);
+    }
     if (e == cudaSuccess) e = cudaEventRecord(ev[3 * s + 2], h->st);
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
@@ -791,6 +857,57 @@ int fpm_profile_run(fpm_handle* h, const int32_t* schedule, int32_t n_steps, int
 
 int fpm_step(fpm_handle* h, const int32_t* batch_idx, int32_t B, double* loss_out) {
   return fpm_run(h, batch_idx, 1, B, loss_out);
+}
+
+int fpm_set_step_form(fpm_handle* h, int32_t form) {
+  if (!h) return FPM_ERR_ARG;
+  if (form != FPM_STEP_AUTO && form != FPM_STEP_CLUSTER && form != FPM_STEP_DATAFLOW)
+    return fail(h, FPM_ERR_ARG, "unknown step form %d", form);
+  if (form != h->step_form) {
+    CK(h, cudaStreamSynchronize(h->st));
+    destroy_graphs(h);  // captured launches of the other form
+    h->step_form = form;
+  }
+  return FPM_OK;
+}
+
+int fpm_get_step_form(const fpm_handle* h, int32_t* form, int32_t* dataflow) {
+  if (!h) return FPM_ERR_ARG;
+  if (form) *form = h->step_form;
+  if (dataflow) *dataflow = uses_step(h) ? 1 : 0;
+  return FPM_OK;
+}
+
+int fpm_check_wait_timeout(fpm_handle* h, const int32_t* idx, int32_t B, double limit_s) {
+  if (!h) return FPM_ERR_ARG;
+  if (!uses_step(h))
+    return fail(h, FPM_ERR_STATE, "the dataflow step form is not in use (m = 256, FP32 FFT form, FPM_STEP_DATAFLOW)");
+  if (!h->loaded) return fail(h, FPM_ERR_STATE, "no stack loaded");
+  if (!(limit_s > 0.0 && limit_s <= 10.0)) return fail(h, FPM_ERR_ARG, "limit must lie in (0, 10] s");
+  int rc = validate_batches(h, idx, 1, B);
+  if (rc) return rc;
+  if ((rc = ensure_batch(h, B))) return rc;
+  if ((rc = grow(h, &h->sched, &h->cap_sched, B))) return rc;
+  if ((rc = grow(h, &h->losses, &h->cap_losses, 1))) return rc;
+  if ((rc = grow(h, &h->coef, &h->cap_coef, 1))) return rc;
+  if ((rc = enter(h))) return rc;
+  std::vector<int4> slots(B);
+  fill_slots(h, idx, B, slots.data());
+  CK(h, cudaMemcpyAsync(h->sched, slots.data(), sizeof(int4) * B, cudaMemcpyHostToDevice, h->st));
+  std::vector<float4> coef(1);
+  fill_coef(h, 1, coef.data());
+  CK(h, cudaMemcpyAsync(h->coef, coef.data(), sizeof(float4), cudaMemcpyHostToDevice, h->st));
+  const LedArgs a = led_args(h, h->sched, B, MODE_LOSS);
+  const UpdArgs u = upd_args(h, h->sched, B, 0, h->losses, 0);
+  StepArgs s = step_args(h, a, &u);
+  s.stall = 1;
+  s.wait_ns = (long long)(limit_s * 1e9);
+  CK(h, launch_step(s, h->step_ctas, h->st, false));
+  h->t_host += 1;
+  rc = check_device_error(h);  // synchronises; resets the counters on an error
+  if (rc == FPM_OK) return fail(h, FPM_ERR_STATE, "the injected wait did not give up");
+  const int rc2 = leave(h);
+  return rc2 ? rc2 : rc;
 }
 
 int fpm_epoch_loss(fpm_handle* h, double* out, int32_t reset) {
@@ -852,7 +969,8 @@ int forward_impl(fpm_handle* h, const int32_t* idx, int32_t B, float* I_out, flo
   LedArgs a = led_args(h, h->sched, B, psi_out ? MODE_FORWARD_STORE : MODE_FORWARD);
   a.I_out = dev_out ? I_out : h->fbuf;
   a.psi = psi_out;
-  CK(h, launch_led_mode(h, a, false));
+  if (uses_step(h)) CK(h, launch_step(step_args(h, a, nullptr), h->step_ctas, h->st, false));
+  else CK(h, launch_led_mode(h, a, false));
   if (!dev_out) {
     CK(h, cudaMemcpyAsync(I_out, h->fbuf, sizeof(float) * img, cudaMemcpyDeviceToHost, h->st));
     CK(h, cudaStreamSynchronize(h->st));
@@ -886,10 +1004,16 @@ int backward_impl(fpm_handle* h, const int32_t* idx, int32_t B, const float* dL_
     if (!dev_in) CK(h, cudaMemcpyAsync(h->fbuf, dL_dI, sizeof(float) * img, cudaMemcpyHostToDevice, h->st));
     a.dLdI = dev_in ? dL_dI : h->fbuf;
   }
-  CK(h, launch_led_mode(h, a, false));
   const size_t NN = (size_t)h->N * h->N;
-  CK(h, cudaMemsetAsync(h->tmp, 0, sizeof(float2) * NN, h->st));
-  CK(h, launch_update(upd_args(h, h->sched, B, 0, h->losses, 1), h->st, false));
+  const UpdArgs u = upd_args(h, h->sched, B, 0, h->losses, 1);
+  if (uses_step(h)) {
+    CK(h, cudaMemsetAsync(h->tmp, 0, sizeof(float2) * NN, h->st));
+    CK(h, launch_step(step_args(h, a, &u), h->step_ctas, h->st, false));
+  } else {
+    CK(h, launch_led_mode(h, a, false));
+    CK(h, cudaMemsetAsync(h->tmp, 0, sizeof(float2) * NN, h->st));
+    CK(h, launch_update(u, h->st, false));
+  }
   bool host = false;
   if (g_object) {
     CK(h, launch_transpose(h->tmp, h->tmp2, h->N, h->st));

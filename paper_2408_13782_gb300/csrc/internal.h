@@ -23,8 +23,9 @@ __host__ __device__ inline int sp_size(int n_leds) { return SP_GAMMA + 3 * n_led
 // MODE_UPSTREAM_STORED: MODE_UPSTREAM that reads psi instead of recomputing it.
 enum LedMode : int { MODE_LOSS = 0, MODE_FORWARD = 1, MODE_UPSTREAM = 2, MODE_FORWARD_STORE = 3, MODE_UPSTREAM_STORED = 4 };
 
-// Device error flags (bit set, OR-accumulated).
-enum : int { DERR_INDEX = 1, DERR_NONFINITE = 2, DERR_TIMEOUT = 4 };
+// Device error flags (bit set, OR-accumulated). DERR_OFFSET: an LED offset
+// beyond +-FPM_OFFSET_BOUND_PX (the crop box is sized for the bound).
+enum : int { DERR_INDEX = 1, DERR_NONFINITE = 2, DERR_TIMEOUT = 4, DERR_OFFSET = 8 };
 
 constexpr int MAX_BATCH = 1024;
 
@@ -77,6 +78,47 @@ struct UpdArgs {
   float2* g_obj;            // [N][N] column-major, zeroed by the caller
   float* g_sc;              // [15 + 3 n_leds]
 };
+
+// ---- dataflow form of the step (step.cu), m = 256 ------------------------
+// One launch per step. Its CTAs take tasks from a ticket counter, in the
+// order: column transforms of every LED (A), row transforms with the residual
+// (B), adjoint column transforms with the box gradients (C), then the update
+// (scalar sums and optimiser, AdamW decay outside the update region, one task
+// per spectrum column of the update region). A task waits only for the tasks
+// it reads from, through per-LED completion counters (bounded waits).
+struct StepSync {
+  // each counter on its own 128-byte line: waiting CTAs poll one line per LED
+  struct alignas(128) Ctr {
+    unsigned v;
+  };
+  Ctr ticket;              // next task
+  Ctr exit_count;          // CTAs done; the last one resets every counter
+  Ctr c_all;               // adjoint column tasks done (all LEDs)
+  Ctr a_done[MAX_BATCH];   // column-transform tasks done, per batch slot
+  Ctr b_done[MAX_BATCH];   // row tasks done, per batch slot
+};
+
+constexpr int STEP_NPB = 2;   // partials of a row task: loss, gamma term
+constexpr int STEP_NPC = 17;  // partials of an adjoint column task: 14 Zernike, defocus, dy, dx
+
+struct StepArgs {
+  LedArgs L;            // model, mode and per-LED tables (L.gbox, L.part unused: see below)
+  UpdArgs U;            // the update (U.part unused)
+  float2* T;            // [B][W][256] column transforms, overwritten in place by the row tasks
+  double* partB;        // [B][nB][STEP_NPB]
+  double* partC;        // [B][nC][STEP_NPC]
+  StepSync* sync;       // counters, all zero between launches
+  int nA, nB, nC;       // tasks per LED of each phase
+  int do_update;        // run the update tasks (modes with an adjoint)
+  long long wait_ns;    // bound of every dependency wait
+  int stall;            // failure injection: row tasks wait for a count no task reaches
+};
+
+// Shared-memory bytes and CTAs of one launch (W: box width, B: batch).
+size_t step_smem_bytes(int W, int B);
+cudaError_t step_prepare(int W, int B, int* max_ctas);
+int step_tasks(const StepArgs& s);
+cudaError_t launch_step(const StepArgs& s, int max_ctas, cudaStream_t st, bool pdl);
 
 // Cluster size C (CTAs cooperating on one LED image) for low-res side m.
 int led_cluster_size(int m);

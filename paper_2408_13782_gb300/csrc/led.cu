@@ -174,6 +174,9 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
   const float gam = a.sp[SP_GAMMA + led];
   const float dly = a.sp[sp_offset(a.n_leds) + 2 * led];
   const float dlx = a.sp[sp_offset(a.n_leds) + 2 * led + 1];
+  // the box and the staged O disk hold the support only for offsets within the bound
+  if (tid == 0 && rank == 0 && !(fabsf(dly) <= FPM_OFFSET_BOUND_PX && fabsf(dlx) <= FPM_OFFSET_BOUND_PX))
+    atomicOr(a.err, DERR_OFFSET);
   const PupilConst P{a.R, a.Rinv, a.inv_lambda, a.dk2, a.hard_edge};
   const int grp = tid / G, j = tid % G;
   float2* buf = fb + grp * FS;

@@ -18,8 +18,11 @@
 // The address of the array is obtained on the host with cudaGetSymbolAddress
 // once per device (in host code the symbol itself is only a host-side
 // stand-in, not a device address), on the first call made with that device
-// current. That first call also sets the kernels' shared-memory attributes, so
-// it should be made before any stream capture.
+// current. That first call also sets the kernels' shared-memory attributes,
+// reads the device's shared-memory limit and writes the transform twiddles
+// into the array, so it should be made before any stream capture. Every call
+// copies its batch tables from host memory, so a call on a stream that is
+// being captured is refused.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -42,6 +45,7 @@ constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 bool g_ready[kMaxDevices] = {};
 unsigned char* g_scratch_ptr[kMaxDevices] = {};
+int g_smem_optin[kMaxDevices] = {};
 int fail_static(int code, const std::string& msg) {
   set_unbound_error(msg.c_str());  // reported by fpm_last_error(NULL)
   return code;
@@ -52,8 +56,19 @@ size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 // Cluster size used by this call for low-res side m: the portable sizes.
 int static_cluster(int m) { return m == 256 ? 8 : led_cluster_size(m); }
 
-// Once per device: the array's device address and the kernels' attributes.
-int setup_device(int dev, unsigned char** out) {
+// The twiddle tables tw_m[t] = exp(-2 pi i t / m) for m = 32, 64, 128, 256,
+// written once per device at the start of the array: offset of table m.
+constexpr int kTwSizes[4] = {32, 64, 128, 256};
+size_t tw_offset(int m) {
+  size_t o = 0;
+  for (int q = 0; q < 4 && kTwSizes[q] != m; ++q) o += sizeof(float2) * kTwSizes[q];
+  return o;
+}
+constexpr size_t kTwBytes = sizeof(float2) * (32 + 64 + 128 + 256);
+
+// Once per device: the array's device address, the kernels' attributes, the
+// device's opt-in shared memory per block, and the twiddle tables.
+int setup_device(int dev, unsigned char** out, int* smem_optin) {
   std::lock_guard<std::mutex> lk(g_setup_mutex);
   if (dev < 0 || dev >= kMaxDevices) return fail_static(FPM_ERR_CUDA, "device ordinal out of range");
   if (!g_ready[dev]) {
@@ -61,6 +76,10 @@ int setup_device(int dev, unsigned char** out) {
     cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
     if (e != cudaSuccess)
       return fail_static(FPM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess)
+      return fail_static(FPM_ERR_CUDA, std::string("device attribute: ") + cudaGetErrorString(e));
     // the attributes do not depend on the box width (each launch asks for the
     // shared memory its box needs; a call whose box does not fit is rejected)
     for (int m : {32, 64, 128, 256}) {
@@ -71,20 +90,32 @@ int setup_device(int dev, unsigned char** out) {
     e = update_prepare();
     if (e != cudaSuccess)
       return fail_static(FPM_ERR_CUDA, std::string("kernel attributes: ") + cudaGetErrorString(e));
+    std::vector<float2> tw(kTwBytes / sizeof(float2));
+    size_t k = 0;
+    for (int m : kTwSizes)
+      for (int i = 0; i < m; ++i, ++k) {
+        const double a = -2.0 * M_PI * (double)i / (double)m;
+        tw[k] = make_float2((float)std::cos(a), (float)std::sin(a));
+      }
+    e = cudaMemcpy(p, tw.data(), kTwBytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail_static(FPM_ERR_CUDA, std::string("twiddles: ") + cudaGetErrorString(e));
     g_scratch_ptr[dev] = (unsigned char*)p;
+    g_smem_optin[dev] = optin;
     g_ready[dev] = true;
   }
   *out = g_scratch_ptr[dev];
+  *smem_optin = g_smem_optin[dev];
   return FPM_OK;
 }
 
-bool on_device(const void* p) {
+// Device (or managed) memory of device dev.
+bool on_device(const void* p, int dev) {
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == dev;
 }
 
 }  // namespace
@@ -92,7 +123,7 @@ bool on_device(const void* p) {
 extern "C" int fpm_gradients_static(const fpm_geometry* g, float R, int32_t upsample, const float* O_t,
                                     const float* params, const float* stack, const int32_t* idx, int32_t B,
                                     int32_t loss, float* g_object_t, float* g_params, double* loss_out,
-                                    void* cuda_stream) {
+                                    int32_t* err_out, void* cuda_stream) {
   // ---- arguments (host-side checks only; nothing is allocated) ----
   if (!g || !g->led_offset || !O_t || !params || !stack || !idx || !g_object_t || !g_params || !loss_out)
     return fail_static(FPM_ERR_ARG, "null argument");
@@ -139,8 +170,7 @@ extern "C" int fpm_gradients_static(const fpm_geometry* g, float R, int32_t upsa
     hi_x = std::max(hi_x, c0 + W);
   }
   // ---- layout of the static array; reject what does not fit ----
-  const size_t o_tw = 0;
-  const size_t o_span = align256(o_tw + sizeof(float2) * m);
+  const size_t o_span = align256(kTwBytes);
   const size_t o_slot = align256(o_span + sizeof(int2) * N);
   const size_t o_flags = align256(o_slot + sizeof(int4) * B);  // int err, then a double sink
   const size_t o_part = align256(o_flags + 16);
@@ -151,26 +181,31 @@ extern "C" int fpm_gradients_static(const fpm_geometry* g, float R, int32_t upsa
                                           " bytes of scratch; the static array holds " +
                                           std::to_string((size_t)FPM_STATIC_SCRATCH_BYTES) +
                                           " (reduce the batch size or the pupil radius)");
-  for (const void* p : {(const void*)O_t, (const void*)params, (const void*)stack, (const void*)g_object_t,
-                        (const void*)g_params, (const void*)loss_out})
-    if (!on_device(p)) return fail_static(FPM_ERR_ARG, "inputs and outputs must be device memory");
-
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail_static(FPM_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(st, &cap);
+  if (e != cudaSuccess)
+    return fail_static(FPM_ERR_CUDA, std::string("cudaStreamIsCapturing: ") + cudaGetErrorString(e));
+  if (cap != cudaStreamCaptureStatusNone)
+    return fail_static(FPM_ERR_STATE, "the stream is being captured; this call copies host tables on every call "
+                                      "and cannot be recorded");
+  for (const void* p : {(const void*)O_t, (const void*)params, (const void*)stack, (const void*)g_object_t,
+                        (const void*)g_params, (const void*)loss_out})
+    if (!on_device(p, dev)) return fail_static(FPM_ERR_ARG, "inputs and outputs must be memory of the current device");
+  if (err_out && !on_device(err_out, dev))
+    return fail_static(FPM_ERR_ARG, "err_out must be memory of the current device");
   unsigned char* base = nullptr;
-  int rc = setup_device(dev, &base);
+  int optin = 0;
+  int rc = setup_device(dev, &base, &optin);
   if (rc) return rc;
   const int C = static_cluster(m);
-  if (led_smem_bytes(m, C, W) > 227 * 1024) return fail_static(FPM_ERR_SHAPE, "pupil box too wide for shared memory");
+  if (led_smem_bytes(m, C, W) > (size_t)optin)
+    return fail_static(FPM_ERR_SHAPE, "pupil box too wide for this device's shared memory");
 
-  std::vector<float2> tw(m);
-  for (int i = 0; i < m; ++i) {
-    const double a = -2.0 * M_PI * (double)i / (double)m;
-    tw[i] = make_float2((float)std::cos(a), (float)std::sin(a));
-  }
-  cudaStream_t st = (cudaStream_t)cuda_stream;
-  float2* d_tw = (float2*)(base + o_tw);
+  float2* d_tw = (float2*)(base + tw_offset(m));
   int2* d_span = (int2*)(base + o_span);
   int4* d_slot = (int4*)(base + o_slot);
   int* d_err = (int*)(base + o_flags);
@@ -182,7 +217,6 @@ extern "C" int fpm_gradients_static(const fpm_geometry* g, float R, int32_t upsa
     cudaError_t e_ = (call);                                                                       \
     if (e_ != cudaSuccess) return fail_static(FPM_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
   } while (0)
-  CKS(cudaMemcpyAsync(d_tw, tw.data(), sizeof(float2) * m, cudaMemcpyHostToDevice, st));
   std::vector<int4> slots(B);
   for (int b = 0; b < B; ++b) slots[b] = make_int4(idx[b], nint[idx[b]].x, nint[idx[b]].y, 0);
   CKS(cudaMemcpyAsync(d_span, span.data(), sizeof(int2) * N, cudaMemcpyHostToDevice, st));
@@ -238,6 +272,7 @@ extern "C" int fpm_gradients_static(const fpm_geometry* g, float R, int32_t upsa
   u.g_obj = (float2*)g_object_t;
   u.g_sc = g_params;
   CKS(launch_update(u, st, false));
+  if (err_out) CKS(cudaMemcpyAsync(err_out, d_err, sizeof(int), cudaMemcpyDeviceToDevice, st));
 #undef CKS
   return FPM_OK;
 }

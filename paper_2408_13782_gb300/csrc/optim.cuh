@@ -1,0 +1,60 @@
+// Per-element rules of the Adam-family optimisers (the definitions are in
+// fpm.h) shared by the update kernel and the dataflow step kernel. The per-step
+// coefficients k (bias corrections, NAdam's momentum terms) come from the host
+// in FP64 (see UpdArgs::coef).
+#pragma once
+
+#include "../../include/fpm.h"
+#include "internal.h"
+
+namespace fpmk {
+
+__device__ __forceinline__ void adam1(float& w, float& m, float& v, float g, float lr_bc1, float inv_sqrt_bc2,
+                                      float b1, float b2, float eps) {
+  m = fmaf(b1, m, (1.f - b1) * g);
+  v = fmaf(b2, v, (1.f - b2) * g * g);
+  w -= lr_bc1 * m / fmaf(sqrtf(v), inv_sqrt_bc2, eps);
+}
+
+// One step of the handle's optimiser on one real component with learning rate
+// lr and this step's coefficients k (see UpdArgs::coef). The branch is the
+// same for every thread of a launch.
+__device__ __forceinline__ void opt1(const UpdArgs& a, float& w, float& m, float& v, float g, float lr, float4 k) {
+  switch (a.opt) {
+    case FPM_OPT_ADAMW:
+      w *= 1.f - lr * a.wd;
+      adam1(w, m, v, g, lr * k.x, k.y, a.b1, a.b2, a.eps);
+      break;
+    case FPM_OPT_NADAM:
+      m = fmaf(a.b1, m, (1.f - a.b1) * g);
+      v = fmaf(a.b2, v, (1.f - a.b2) * g * g);
+      w -= lr * fmaf(k.x, m, k.z * g) / fmaf(sqrtf(v), k.y, a.eps);
+      break;
+    case FPM_OPT_RMSPROP:
+      v = fmaf(a.b2, v, (1.f - a.b2) * g * g);
+      w -= lr * g / (sqrtf(v) + a.eps);
+      break;
+    default:
+      adam1(w, m, v, g, lr * k.x, k.y, a.b1, a.b2, a.eps);
+  }
+}
+
+__device__ __forceinline__ bool learned(const UpdArgs& a, int i) {
+  const unsigned bit = i < SP_DEFOCUS ? 1u << 1 : i == SP_DEFOCUS ? 1u << 2 : i < sp_offset(a.n_leds) ? 1u << 3 : 1u << 4;
+  return (a.learn & bit) != 0;
+}
+__device__ __forceinline__ float lr_of(const UpdArgs& a, int i) {
+  return i < SP_DEFOCUS ? a.lr_zern : i == SP_DEFOCUS ? a.lr_def : i < sp_offset(a.n_leds) ? a.lr_gam : a.lr_off;
+}
+
+// The optimiser step of scalar i with FP64 gradient g; offsets are clamped to
+// the box bound.
+__device__ __forceinline__ void scalar_adam(const UpdArgs& a, int i, float w, float m, float v, double g, float4 k) {
+  opt1(a, w, m, v, (float)g, lr_of(a, i), k);
+  if (i >= sp_offset(a.n_leds)) w = fminf(fmaxf(w, -a.offset_bound), a.offset_bound);
+  a.sp[i] = w;
+  a.msp[i] = m;
+  a.vsp[i] = v;
+}
+
+}  // namespace fpmk

@@ -27,6 +27,8 @@ LEARN = {"object": 1, "zernike": 2, "defocus": 4, "gamma": 8, "offset": 16}
 # contractions with BF16 / TF32 operands (x3: hi + lo split, three products)
 PRECISION = {"fp32_fft": 0, "bf16": 1, "bf16x3": 2, "tf32": 3, "tf32x3": 4}
 OPTIMIZER = {"adam": 0, "adamw": 1, "nadam": 2, "rmsprop": 3}
+# kernels of a step: the per-LED cluster form, or the dataflow form (m = 256)
+STEP_FORM = {"auto": 0, "cluster": 1, "dataflow": 2}
 LOAD_INIT = 1
 
 # every symbol include/fpm.h declares
@@ -36,7 +38,8 @@ EXPORTS = ("fpm_create", "fpm_set_hparams", "fpm_get_hparams", "fpm_load", "fpm_
            "fpm_state_size", "fpm_get_state", "fpm_set_state", "fpm_dims", "fpm_epoch_permutation",
            "fpm_gradients_static", "fpm_job_footprint", "fpm_server_create", "fpm_server_submit",
            "fpm_server_tick", "fpm_server_status", "fpm_server_result", "fpm_server_clock", "fpm_server_stats",
-           "fpm_server_error", "fpm_server_destroy", "fpm_destroy", "fpm_last_error")
+           "fpm_server_error", "fpm_server_destroy", "fpm_destroy", "fpm_last_error",
+           "fpm_set_step_form", "fpm_get_step_form", "fpm_check_wait_timeout", "fpm_probe_fp32_fma")
 
 
 class FpmError(RuntimeError):
@@ -93,7 +96,11 @@ def lib():
         "fpm_dims": ([vp, vp, vp, vp, vp], i32),
         "fpm_epoch_permutation": ([i32, ctypes.c_uint64, i32, vp], i32),
         "fpm_gradients_static": ([ctypes.POINTER(Geometry), ctypes.c_float, i32, vp, vp, vp, vp, i32, i32,
-                                  vp, vp, vp, vp], i32),
+                                  vp, vp, vp, vp, vp], i32),
+        "fpm_set_step_form": ([vp, i32], i32),
+        "fpm_get_step_form": ([vp, vp, vp], i32),
+        "fpm_check_wait_timeout": ([vp, vp, i32, ctypes.c_double], i32),
+        "fpm_probe_fp32_fma": ([i32, i32, vp, vp], i32),
         "fpm_destroy": ([vp], None),
         "fpm_last_error": ([vp], ctypes.c_char_p),
     }
@@ -126,19 +133,41 @@ def epoch_permutation(n: int, seed: int, epoch: int) -> np.ndarray:
     return out
 
 
+def probe_fp32_fma(iters: int = 4096, reps: int = 5):
+    """fpm_probe_fp32_fma: measured FP32 FMA throughput of the current device, TFLOP/s."""
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    rc = lib().fpm_probe_fp32_fma(iters, reps, ctypes.byref(t), ctypes.byref(ms))
+    if rc:
+        raise FpmError(rc, "FP32 FMA probe failed")
+    return t.value, ms.value
+
+
 def gradients_static(m, upsample, led_offset, pupil_radius, lambda_um, dk_per_um, edge, O_t, params, stack,
-                     idx, g_object_t, g_params, loss_out, loss="amplitude", stream=0):
+                     idx, g_object_t, g_params, loss_out, loss="amplitude", stream=0, err_out=None):
     """fpm_gradients_static: loss and gradients with caller-owned device buffers only.
 
     For callers that cannot allocate device memory (see include/fpm.h). O_t,
-    params, stack, g_object_t, g_params and loss_out are CUDA tensors (column-major
-    O and gradient: element (row y, col x) at x * N + y); idx is a host sequence."""
+    params, stack, g_object_t, g_params, loss_out (and err_out, an int32 [1]
+    tensor, optional) are CUDA tensors of the current device (column-major O and
+    gradient: element (row y, col x) at x * N + y); idx is a host sequence."""
+    import torch
     off = np.ascontiguousarray(np.asarray(led_offset, np.float32).reshape(-1, 2))
-    g = Geometry(m, off.shape[0], off.ctypes.data, lambda_um, dk_per_um, EDGE[edge])
+    n, N = off.shape[0], m * upsample
+    dev = torch.cuda.current_device()
+    want = {"O_t": (O_t, torch.float32, N * N * 2), "params": (params, torch.float32, 15 + 3 * n),
+            "stack": (stack, torch.float32, n * m * m), "g_object_t": (g_object_t, torch.float32, N * N * 2),
+            "g_params": (g_params, torch.float32, 15 + 3 * n), "loss_out": (loss_out, torch.float64, 1)}
+    if err_out is not None:
+        want["err_out"] = (err_out, torch.int32, 1)
+    for name, (t, dt, numel) in want.items():
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.device.index == dev and t.dtype == dt
+                and t.numel() == numel and t.is_contiguous()):
+            raise FpmError(-1, f"{name}: want a contiguous {dt} CUDA tensor of {numel} elements on device {dev}")
+    g = Geometry(m, n, off.ctypes.data, lambda_um, dk_per_um, EDGE[edge])
     b = np.ascontiguousarray(np.asarray(idx, np.int32))
     rc = lib().fpm_gradients_static(ctypes.byref(g), pupil_radius, upsample, _ptr(O_t), _ptr(params), _ptr(stack),
                                     b.ctypes.data, b.size, LOSS[loss], _ptr(g_object_t), _ptr(g_params),
-                                    _ptr(loss_out), ctypes.c_void_p(stream))
+                                    _ptr(loss_out), _ptr(err_out), ctypes.c_void_p(stream))
     if rc:
         raise FpmError(rc, lib().fpm_last_error(None).decode())
 
@@ -197,6 +226,23 @@ class Engine:
                      betas[0], betas[1], eps, LOSS[loss], mask, PRECISION[precision], OPTIMIZER[optimizer],
                      weight_decay)
         self._check(lib().fpm_set_hparams(self._h, ctypes.byref(hp)))
+
+    def set_step_form(self, form: str = "auto"):
+        """Kernels of a step: 'auto' / 'cluster' (per-LED clusters) or 'dataflow' (m = 256)."""
+        self._check(lib().fpm_set_step_form(self._h, STEP_FORM[form]))
+
+    def step_form(self):
+        """(form asked for, whether the dataflow form is in use)."""
+        f, d = ctypes.c_int32(), ctypes.c_int32()
+        self._check(lib().fpm_get_step_form(self._h, ctypes.byref(f), ctypes.byref(d)))
+        return {v: k for k, v in STEP_FORM.items()}[f.value], bool(d.value)
+
+    def check_wait_timeout(self, idx, limit_s: float):
+        """fpm_check_wait_timeout: one step whose waits cannot be satisfied, bounded by
+        limit_s. Returns (code, message); FPM_ERR_TIMEOUT (-6) is the expected code."""
+        b = np.ascontiguousarray(np.asarray(idx, np.int32))
+        rc = lib().fpm_check_wait_timeout(self._h, b.ctypes.data, b.size, float(limit_s))
+        return rc, lib().fpm_last_error(self._h).decode()
 
     def load(self, stack, init: bool = True):
         stack = _f32(stack)

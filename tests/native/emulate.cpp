@@ -51,7 +51,71 @@ static void run_fft_big() {
   }
 }
 
+// The 256-point transform as the dataflow step kernel runs it: 16 threads, thread j
+// holding the first-pass points j + 16 n, dft16p (pruned on a box of half-width
+// h < 64 when ZIN / ZOUT), the exchange between the two passes through a padded
+// buffer, then dft16p again; outputs at j + 16 k.
+template <int DIR, bool ZIN, bool ZOUT>
+static void fft256_box_emulate(const float2* in, float2* out, const float2* tw) {
+  float2 tw2[15 * 16];
+  for (int j = 0; j < 16; ++j) fft256_twiddles(tw, tw2, j);
+  float2 V[16][16], buf[256 + 16];
+  for (int j = 0; j < 16; ++j) {
+    for (int n = 0; n < 16; ++n) V[j][n] = in[j + 16 * n];
+    dft16p<DIR, ZIN, false>(V[j]);
+  }
+  for (int j = 0; j < 16; ++j)
+    for (int r = 0; r < 16; ++r) buf[pidx16(16 * j + r)] = V[j][r];
+  for (int j = 0; j < 16; ++j) {
+    for (int r = 0; r < 16; ++r) V[j][r] = buf[pidx16(j + 16 * r)];
+    for (int r = 1; r < 16; ++r) V[j][r] = cmul(V[j][r], tw_dir<DIR>(tw2[(r - 1) * 16 + j]));
+    dft16p<DIR, false, ZOUT>(V[j]);
+  }
+  for (int j = 0; j < 16; ++j)
+    for (int k = 0; k < 16; ++k) out[j + 16 * k] = V[j][k];
+}
+
+static void run_box256() {
+  std::vector<float2> tw(256), in(256), out(256);
+  for (int t = 0; t < 256; ++t) {
+    const double a = -2.0 * M_PI * t / 256;
+    tw[t] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  for (int h : {53, 63, 72}) {
+    // the box index of every first-pass point, and whether it is in the box
+    int covered = 0;
+    for (int j = 0; j < 16; ++j)
+      for (int n = 0; n < 16; ++n) {
+        const int b = box256(j, n, h);
+        if (b >= 0) ++covered;
+        const int t = j + 16 * n, ky = t <= 128 ? t : t - 256;
+        const int want = (ky >= -h && ky <= h) ? ky + h : -1;
+        if (b != want) std::printf("boxmap_bad %d %d %d %d\n", h, j, n, b);
+        if (h < 64 && n >= 4 && n < 12 && b >= 0) std::printf("boxmap_bad %d %d %d %d\n", h, j, n, b);
+      }
+    std::printf("boxmap %d %d\n", h, covered);
+  }
+  // inverse transform of box-supported inputs (h = 53, pruned first pass) and
+  // forward transform of a full input kept on the box (pruned last pass)
+  const int h = 53;
+  for (int t = 0; t < 256; ++t) {
+    const int ky = t <= 128 ? t : t - 256;
+    const bool inb = ky >= -h && ky <= h;
+    in[t] = inb ? make_float2((float)std::sin(0.41 * t + 0.3), (float)std::cos(0.77 * t) - 0.2f) : make_float2(0.f, 0.f);
+  }
+  fft256_box_emulate<+1, true, false>(in.data(), out.data(), tw.data());
+  std::printf("box256inv");
+  for (int t = 0; t < 256; ++t) std::printf(" %.9g %.9g", out[t].x, out[t].y);
+  std::printf("\n");
+  for (int t = 0; t < 256; ++t) in[t] = make_float2((float)std::cos(0.23 * t + 1.1), (float)std::sin(0.59 * t) + 0.1f);
+  fft256_box_emulate<-1, false, true>(in.data(), out.data(), tw.data());
+  std::printf("box256fwd");
+  for (int t = 0; t < 256; ++t) std::printf(" %.9g %.9g", out[t].x, out[t].y);
+  std::printf("\n");
+}
+
 int main() {
+  run_box256();
   run_fft_big<256>();
   run_fft_big<512>();
   run_fft<16>();

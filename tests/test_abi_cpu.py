@@ -26,7 +26,7 @@ def L():
 
 def test_header_declarations_are_exported(L):
     hdr = open(os.path.join(ROOT, "include", "fpm.h")).read()
-    declared = set(re.findall(r"\b(fpm_[a-z_]+)\s*\(", hdr))
+    declared = set(re.findall(r"\b(fpm_[a-z0-9_]+)\s*\(", hdr))
     assert declared, "no declarations parsed"
     assert declared == set(fpm.EXPORTS)
     for name in declared:

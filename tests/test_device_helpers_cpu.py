@@ -47,6 +47,29 @@ def test_fft_passes_match_numpy(emulated):
         assert err < 2e-6, (M, d, err)
 
 
+def test_pruned_256_point_transforms_match_numpy(emulated):
+    """The dataflow kernel's 256-point transforms with the pruned radix-16 passes: the
+    box map of the first-pass points, an inverse transform of box-supported inputs
+    (pruned first pass) and a forward transform kept on the box (pruned last pass)."""
+    assert "boxmap_bad" not in emulated
+    assert {int(v[0]): int(v[1]) for v in emulated["boxmap"]} == {53: 107, 63: 127, 72: 145}
+    h = 53
+    t = np.arange(256)
+    ky = np.where(t <= 128, t, t - 256)
+    box = np.abs(ky) <= h
+    x = np.where(box, np.sin(0.41 * t + 0.3).astype(np.float32)
+                 + 1j * (np.cos(0.77 * t).astype(np.float32) - np.float32(0.2)), 0)
+    got = np.array(emulated["box256inv"][0], float).view(complex)
+    ref = np.fft.ifft(x) * 256
+    assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 2e-6
+    x = np.cos(0.23 * t + 1.1).astype(np.float32) + 1j * (np.sin(0.59 * t).astype(np.float32) + np.float32(0.1))
+    got = np.array(emulated["box256fwd"][0], float).view(complex)
+    ref = np.fft.fft(x)
+    err = np.linalg.norm((got - ref)[box]) / np.linalg.norm(ref[box])
+    assert err < 2e-6
+    assert np.all(got[64:192] == 0)   # the pruned outputs (second-pass rows 4..11) are left at zero
+
+
 def test_zernike_table_matches_oracle(emulated):
     for vals in emulated["zern"]:
         v = np.array(vals, float)

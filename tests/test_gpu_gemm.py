@@ -28,8 +28,9 @@ from tests.gpu_common import engine_for, multiparam_problem, push, record, rel_l
 pytestmark = pytest.mark.gpu
 
 MODES = ("bf16", "bf16x3", "tf32", "tf32x3")
-TOL_I = {"bf16": 2e-2, "bf16x3": 2e-4, "tf32": 5e-3, "tf32x3": 1e-5}
-TOL_G = {"bf16": 5e-2, "bf16x3": 2e-3, "tf32": 1e-2, "tf32x3": 1e-4}
+# the split forms are held to the FP32 path's tolerances (1e-5 / 1e-4)
+TOL_I = {"bf16": 2e-2, "bf16x3": 1e-5, "tf32": 5e-3, "tf32x3": 1e-5}
+TOL_G = {"bf16": 5e-2, "bf16x3": 1e-4, "tf32": 1e-2, "tf32x3": 1e-4}
 TOL_O = {"bf16": 0.5, "bf16x3": 2e-2, "tf32": 0.2, "tf32x3": 1e-3}
 
 

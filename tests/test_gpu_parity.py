@@ -381,6 +381,43 @@ def test_c2_batch_gradients_and_steps(c2_problem):
     assert eo <= 1e-4
 
 
+@pytest.mark.slow
+def test_c2_epoch_all_learned(c2_problem):
+    """One pass (14 full batches of 16 and the last LED) of the 1024^2 / 256^2 / 225-LED workload with
+    every parameter learned, against the oracle on the same schedule. The scalars
+    start off the paper's symmetric initial point (zero offsets and aberrations,
+    real object), where the centre LED's offset gradient vanishes and Adam would
+    turn FP32 rounding into a full step."""
+    c, I, o, g_n, g_t, prm_t = c2_problem
+    hp = orc.Hparams(lr=dict(c.lr), learn=c.learn)
+    rng = np.random.default_rng(3)
+    prm0 = orc.Params.initial(g_n)
+    prm0.zernike = rng.normal(0, 0.05, 14)
+    prm0.defocus = 1.0
+    prm0.offset = rng.uniform(-0.3, 0.3, prm0.offset.shape)
+    rec = orc.Reconstruction(g_n, I, hp, prm=prm0)
+    eng = engine_for(g_n)
+    hparams_to_engine(eng, hp)
+    eng.load(I, init=True)
+    eng.set(zernike=prm0.zernike, defocus=prm0.defocus, offset=prm0.offset)
+    perm = S.epoch_permutation(c.n_leds, c.seed, 0)
+    nfull = c.n_leds // c.B                       # 14 full batches of 16, then one of 1
+    sched = perm[:nfull * c.B].reshape(nfull, c.B)
+    ref = rec.run(list(sched) + [perm[nfull * c.B:]])
+    got = list(eng.run(sched)) + [eng.step(perm[nfull * c.B:])]
+    record("c2.epoch.losses", rel_l2(got, ref))
+    assert rel_l2(got, ref) <= 1e-5
+    st = eng.get()
+    eo = rel_l2(st["object"], rec.O)
+    record("c2.epoch.object", eo)
+    assert eo <= TOL_O
+    for name, r in (("zernike", rec.prm.zernike), ("gamma", rec.prm.gamma), ("offset", rec.prm.offset)):
+        e = rel_l2(st[name], r)
+        record(f"c2.epoch.{name}", e)
+        assert e <= TOL_O, (name, e)
+    assert abs(st["defocus"] - rec.prm.defocus) <= TOL_O * abs(rec.prm.defocus)
+
+
 # --------------------------------------------------------------------------
 # edge cases and errors
 # --------------------------------------------------------------------------

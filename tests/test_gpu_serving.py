@@ -4,9 +4,11 @@ direct engine run, and admission by device-memory footprint."""
 import numpy as np
 import pytest
 
+import oracle as orc
 from paper_2408_13782_gb300 import Engine
 from paper_2408_13782_gb300 import serve as sv
 from synth import recipes as S
+from tests.helpers import rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -61,6 +63,25 @@ def test_served_job_equals_a_direct_run():
         if c.n_leds % c.B:
             eng.step(perm[nfull * c.B:])
     assert np.array_equal(eng.get()["object"], res[0]["object"])
+
+
+def test_served_job_equals_the_oracle():
+    """A served job against the FP64 oracle's reconstruction on the same schedule:
+    each epoch a fresh permutation (Eq. 13-14), its full batches, then the short one."""
+    c, desc, stack = _job(256, 7, 13, max_epochs=2)
+    st, res = _serve([((c, desc, stack), 0.0)])
+    assert st[0]["state"] == sv.JOB_DONE and st[0]["epochs"] == 2
+    nominal = S.led_grid(c.grid, c.pitch, c.jitter, c.seed)[0]
+    g = orc.Geometry(c.N, c.m, nominal, c.R, c.edge, c.lambda_um, c.dk_per_um)
+    rec = orc.Reconstruction(g, stack, orc.Hparams(lr=dict(object=0.5), learn=("object",)))
+    losses = []
+    for e in range(2):
+        perm = S.epoch_permutation(c.n_leds, c.seed, e)
+        batches = [perm[k:k + c.B] for k in range(0, c.n_leds, c.B)]
+        losses.append(sum(rec.run(batches)))
+    err = rel_l2(res[0]["object"], rec.O)
+    assert err <= 1e-3, err
+    assert abs(st[0]["loss"] - losses[-1]) <= 1e-5 * losses[-1]
 
 
 def test_admission_waits_for_memory():

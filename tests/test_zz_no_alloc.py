@@ -1,4 +1,4 @@
-"""The allocation-free gradient call against the handle-based one.
+"""The allocation-free gradient call against the handle-based one and the oracle.
 
 fpm_gradients_static exists for callers that cannot allocate device memory
 (code running while a host framework owns the device memory pool, or real-time
@@ -6,7 +6,9 @@ loops where an allocation may block): every buffer is theirs, and the
 intermediates live in a fixed static array inside the library. It must give
 the same loss and gradients as fpm_backward, the existing entry point, within
 the parity tests' tolerances (1e-5 on the loss, 1e-4 on every gradient), on
-consecutive calls - the second call reuses the array the first one left behind.
+consecutive calls - the second call reuses the array the first one left behind
+- for both losses and both pupil edges, with offsets at the bound; and the
+same as the FP64 oracle. Its optional err_out reports the kernels' error bits.
 This file is collected last so that a failure here stops a run only after all
 other tests have run.
 """
@@ -14,6 +16,7 @@ other tests have run.
 import numpy as np
 import pytest
 
+import oracle as orc
 from paper_2408_13782_gb300 import FpmError
 from paper_2408_13782_gb300 import engine as E
 from tests.gpu_common import engine_for, multiparam_problem, push, rel_l2
@@ -21,6 +24,7 @@ from tests.gpu_common import engine_for, multiparam_problem, push, rel_l2
 pytestmark = pytest.mark.gpu
 
 TOL_LOSS, TOL_G = 1e-5, 1e-4
+BOUND = 1.0  # FPM_OFFSET_BOUND_PX
 
 
 def _device_inputs(torch, O, prm, I):
@@ -29,6 +33,31 @@ def _device_inputs(torch, O, prm, I):
     O_t = torch.from_numpy(np.stack([Ot.real, Ot.imag], -1).astype(np.float32)).to(dev)
     params = np.concatenate([prm.zernike, [prm.defocus], prm.gamma, prm.offset.ravel()]).astype(np.float32)
     return dev, O_t, torch.from_numpy(params).to(dev), torch.from_numpy(np.ascontiguousarray(I, np.float32)).to(dev)
+
+
+def _call(torch, g, dev, O_t, params, stack, batch, loss="amplitude"):
+    n = g.n_leds
+    gO_t = torch.full_like(O_t, float("nan"))
+    gp = torch.full((15 + 3 * n,), float("nan"), dtype=torch.float32, device=dev)
+    L = torch.full((1,), float("nan"), dtype=torch.float64, device=dev)
+    err = torch.full((1,), -1, dtype=torch.int32, device=dev)
+    E.gradients_static(g.m, g.s, g.nominal, g.R, g.lambda_um, g.dk_per_um, g.edge, O_t, params, stack,
+                       batch, gO_t, gp, L, loss=loss, stream=torch.cuda.current_stream().cuda_stream, err_out=err)
+    torch.cuda.synchronize()
+    go = gO_t.cpu().numpy()
+    gpv = gp.cpu().numpy().astype(np.float64)
+    return dict(object=(go[..., 0] + 1j * go[..., 1].astype(np.float64)).T, zernike=gpv[:14],
+                defocus=float(gpv[14]), gamma=gpv[15:15 + n], offset=gpv[15 + n:].reshape(n, 2),
+                loss=float(L.cpu().numpy()[0]), err=int(err.cpu().numpy()[0]))
+
+
+def _assert_close(got, ref):
+    assert abs(got["loss"] - ref["loss"]) <= TOL_LOSS * abs(ref["loss"])
+    assert rel_l2(got["object"], ref["object"]) <= TOL_G
+    assert rel_l2(got["zernike"], ref["zernike"]) <= TOL_G
+    assert rel_l2([got["defocus"]], [ref["defocus"]]) <= TOL_G
+    assert rel_l2(got["gamma"], ref["gamma"]) <= TOL_G
+    assert rel_l2(got["offset"], ref["offset"]) <= TOL_G
 
 
 @pytest.mark.parametrize("m,grid,batches", [
@@ -43,29 +72,46 @@ def test_static_gradients_equal_backward_on_consecutive_calls(m, grid, batches):
     eng.load(I, init=False)
     push(eng, O, prm)
     dev, O_t, params, stack = _device_inputs(torch, O, prm, I)
-    n = g.n_leds
     for batch in batches:
-        ref = eng.backward(batch)
-        gO_t = torch.full_like(O_t, float("nan"))
-        gp = torch.full((15 + 3 * n,), float("nan"), dtype=torch.float32, device=dev)
-        loss = torch.full((1,), float("nan"), dtype=torch.float64, device=dev)
-        E.gradients_static(g.m, g.s, g.nominal, g.R, g.lambda_um, g.dk_per_um, g.edge, O_t, params, stack,
-                           batch, gO_t, gp, loss, stream=torch.cuda.current_stream().cuda_stream)
-        torch.cuda.synchronize()
-        go = gO_t.cpu().numpy()
-        g_obj = (go[..., 0] + 1j * go[..., 1].astype(np.float64)).T
-        gpv = gp.cpu().numpy().astype(np.float64)
-        L = float(loss.cpu().numpy()[0])
-        assert abs(L - ref["loss"]) <= TOL_LOSS * abs(ref["loss"])
-        assert rel_l2(g_obj, ref["object"]) <= TOL_G
-        assert rel_l2(gpv[:14], ref["zernike"]) <= TOL_G
-        assert rel_l2([gpv[14]], [ref["defocus"]]) <= TOL_G
-        assert rel_l2(gpv[15:15 + n], ref["gamma"]) <= TOL_G
-        assert rel_l2(gpv[15 + n:].reshape(n, 2), ref["offset"]) <= TOL_G
+        got = _call(torch, g, dev, O_t, params, stack, batch)
+        assert got["err"] == 0
+        _assert_close(got, eng.backward(batch))
     eng.close()
 
 
-def test_static_gradients_reject_a_batch_larger_than_the_array():
+@pytest.mark.parametrize("loss,edge", [("amplitude", "hard"), ("intensity", "aa"), ("intensity", "hard")])
+def test_static_gradients_losses_edges_and_offsets_at_the_bound(loss, edge):
+    """Both losses and pupil edges, every offset of the batch at +-bound (the widest
+    support the crop box is sized for), against fpm_backward and the oracle."""
+    torch = pytest.importorskip("torch")
+    c, I, g, prm, O = multiparam_problem(m=64, grid=5, edge=edge, seed=73)
+    rng = np.random.default_rng(5)
+    batch = [7, 12, 2, 18, 0]
+    prm.offset[batch] = BOUND * rng.choice([-1.0, 1.0], size=(len(batch), 2))
+    eng = engine_for(g)
+    eng.set_hparams(loss=loss)
+    eng.load(I, init=False)
+    push(eng, O, prm)
+    dev, O_t, params, stack = _device_inputs(torch, O, prm, I)
+    got = _call(torch, g, dev, O_t, params, stack, batch, loss=loss)
+    assert got["err"] == 0
+    _assert_close(got, eng.backward(batch))
+    L, ref, _ = orc.loss_and_grad(O, prm, g, batch, I.astype(np.float64), loss)
+    _assert_close(got, dict(ref, loss=L))
+    eng.close()
+
+
+def test_static_gradients_report_an_offset_beyond_the_bound():
+    torch = pytest.importorskip("torch")
+    c, I, g, prm, O = multiparam_problem(m=64, grid=5, seed=74)
+    prm.offset[3] = [1.5, -0.2]
+    dev, O_t, params, stack = _device_inputs(torch, O, prm, I)
+    assert _call(torch, g, dev, O_t, params, stack, [1, 2])["err"] == 0      # LED 3 not in the batch
+    assert _call(torch, g, dev, O_t, params, stack, [1, 3, 2])["err"] == 8   # FPM_DEVERR_OFFSET
+    assert _call(torch, g, dev, O_t, params, stack, [4])["err"] == 0        # cleared by the next call
+
+
+def test_static_gradients_reject_a_batch_larger_than_the_array_and_capture():
     torch = pytest.importorskip("torch")
     c, I, g, prm, O = multiparam_problem(m=256, grid=15, pitch=12.0, R=50.0, seed=72)
     dev, O_t, params, stack = _device_inputs(torch, O, prm, I)
@@ -76,3 +122,11 @@ def test_static_gradients_reject_a_batch_larger_than_the_array():
         E.gradients_static(g.m, g.s, g.nominal, g.R, g.lambda_um, g.dk_per_um, g.edge, O_t, params, stack,
                            list(range(64)), gO_t, gp, loss)
     assert e.value.code == -2 and "static array holds" in str(e.value)
+    # a call on a stream being captured is refused (its host tables cannot be recorded)
+    s = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with pytest.raises(FpmError) as e:
+        with torch.cuda.graph(graph, stream=s, capture_error_mode="relaxed"):
+            E.gradients_static(g.m, g.s, g.nominal, g.R, g.lambda_um, g.dk_per_um, g.edge, O_t, params, stack,
+                               list(range(8)), gO_t, gp, loss, stream=s.cuda_stream)
+    assert e.value.code == -8
