@@ -20,6 +20,7 @@ from .fpm import (  # noqa: F401
     pupil,
     object_spectrum,
     bilinear_upsample,
+    bilinear_nodes,
     init_object,
     crop,
     forward_fields,

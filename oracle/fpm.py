@@ -35,6 +35,11 @@ Readings where the paper is silent or garbled:
   pixel r on high-res pixel s*r and a periodic boundary, zero phase;
   gamma = 1, aberrations = 0, z = 0, delta = fractional part of the nominal
   LED offsets;
+* free-form pupil (the pupil-recovery reference of Section 2.2): an optional
+  complex field P on the integer nodes of the crop grid (index p + m/2),
+  multiplying the parametric pupil; it is evaluated at q = p - delta_i by
+  bilinear interpolation between the four nodes around q, so that
+  M_i(p) = A(q) exp(i chi(q)) P~(q); P = 1 (or None) is the parametric model;
 * Adam (Kingma & Ba 2015, bias-corrected; or AdamW, NAdam, RMSprop, the other
   members of the Adam family) on every real component of every
   learnable tensor, every step; sub-pixel offsets clamped to +-offset_bound
@@ -170,6 +175,7 @@ class Params:
     defocus: float             # z, um
     gamma: np.ndarray          # [n_leds] intensity factors
     offset: np.ndarray         # [n_leds, 2] sub-pixel LED offsets delta, px
+    pupil_ff: np.ndarray | None = None   # [m, m] complex free-form pupil nodes, or None (all ones)
 
     @staticmethod
     def initial(geom: Geometry) -> "Params":
@@ -178,13 +184,14 @@ class Params:
 
     def copy(self) -> "Params":
         return Params(self.zernike.copy(), float(self.defocus),
-                      self.gamma.copy(), self.offset.copy())
+                      self.gamma.copy(), self.offset.copy(),
+                      None if self.pupil_ff is None else self.pupil_ff.copy())
 
 
 @dataclass
 class Hparams:
     lr: dict = field(default_factory=lambda: dict(
-        object=0.1, zernike=0.01, defocus=0.1, gamma=0.01, offset=0.01))
+        object=0.1, zernike=0.01, defocus=0.1, gamma=0.01, offset=0.01, pupil=0.01))
     beta1: float = 0.9
     beta2: float = 0.999
     eps: float = 1e-8
@@ -234,7 +241,25 @@ def init_object(I_centre: np.ndarray, s: int) -> np.ndarray:
     return object_spectrum(o0.astype(np.complex128), s)
 
 
-def pupil(geom: Geometry, zern, z: float, delta):
+def bilinear_nodes(P: np.ndarray, qy: np.ndarray, qx: np.ndarray):
+    """Bilinear interpolation of node values P[n + m/2] (n on the integer grid,
+    m = P.shape[0]) at points q, with its derivatives along qy and qx.
+    Returns (value, d/dqy, d/dqx, (iy, ix, fy, fx)): the lower-left node index
+    (clipped to the grid) and the fractional parts."""
+    m = P.shape[0]
+    fy0, fx0 = np.floor(qy), np.floor(qx)
+    fy, fx = qy - fy0, qx - fx0
+    iy = np.clip(fy0.astype(np.int64) + m // 2, 0, m - 2)
+    ix = np.clip(fx0.astype(np.int64) + m // 2, 0, m - 2)
+    p00, p01 = P[iy, ix], P[iy, ix + 1]
+    p10, p11 = P[iy + 1, ix], P[iy + 1, ix + 1]
+    val = (1 - fy) * ((1 - fx) * p00 + fx * p01) + fy * ((1 - fx) * p10 + fx * p11)
+    d_qy = (1 - fx) * (p10 - p00) + fx * (p11 - p01)
+    d_qx = (1 - fy) * (p01 - p00) + fy * (p11 - p10)
+    return val, d_qy, d_qx, (iy, ix, fy, fx)
+
+
+def pupil(geom: Geometry, zern, z: float, delta, ff=None):
     """Pupil factor M(p) = A(q) exp(i chi(q)), q = p - delta, on the m x m grid.
 
     p runs over [-m/2, m/2)^2 (centred low-res spectrum index), q in px.
@@ -270,8 +295,13 @@ def pupil(geom: Geometry, zern, z: float, delta):
     dka_y = np.where(inside, -2 * math.pi * dk2 * qy / root, 0.0)
     dka_x = np.where(inside, -2 * math.pi * dk2 * qx / root, 0.0)
     chi = theta + z * kappa
-    return dict(M=A * np.exp(1j * chi), A=A, chi=chi, Z=Z, kappa=kappa,
-                dA=(dAy, dAx), dchi=(dth_y + z * dka_y, dth_x + z * dka_x))
+    M0 = A * np.exp(1j * chi)
+    out = dict(M=M0, M0=M0, A=A, chi=chi, Z=Z, kappa=kappa,
+               dA=(dAy, dAx), dchi=(dth_y + z * dka_y, dth_x + z * dka_x), ff=None)
+    if ff is not None:   # free-form factor P~(q) on top of the parametric pupil
+        Pt, dPy, dPx, nodes = bilinear_nodes(np.asarray(ff, np.complex128), qy, qx)
+        out.update(M=M0 * Pt, Pt=Pt, dP=(dPy, dPx), nodes=nodes, ff=True)
+    return out
 
 
 def crop(O: np.ndarray, geom: Geometry, i: int) -> np.ndarray:
@@ -285,7 +315,7 @@ def crop(O: np.ndarray, geom: Geometry, i: int) -> np.ndarray:
 
 def forward_fields(O, prm: Params, geom: Geometry, i: int):
     """Eq. (3) for one LED: returns (Phi, psi, pupil dict)."""
-    P = pupil(geom, prm.zernike, prm.defocus, prm.offset[i])
+    P = pupil(geom, prm.zernike, prm.defocus, prm.offset[i], prm.pupil_ff)
     Phi = crop(O, geom, i) * P["M"]
     psi = np.fft.ifft2(np.fft.ifftshift(Phi))
     return Phi, psi, P
@@ -305,7 +335,8 @@ def loss_and_grad(O, prm: Params, geom: Geometry, idx, I_meas, loss: str = "ampl
 
     I_meas: measured intensities for every LED, [n_leds, m, m].
     Returns (L, grads, per_led_losses) with grads keys object [N, N] complex,
-    zernike [14], defocus, gamma [n_leds], offset [n_leds, 2].
+    zernike [14], defocus, gamma [n_leds], offset [n_leds, 2], and pupil
+    [m, m] complex (the free-form nodes; None without a free-form pupil).
     """
     m = geom.m
     gO = np.zeros_like(O, dtype=np.complex128)
@@ -313,6 +344,7 @@ def loss_and_grad(O, prm: Params, geom: Geometry, idx, I_meas, loss: str = "ampl
     g_z = 0.0
     g_gamma = np.zeros(geom.n_leds)
     g_off = np.zeros((geom.n_leds, 2))
+    g_pup = None if prm.pupil_ff is None else np.zeros((m, m), np.complex128)
     per_led = []
     for i in idx:
         i = int(i)
@@ -350,10 +382,21 @@ def loss_and_grad(O, prm: Params, geom: Geometry, idx, I_meas, loss: str = "ampl
         t = np.real(np.conj(g_M) * 1j * M)              # dL/dchi per pixel
         g_zern += np.tensordot(P["Z"], t, axes=([1, 2], [0, 1]))
         g_z += float(np.sum(t * P["kappa"]))
-        e = np.real(np.conj(g_M) * np.exp(1j * P["chi"]))  # dL/dA per pixel
+        eP = np.exp(1j * P["chi"]) * (P["Pt"] if P["ff"] else 1.0)
+        e = np.real(np.conj(g_M) * eP)                     # dL/dA per pixel
         for ax in (0, 1):
             g_off[i, ax] -= float(np.sum(t * P["dchi"][ax] + e * P["dA"][ax]))
-    grads = dict(object=gO, zernike=g_zern, defocus=g_z, gamma=g_gamma, offset=g_off)
+        if P["ff"]:
+            # G = dL/dP~ per pixel; P~ moves with q = p - delta, and spreads G
+            # over its four nodes with the bilinear weights
+            G = np.conj(P["M0"]) * g_M
+            for ax in (0, 1):
+                g_off[i, ax] -= float(np.sum(np.real(np.conj(G) * P["dP"][ax])))
+            iy, ix, fy, fx = P["nodes"]
+            for dy, dx, w in ((0, 0, (1 - fy) * (1 - fx)), (0, 1, (1 - fy) * fx),
+                              (1, 0, fy * (1 - fx)), (1, 1, fy * fx)):
+                np.add.at(g_pup, (iy + dy, ix + dx), w * G)
+    grads = dict(object=gO, zernike=g_zern, defocus=g_z, gamma=g_gamma, offset=g_off, pupil=g_pup)
     return float(sum(per_led)), grads, per_led
 
 
@@ -445,6 +488,8 @@ class Reconstruction:
 
     def step(self, idx) -> float:
         hp = self.hp
+        if "pupil" in hp.learn and self.prm.pupil_ff is None:   # a learned free-form pupil starts at 1
+            self.prm.pupil_ff = np.ones((self.geom.m, self.geom.m), np.complex128)
         L, g, _ = loss_and_grad(self.O, self.prm, self.geom, idx, self.I, hp.loss)
         self.t += 1
         t = self.t
@@ -461,6 +506,12 @@ class Reconstruction:
                 w = getattr(self.prm, attr)
                 mm, vv = self._moments(name, w.shape)
                 self._update(w, g[name], mm, vv, hp.lr[name])
+        if "pupil" in hp.learn:
+            w = np.stack([self.prm.pupil_ff.real, self.prm.pupil_ff.imag], axis=-1)
+            gw = np.stack([g["pupil"].real, g["pupil"].imag], axis=-1)
+            mm, vv = self._moments("pupil", w.shape)
+            self._update(w, gw, mm, vv, hp.lr["pupil"])
+            self.prm.pupil_ff = w[..., 0] + 1j * w[..., 1]
         if "defocus" in hp.learn:
             w = np.array([self.prm.defocus])
             mm, vv = self._moments("defocus", (1,))
