@@ -43,7 +43,9 @@ Readings where the paper is silent or garbled:
 * Adam (Kingma & Ba 2015, bias-corrected; or AdamW, NAdam, RMSprop, the other
   members of the Adam family) on every real component of every
   learnable tensor, every step; sub-pixel offsets clamped to +-offset_bound
-  after each update.
+  and intensity factors held at or above gamma_floor (1e-3; the amplitude loss
+  takes sqrt(gamma), which long runs of Adam steps on noisy dark-field images
+  can otherwise drive below zero) after each update.
 
 Parity pins (tests/test_oracle_*.py): brute-force DFT, Parseval, closed forms
 (constant object, cosine grating, global phase), central finite differences
@@ -198,6 +200,7 @@ class Hparams:
     loss: str = "amplitude"    # 'amplitude' | 'intensity' | 'linear'
     learn: tuple = ("object",)
     offset_bound: float = 1.0
+    gamma_floor: float = 1e-3  # intensity factors are held >= this (the amplitude loss takes sqrt(gamma))
     optimizer: str = "adam"    # 'adam' | 'adamw' | 'nadam' | 'rmsprop' (the Adam family of Section 2.2)
     weight_decay: float = 0.0  # AdamW's decoupled decay
     momentum_decay: float = 0.004  # NAdam's momentum schedule
@@ -519,6 +522,8 @@ class Reconstruction:
             self.prm.defocus = float(w[0])
         if "offset" in hp.learn:
             np.clip(self.prm.offset, -hp.offset_bound, hp.offset_bound, out=self.prm.offset)
+        if "gamma" in hp.learn:
+            np.maximum(self.prm.gamma, hp.gamma_floor, out=self.prm.gamma)
         self.epoch_loss += L
         return L
 

@@ -147,3 +147,20 @@ def test_oracle_reconstruction_reduces_loss():
     e0 = sum(losses[:per_epoch])
     e2 = sum(losses[-per_epoch:])
     assert e2 < 0.95 * e0
+
+
+def test_intensity_factors_held_at_the_floor():
+    """A step large enough to push some gamma below zero leaves it at the floor
+    (the amplitude loss takes sqrt(gamma)); the others move as Adam says."""
+    from tests.helpers import generic_params, tiny_geometry
+    g, _, _ = tiny_geometry()
+    prm = generic_params(g, seed=3)
+    prm.gamma[:] = 0.5
+    rng = np.random.default_rng(4)
+    O = rng.normal(size=(g.N, g.N)) + 1j * rng.normal(size=(g.N, g.N))
+    I = orc.forward(O, prm, g, range(g.n_leds)) * 0.2      # measured darker: every gamma gradient > 0
+    hp = orc.Hparams(lr=dict(object=0.0, zernike=0.0, defocus=0.0, gamma=2.0, offset=0.0), learn=("gamma",))
+    rec = orc.Reconstruction(g, I, hp, O0=O, prm=prm)
+    rec.step([0, 1, 2])
+    assert np.all(rec.prm.gamma[[0, 1, 2]] == hp.gamma_floor)      # 0.5 - ~2 < 0: held at the floor
+    assert np.all(rec.prm.gamma[3:] == 0.5)                          # zero gradient, first step: no move

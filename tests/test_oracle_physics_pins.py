@@ -145,6 +145,7 @@ def test_reconstruction_step_matches_torch_autograd_and_optim():
         opt.step()
         with torch.no_grad():
             t["offset"].clamp_(-hp.offset_bound, hp.offset_bound)
+            t["gamma"].clamp_(min=hp.gamma_floor)
         assert float(L.detach()) == pytest.approx(L_ref, rel=1e-11)
     np.testing.assert_allclose(rec.O, t["object"].detach().numpy(), rtol=1e-10, atol=1e-10)
     np.testing.assert_allclose(rec.prm.zernike, t["zernike"].detach().numpy(), rtol=1e-10, atol=1e-12)

@@ -160,6 +160,7 @@ def test_reconstruction_with_free_form_pupil_matches_torch():
         opt.step()
         with torch.no_grad():
             t["offset"].clamp_(-hp.offset_bound, hp.offset_bound)
+            t["gamma"].clamp_(min=hp.gamma_floor)
         assert float(L.detach()) == pytest.approx(L_ref, rel=1e-11)
     np.testing.assert_allclose(rec.prm.pupil_ff, t["pupil"].detach().numpy(), rtol=1e-10, atol=1e-10)
     np.testing.assert_allclose(rec.O, t["object"].detach().numpy(), rtol=1e-10, atol=1e-10)
