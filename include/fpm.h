@@ -30,7 +30,8 @@
  *     Intensity form (Eq. 4): L = sum (gamma_i |psi_i|^2 - I_meas)^2.
  *   - Gradients of real L w.r.t. complex w are dL/dRe w + i dL/dIm w.
  *   - Adam (Kingma & Ba, bias corrected) per real component of every learnable
- *     tensor, every step; delta is clamped to +-FPM_OFFSET_BOUND_PX per axis.
+ *     tensor, every step; delta is clamped to +-FPM_OFFSET_BOUND_PX per axis and
+ *     gamma held at or above FPM_GAMMA_FLOOR after each update.
  *
  * Pointers: any buffer argument may be host memory (pageable or pinned) or
  * device memory of the engine's device; the direction of each copy is taken
@@ -74,7 +75,8 @@ extern "C" {
 #define FPM_LEARN_DEFOCUS  (1u << 2)
 #define FPM_LEARN_GAMMA    (1u << 3)
 #define FPM_LEARN_OFFSET   (1u << 4)
-#define FPM_LEARN_ALL      0x1Fu
+#define FPM_LEARN_PUPIL    (1u << 5)  /* the free-form pupil field (see fpm_set_pupil) */
+#define FPM_LEARN_ALL      0x3Fu
 
 #define FPM_PRECISION_FP32_FFT 0  /* hand-written shared-memory FFTs, FP32 */
 /* The m-point 2-D (inverse) DFTs of the forward model (Section 2.1, Eq. 3) and
@@ -95,6 +97,7 @@ extern "C" {
 
 #define FPM_N_ZERNIKE     14  /* Noll j = 2..15 */
 #define FPM_OFFSET_BOUND_PX 1.0f
+#define FPM_GAMMA_FLOOR     1e-3f  /* learned intensity factors are held >= this (the amplitude loss takes sqrt) */
 
 typedef struct fpm_handle fpm_handle;
 
@@ -136,13 +139,14 @@ typedef struct fpm_hparams {
   int32_t precision;        /* FPM_PRECISION_*: FP32 FFTs (default) or a tensor-core DFT form */
   int32_t optimizer;        /* FPM_OPT_*; default FPM_OPT_ADAM */
   float weight_decay;       /* FPM_OPT_ADAMW's decay rate (>= 0), applied to every learnable group */
+  float lr_pupil;           /* learning rate of the free-form pupil field (FPM_LEARN_PUPIL) */
 } fpm_hparams;
 
 /* Create an engine for N = m * upsample, pupil radius R (spectral px).
  * Requires every crop box (half-width floor(R + 1/2 + sqrt(2) * FPM_OFFSET_BOUND_PX) + 1)
  * to lie inside the N x N spectrum and inside the m x m window.
  * cuda_stream: a cudaStream_t (e.g. torch.cuda.current_stream().cuda_stream); NULL = default.
- * Default hyper-parameters: lr 0.1 / 0.01 / 0.1 / 0.01 / 0.01, betas 0.9 / 0.999,
+ * Default hyper-parameters: lr 0.1 / 0.01 / 0.1 / 0.01 / 0.01 (pupil field 0.01), betas 0.9 / 0.999,
  * eps 1e-8, amplitude loss, learn object only, Adam, no weight decay. On success *out owns device memory
  * until fpm_destroy. */
 int fpm_create(const fpm_geometry* g, float pupil_radius_px, int32_t upsample,
@@ -256,11 +260,33 @@ int fpm_set(fpm_handle* h, const float* O, const float* zernike, const float* de
 /* O <- fftshift(fft2(o)) / s^2 for a real-space transmission o [N][N][2]. */
 int fpm_set_object_field(fpm_handle* h, const float* o);
 
+/* Free-form pupil (the pupil-recovery reading of Section 2.2, "pupil function"):
+ * a complex field P on the integer nodes n of the crop box (|n_y|, |n_x| <= h,
+ * W = 2h + 1 nodes a side, W from fpm_dims) that multiplies the parametric
+ * pupil. LED i sees it at q = p - delta_i by bilinear interpolation between the
+ * four nodes around q:
+ *     M_i(p) = A(q) exp(i (sum_j c_j Z_j(q/R) + z kappa(q))) * P~(q).
+ * Without a field (the default) M_i is the parametric pupil. fpm_set_pupil
+ * puts P (host or device, [W][W][2], row-major: node (n_y, n_x) at
+ * (n_y + h) * W + n_x + h) into the model; P == NULL takes it out (refused
+ * while FPM_LEARN_PUPIL is set). Setting FPM_LEARN_PUPIL puts the field in
+ * (at its current values; fpm_load with FPM_LOAD_INIT resets it to 1 and its
+ * moments to 0) and the optimiser then updates it every step with lr_pupil.
+ * fpm_get_pupil copies the field out (P nullable; *in_use nullable: whether it
+ * is in the model). fpm_pupil_gradient gives dL/dRe P + i dL/dIm P of the last
+ * fpm_backward or fpm_backward_fields ([W][W][2], same layout; FPM_ERR_STATE
+ * without a field). The field needs the FP32 FFT form (FPM_ERR_ARG otherwise). */
+int fpm_set_pupil(fpm_handle* h, const float* P);
+int fpm_get_pupil(fpm_handle* h, float* P, int32_t* in_use);
+int fpm_pupil_gradient(fpm_handle* h, float* g);
+
 /* Full optimiser state for checkpoint / resume. Sizes in floats: */
 int64_t fpm_state_size(const fpm_handle* h);
 /* Layout: O, m_O, v_O ([N][N][2] each), then params, m_params, v_params
- * ([15 + 3 n_leds] each: zernike, z, gamma, delta), then {step count, epoch loss}
- * stored as two float64 in the last four floats. The layout is the same for every
+ * ([15 + 3 n_leds] each: zernike, z, gamma, delta), then the free-form pupil
+ * field, m_P, v_P ([W][W][2] each, node (n_y, n_x) at (n_x + h) * W + n_y + h),
+ * then {step count, epoch loss, field in the model (0 or 1)} stored as three
+ * float64 in the last six floats. The layout is the same for every
  * optimiser: RMSprop leaves the m arrays at zero, and NAdam's product of momentum
  * coefficients is rebuilt from the step count. */
 int fpm_get_state(fpm_handle* h, float* state);
@@ -268,6 +294,15 @@ int fpm_set_state(fpm_handle* h, const float* state);
 
 /* Sizes of this handle. */
 int fpm_dims(const fpm_handle* h, int32_t* N, int32_t* m, int32_t* n_leds, int32_t* box);
+
+/* Device memory held by the handle (bytes), and a limit on it (bytes; <= 0:
+ * none, the default). A call that would grow the handle's buffers past the
+ * limit (a larger batch, a longer run, a tensor-core form) returns FPM_ERR_OOM
+ * before touching any buffer, and the handle stays usable with what it has;
+ * the limit does not shrink what is already held. fpm_memory_used returns
+ * FPM_ERR_ARG for a NULL handle. */
+int fpm_set_memory_limit(fpm_handle* h, int64_t bytes);
+int64_t fpm_memory_used(const fpm_handle* h);
 
 /* Host-side random batch order (Eq. 13-14): the permutation of range(n) for
  * pass `epoch`: SplitMix64 (Steele, Lea & Flood 2014) seeded with
@@ -391,6 +426,17 @@ typedef struct fpm_job_status {
   int64_t led_updates;       /* LED images processed (forward + backward) */
   int64_t footprint;         /* device bytes reserved while resident */
 } fpm_job_status;
+
+/* Order in which queued jobs are considered for admission (each still needs a
+ * free slot and room in the memory budget; a job that does not fit is passed
+ * over for now): FPM_ADMIT_ARRIVAL (default) in arrival order;
+ * FPM_ADMIT_SMALLEST smallest expected work first (LED images x m^2 x
+ * max_epochs), ties in arrival order - shorter jobs then finish sooner, which
+ * lowers the median time to converge under load at the cost of the larger
+ * jobs' wait. */
+#define FPM_ADMIT_ARRIVAL  0
+#define FPM_ADMIT_SMALLEST 1
+int fpm_server_set_admission(fpm_server* s, int32_t order);
 
 /* Device bytes a job holds while resident (its admission size). */
 int64_t fpm_job_footprint(const fpm_job_desc* d);

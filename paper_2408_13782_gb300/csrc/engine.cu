@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <utility>
 #include <vector>
@@ -93,6 +94,15 @@ struct fpm_handle {
   StepSync* sync = nullptr;    // zero between launches
   int step_ctas = 0;           // CTAs that fit at once (for capB)
   long long wait_ns = 200000000LL;  // bound of the kernels' dependency waits
+  // free-form pupil: node field on the box grid [W][W] (column-major by box
+  // column), its moments, its gradient (fpm_backward), per-LED gradient boxes
+  // and placements; pupil_on: the field takes part in the model
+  float2 *Pff = nullptr, *mPff = nullptr, *vPff = nullptr, *gPff = nullptr, *pbox = nullptr;
+  float4* pwt = nullptr;
+  bool pupil_on = false;
+  // device memory of the handle (every buffer goes through dalloc / dfree)
+  int64_t mem_used = 0, mem_limit = 0;  // limit <= 0: none
+  std::map<void*, size_t> mem_sizes;
 };
 
 namespace {
@@ -106,6 +116,64 @@ int fail(fpm_handle* h, int code, const char* fmt, ...) {
   if (h) h->msg = buf;
   else g_create_error = buf;
   return code;
+}
+
+// Device memory of a handle: each buffer is allocated and freed through these,
+// so the handle knows its footprint and can refuse to grow past its limit
+// (fpm_set_memory_limit) before any buffer is touched.
+size_t mem_of(const fpm_handle* h, const void* p) {
+  const auto it = h->mem_sizes.find(const_cast<void*>(p));
+  return it == h->mem_sizes.end() ? 0 : it->second;
+}
+bool mem_fits(const fpm_handle* h, size_t freed, size_t added) {
+  return h->mem_limit <= 0 || (int64_t)(h->mem_used - (int64_t)freed + (int64_t)added) <= h->mem_limit;
+}
+// Buffers are stream-ordered allocations from the device's memory pool on the
+// handle's stream (cudaMallocAsync / cudaFreeAsync), which unlike cudaFree do
+// not synchronise the whole device: a serving process that admits and retires
+// jobs does not stall the jobs still running. The pool keeps freed memory for
+// reuse (release threshold raised once per device in this process).
+void keep_pool_memory() {
+  static std::mutex mu;
+  static std::vector<int> done;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  for (int d : done)
+    if (d == dev) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  done.push_back(dev);
+}
+
+template <class T>
+cudaError_t dalloc(fpm_handle* h, T** p, size_t bytes) {
+  if (!mem_fits(h, 0, bytes)) return cudaErrorMemoryAllocation;
+  const cudaError_t e = cudaMallocAsync((void**)p, bytes, h->st);
+  if (e == cudaSuccess) {
+    h->mem_used += (int64_t)bytes;
+    h->mem_sizes[(void*)*p] = bytes;
+  }
+  return e;
+}
+template <class T>
+cudaError_t dfree(fpm_handle* h, T*& p) {
+  if (!p) return cudaSuccess;
+  const auto it = h->mem_sizes.find((void*)p);
+  if (it != h->mem_sizes.end()) {
+    h->mem_used -= (int64_t)it->second;
+    h->mem_sizes.erase(it);
+  }
+  const cudaError_t e = cudaFreeAsync((void*)p, h->st);
+  p = nullptr;
+  return e;
 }
 
 #define CK(h, call)                                                                          \
@@ -147,11 +215,9 @@ void destroy_graphs(fpm_handle* h) {
 
 void free_all(fpm_handle* h) {
   destroy_graphs(h);
-  void* dev[] = {h->Ot, h->mO, h->vO, h->tmp, h->tmp2, h->tw_m, h->tw_N, h->meas, h->sp, h->msp, h->vsp,
-                 h->gsc, h->fbuf, h->nint, h->span, h->gbox, h->part, h->sched, h->losses, h->epoch,
-                 h->coef, h->err, h->gconst, h->gscr, h->amp, h->T, h->partB, h->partC, h->sync};
-  for (void* p : dev)
-    if (p) cudaFree(p);
+  for (auto& kv : h->mem_sizes) cudaFreeAsync(kv.first, h->st);  // every device buffer of the handle
+  h->mem_sizes.clear();
+  h->mem_used = 0;
   if (h->h_err) cudaFreeHost(h->h_err);
   if (h->ev_in) cudaEventDestroy(h->ev_in);
   if (h->ev_out) cudaEventDestroy(h->ev_out);
@@ -211,13 +277,18 @@ int validate_batches(fpm_handle* h, const int32_t* idx, int n_steps, int B) {
   return FPM_OK;
 }
 
+int over_limit(fpm_handle* h, size_t freed, size_t added) {
+  return fail(h, FPM_ERR_OOM, "the handle's device-memory limit of %lld bytes would be exceeded (%lld in use, "
+              "%zu more asked for)", (long long)h->mem_limit, (long long)h->mem_used, added - freed);
+}
+
 template <class T>
 int grow(fpm_handle* h, T** p, int* cap, int need) {
   if (*cap >= need) return FPM_OK;
-  if (*p) CK(h, cudaFree(*p));
-  *p = nullptr;
+  if (!mem_fits(h, mem_of(h, *p), sizeof(T) * (size_t)need)) return over_limit(h, mem_of(h, *p), sizeof(T) * (size_t)need);
+  CK(h, dfree(h, *p));
   *cap = 0;
-  CK(h, cudaMalloc((void**)p, sizeof(T) * (size_t)need));
+  CK(h, dalloc(h, p, sizeof(T) * (size_t)need));
   *cap = need;
   destroy_graphs(h);  // graphs hold the old address
   return FPM_OK;
@@ -260,30 +331,41 @@ bool uses_step(const fpm_handle* h) {
 
 int ensure_batch(fpm_handle* h, int B) {
   if (h->hp.precision != FPM_PRECISION_FP32_FFT && h->cap_gscr < B) {
-    if (h->gscr) CK(h, cudaFree(h->gscr));
-    h->gscr = nullptr;
+    const size_t add = h->gp.slot_bytes * (size_t)B;
+    if (!mem_fits(h, mem_of(h, h->gscr), add)) return over_limit(h, mem_of(h, h->gscr), add);
+    CK(h, dfree(h, h->gscr));
     h->cap_gscr = 0;
-    CK(h, cudaMalloc(&h->gscr, h->gp.slot_bytes * (size_t)B));
+    CK(h, dalloc(h, &h->gscr, add));
     h->cap_gscr = B;
     destroy_graphs(h);
   }
   if (h->capB >= B) return FPM_OK;
-  if (h->gbox) CK(h, cudaFree(h->gbox));
-  if (h->part) CK(h, cudaFree(h->part));
-  if (h->T) CK(h, cudaFree(h->T));
-  if (h->partB) CK(h, cudaFree(h->partB));
-  if (h->partC) CK(h, cudaFree(h->partC));
-  h->gbox = nullptr;
-  h->part = nullptr;
-  h->T = nullptr;
-  h->partB = h->partC = nullptr;
+  const size_t sz_box = sizeof(float2) * (size_t)B * h->W * h->W;
+  const size_t sz_part = sizeof(double) * (size_t)B * h->C * NPART;
+  const size_t sz_T = h->sync ? sizeof(float2) * (size_t)B * h->W * 256 : 0;
+  const size_t sz_pB = h->sync ? sizeof(double) * (size_t)B * step_nB() * STEP_NPB : 0;
+  const size_t sz_pC = h->sync ? sizeof(double) * (size_t)B * step_nA(h) * STEP_NPC : 0;
+  const size_t sz_pbox = sz_box, sz_pwt = sizeof(float4) * (size_t)B;
+  const size_t freed = mem_of(h, h->gbox) + mem_of(h, h->part) + mem_of(h, h->T) + mem_of(h, h->partB) +
+                       mem_of(h, h->partC) + mem_of(h, h->pbox) + mem_of(h, h->pwt);
+  const size_t added = sz_box + sz_part + sz_T + sz_pB + sz_pC + sz_pbox + sz_pwt;
+  if (!mem_fits(h, freed, added)) return over_limit(h, freed, added);
+  CK(h, dfree(h, h->gbox));
+  CK(h, dfree(h, h->part));
+  CK(h, dfree(h, h->T));
+  CK(h, dfree(h, h->partB));
+  CK(h, dfree(h, h->partC));
+  CK(h, dfree(h, h->pbox));
+  CK(h, dfree(h, h->pwt));
   h->capB = 0;
-  CK(h, cudaMalloc(&h->gbox, sizeof(float2) * (size_t)B * h->W * h->W));
-  CK(h, cudaMalloc(&h->part, sizeof(double) * (size_t)B * h->C * NPART));
+  CK(h, dalloc(h, &h->gbox, sz_box));
+  CK(h, dalloc(h, &h->part, sz_part));
+  CK(h, dalloc(h, &h->pbox, sz_pbox));
+  CK(h, dalloc(h, &h->pwt, sz_pwt));
   if (h->sync) {  // the dataflow form (m = 256)
-    CK(h, cudaMalloc(&h->T, sizeof(float2) * (size_t)B * h->W * 256));
-    CK(h, cudaMalloc(&h->partB, sizeof(double) * (size_t)B * step_nB() * STEP_NPB));
-    CK(h, cudaMalloc(&h->partC, sizeof(double) * (size_t)B * step_nA(h) * STEP_NPC));
+    CK(h, dalloc(h, &h->T, sz_T));
+    CK(h, dalloc(h, &h->partB, sz_pB));
+    CK(h, dalloc(h, &h->partC, sz_pC));
     CK(h, step_prepare(h->W, B, &h->step_ctas));
   }
   h->capB = B;
@@ -293,10 +375,11 @@ int ensure_batch(fpm_handle* h, int B) {
 
 int ensure_fbuf(fpm_handle* h, size_t floats) {
   if (h->cap_fbuf >= floats) return FPM_OK;
-  if (h->fbuf) CK(h, cudaFree(h->fbuf));
-  h->fbuf = nullptr;
+  if (!mem_fits(h, mem_of(h, h->fbuf), sizeof(float) * floats))
+    return over_limit(h, mem_of(h, h->fbuf), sizeof(float) * floats);
+  CK(h, dfree(h, h->fbuf));
   h->cap_fbuf = 0;
-  CK(h, cudaMalloc(&h->fbuf, sizeof(float) * floats));
+  CK(h, dalloc(h, &h->fbuf, sizeof(float) * floats));
   h->cap_fbuf = floats;
   return FPM_OK;
 }
@@ -333,6 +416,9 @@ LedArgs led_args(fpm_handle* h, const int4* slot_dev, int B, int mode) {
   a.loss = h->hp.loss;
   a.mode = mode;
   a.err = h->err;
+  a.pupil = h->pupil_on ? h->Pff : nullptr;
+  a.pbox = h->pbox;
+  a.pwt = h->pwt;
   return a;
 }
 
@@ -382,6 +468,14 @@ UpdArgs upd_args(fpm_handle* h, const int4* slot_dev, int B, int step_off, doubl
   u.assemble = assemble;
   u.g_obj = h->tmp;
   u.g_sc = h->gsc;
+  u.Pff = h->Pff;
+  u.mPff = h->mPff;
+  u.vPff = h->vPff;
+  u.pbox = h->pbox;
+  u.pwt = h->pwt;
+  u.g_pupil = h->gPff;
+  u.lr_pupil = h->hp.lr_pupil;
+  u.pupil_cols = h->pupil_on ? h->W : 0;
   return u;
 }
 
@@ -422,6 +516,12 @@ int reset_state(fpm_handle* h) {
   CK(h, cudaMemsetAsync(h->msp, 0, sizeof(float) * P, h->st));
   CK(h, cudaMemsetAsync(h->vsp, 0, sizeof(float) * P, h->st));
   CK(h, cudaMemsetAsync(h->epoch, 0, sizeof(double), h->st));
+  const size_t WW = (size_t)h->W * h->W;
+  const std::vector<float2> ones(WW, make_float2(1.f, 0.f));
+  CK(h, cudaMemcpyAsync(h->Pff, ones.data(), sizeof(float2) * WW, cudaMemcpyHostToDevice, h->st));
+  CK(h, cudaMemsetAsync(h->mPff, 0, sizeof(float2) * WW, h->st));
+  CK(h, cudaMemsetAsync(h->vPff, 0, sizeof(float2) * WW, h->st));
+  CK(h, cudaStreamSynchronize(h->st));  // (the host vector above)
   h->t_host = 0;
   return FPM_OK;
 }
@@ -592,6 +692,7 @@ int fpm_create(const fpm_geometry* g, float R, int32_t upsample, void* cuda_stre
   h->hp.lr_defocus = 0.1f;
   h->hp.lr_gamma = 0.01f;
   h->hp.lr_offset = 0.01f;
+  h->hp.lr_pupil = 0.01f;
   h->hp.beta1 = 0.9f;
   h->hp.beta2 = 0.999f;
   h->hp.eps = 1e-8f;
@@ -608,32 +709,39 @@ int fpm_create(const fpm_geometry* g, float R, int32_t upsample, void* cuda_stre
   };
   const size_t NN = (size_t)h->N * h->N;
   const int P = sp_size(h->n);
+  keep_pool_memory();
   bool ok = ck(cudaStreamCreateWithFlags(&h->st, cudaStreamNonBlocking), "stream") &&
             ck(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming), "event") &&
             ck(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming), "event") &&
-            ck(cudaMalloc(&h->Ot, sizeof(float2) * NN), "alloc O") &&
-            ck(cudaMalloc(&h->mO, sizeof(float2) * NN), "alloc m") &&
-            ck(cudaMalloc(&h->vO, sizeof(float2) * NN), "alloc v") &&
-            ck(cudaMalloc(&h->tmp, sizeof(float2) * NN), "alloc tmp") &&
-            ck(cudaMalloc(&h->tmp2, sizeof(float2) * NN), "alloc tmp2") &&
-            ck(cudaMalloc(&h->tw_m, sizeof(float2) * h->m), "alloc tw") &&
-            ck(cudaMalloc(&h->tw_N, sizeof(float2) * h->N), "alloc tw") &&
-            ck(cudaMalloc(&h->meas, sizeof(float) * (size_t)h->n * h->m * h->m), "alloc stack") &&
-            ck(cudaMalloc(&h->amp, sizeof(float) * (size_t)h->n * h->m * h->m), "alloc stack") &&
-            ck(cudaMalloc(&h->sp, sizeof(float) * P), "alloc params") &&
-            ck(cudaMalloc(&h->msp, sizeof(float) * P), "alloc params") &&
-            ck(cudaMalloc(&h->vsp, sizeof(float) * P), "alloc params") &&
-            ck(cudaMalloc(&h->gsc, sizeof(float) * P), "alloc params") &&
-            ck(cudaMalloc(&h->nint, sizeof(int2) * h->n), "alloc leds") &&
-            ck(cudaMalloc(&h->span, sizeof(int2) * h->N), "alloc span") &&
-            ck(cudaMalloc(&h->epoch, sizeof(double)), "alloc") &&
-            ck(cudaMalloc(&h->err, sizeof(int)), "alloc") &&
-            (h->m != 256 || ck(cudaMalloc(&h->sync, sizeof(StepSync)), "alloc")) &&
+            ck(dalloc(h, &h->Ot, sizeof(float2) * NN), "alloc O") &&
+            ck(dalloc(h, &h->mO, sizeof(float2) * NN), "alloc m") &&
+            ck(dalloc(h, &h->vO, sizeof(float2) * NN), "alloc v") &&
+            ck(dalloc(h, &h->tmp, sizeof(float2) * NN), "alloc tmp") &&
+            ck(dalloc(h, &h->tmp2, sizeof(float2) * NN), "alloc tmp2") &&
+            ck(dalloc(h, &h->tw_m, sizeof(float2) * h->m), "alloc tw") &&
+            ck(dalloc(h, &h->tw_N, sizeof(float2) * h->N), "alloc tw") &&
+            ck(dalloc(h, &h->meas, sizeof(float) * (size_t)h->n * h->m * h->m), "alloc stack") &&
+            ck(dalloc(h, &h->amp, sizeof(float) * (size_t)h->n * h->m * h->m), "alloc stack") &&
+            ck(dalloc(h, &h->sp, sizeof(float) * P), "alloc params") &&
+            ck(dalloc(h, &h->msp, sizeof(float) * P), "alloc params") &&
+            ck(dalloc(h, &h->vsp, sizeof(float) * P), "alloc params") &&
+            ck(dalloc(h, &h->gsc, sizeof(float) * P), "alloc params") &&
+            ck(dalloc(h, &h->nint, sizeof(int2) * h->n), "alloc leds") &&
+            ck(dalloc(h, &h->span, sizeof(int2) * h->N), "alloc span") &&
+            ck(dalloc(h, &h->epoch, sizeof(double)), "alloc") &&
+            ck(dalloc(h, &h->err, sizeof(int)), "alloc") &&
+            ck(dalloc(h, &h->Pff, sizeof(float2) * (size_t)h->W * h->W), "alloc pupil") &&
+            ck(dalloc(h, &h->mPff, sizeof(float2) * (size_t)h->W * h->W), "alloc pupil") &&
+            ck(dalloc(h, &h->vPff, sizeof(float2) * (size_t)h->W * h->W), "alloc pupil") &&
+            ck(dalloc(h, &h->gPff, sizeof(float2) * (size_t)h->W * h->W), "alloc pupil") &&
+            (h->m != 256 || ck(dalloc(h, &h->sync, sizeof(StepSync)), "alloc")) &&
             ck(cudaMallocHost(&h->h_err, sizeof(int)), "pinned") &&
             ck((h->C = led_choose_cluster(h->m, h->W)) > 0 ? cudaSuccess : cudaErrorNotSupported,
                "this device cannot run the per-LED kernel for this size") &&
             ck(led_prepare(h->m, h->C, h->W), "kernel attributes") &&
-            ck(update_prepare(), "kernel attributes");
+            ck(update_prepare(), "kernel attributes") &&
+            // the stream-ordered allocations are complete before the copies below
+            ck(cudaStreamSynchronize(h->st), "sync");
   if (ok) {
     const auto twm = twiddles(h->m), twN = twiddles(h->N);
     ok = ck(cudaMemcpy(h->tw_m, twm.data(), sizeof(float2) * h->m, cudaMemcpyHostToDevice), "copy") &&
@@ -668,6 +776,10 @@ int fpm_set_hparams(fpm_handle* h, const fpm_hparams* hp) {
   if (!h || !hp) return fail(h, FPM_ERR_ARG, "null argument");
   if (hp->loss != FPM_LOSS_AMPLITUDE && hp->loss != FPM_LOSS_INTENSITY) return fail(h, FPM_ERR_ARG, "unknown loss");
   if (hp->learn_mask & ~FPM_LEARN_ALL) return fail(h, FPM_ERR_ARG, "unknown learn bits");
+  const bool want_pupil = h->pupil_on || (hp->learn_mask & FPM_LEARN_PUPIL);
+  if (want_pupil && hp->precision != FPM_PRECISION_FP32_FFT)
+    return fail(h, FPM_ERR_ARG, "the free-form pupil needs the FP32 FFT form");
+  if (!std::isfinite(hp->lr_pupil)) return fail(h, FPM_ERR_ARG, "non-finite learning rate");
   if (hp->precision < FPM_PRECISION_FP32_FFT || hp->precision > FPM_PRECISION_TF32X3_GEMM)
     return fail(h, FPM_ERR_ARG, "unknown precision mode");
   if (!(hp->beta1 >= 0.f && hp->beta1 < 1.f && hp->beta2 >= 0.f && hp->beta2 < 1.f && hp->eps > 0.f))
@@ -689,21 +801,25 @@ int fpm_set_hparams(fpm_handle* h, const fpm_hparams* hp) {
     }
     CK(h, cudaStreamSynchronize(h->st));  // kernels in flight may still read the old buffers
     destroy_graphs(h);
-    if (h->gconst) CK(h, cudaFree(h->gconst));
-    if (h->gscr) CK(h, cudaFree(h->gscr));
-    h->gconst = nullptr;
-    h->gscr = nullptr;
+    CK(h, dfree(h, h->gconst));
+    CK(h, dfree(h, h->gscr));
     h->cap_gscr = 0;
     h->gp = gp;
     h->hp.precision = FPM_PRECISION_FP32_FFT;  // until the new form is ready
     if (hp->precision != FPM_PRECISION_FP32_FFT) {
       const std::vector<unsigned char> cst = gemm_constants(gp);
       CK(h, gemm_prepare(gp));
-      CK(h, cudaMalloc(&h->gconst, cst.size()));
-      CK(h, cudaMemcpy(h->gconst, cst.data(), cst.size(), cudaMemcpyHostToDevice));
+      if (!mem_fits(h, 0, cst.size())) return over_limit(h, 0, cst.size());
+      CK(h, dalloc(h, &h->gconst, cst.size()));
+      CK(h, cudaMemcpyAsync(h->gconst, cst.data(), cst.size(), cudaMemcpyHostToDevice, h->st));
+      CK(h, cudaStreamSynchronize(h->st));
     }
   }
   h->hp = *hp;
+  if ((hp->learn_mask & FPM_LEARN_PUPIL) && !h->pupil_on) {
+    h->pupil_on = true;  // a learned field enters the model (it starts at 1 after fpm_load's reset)
+    destroy_graphs(h);
+  }
   if (graph_relevant) destroy_graphs(h);  // the captured kernels hold the hyper-parameters by value
   return FPM_OK;
 }
@@ -722,6 +838,14 @@ int fpm_dims(const fpm_handle* h, int32_t* N, int32_t* m, int32_t* n_leds, int32
   if (box) *box = h->W;
   return FPM_OK;
 }
+
+int fpm_set_memory_limit(fpm_handle* h, int64_t bytes) {
+  if (!h) return FPM_ERR_ARG;
+  h->mem_limit = bytes > 0 ? bytes : 0;
+  return FPM_OK;
+}
+
+int64_t fpm_memory_used(const fpm_handle* h) { return h ? h->mem_used : FPM_ERR_ARG; }
 
 int fpm_load(fpm_handle* h, const float* stack, int32_t flags) {
   if (!h || !stack) return fail(h, FPM_ERR_ARG, "null argument");
@@ -1091,9 +1215,70 @@ int fpm_set_object_field(fpm_handle* h, const float* o) {
   return leave(h);
 }
 
+int fpm_set_pupil(fpm_handle* h, const float* P) {
+  if (!h) return FPM_ERR_ARG;
+  const int W = h->W;
+  const size_t WW = (size_t)W * W;
+  if (!P) {  // back to the parametric pupil
+    if (h->hp.learn_mask & FPM_LEARN_PUPIL)
+      return fail(h, FPM_ERR_STATE, "the free-form pupil is learned (clear FPM_LEARN_PUPIL first)");
+    if (h->pupil_on) {
+      CK(h, cudaStreamSynchronize(h->st));
+      destroy_graphs(h);
+    }
+    h->pupil_on = false;
+    return FPM_OK;
+  }
+  if (h->hp.precision != FPM_PRECISION_FP32_FFT)
+    return fail(h, FPM_ERR_ARG, "the free-form pupil needs the FP32 FFT form");
+  std::vector<float2> hostP(WW), col(WW);
+  int rc = enter(h);
+  if (rc) return rc;
+  CK(h, cudaMemcpyAsync(hostP.data(), P, sizeof(float2) * WW, cudaMemcpyDefault, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  for (int ny = 0; ny < W; ++ny)  // row-major [ny][nx] -> column-major by node column
+    for (int nx = 0; nx < W; ++nx) col[(size_t)nx * W + ny] = hostP[(size_t)ny * W + nx];
+  CK(h, cudaMemcpyAsync(h->Pff, col.data(), sizeof(float2) * WW, cudaMemcpyHostToDevice, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  if (!h->pupil_on) destroy_graphs(h);
+  h->pupil_on = true;
+  return leave(h);
+}
+
+namespace {
+// Copy a node field ([W][W], column-major by node column) into P (row-major [ny][nx]).
+int pupil_field_out(fpm_handle* h, const float2* src, float* P) {
+  const int W = h->W;
+  const size_t WW = (size_t)W * W;
+  std::vector<float2> col(WW), row(WW);
+  int rc = enter(h);
+  if (rc) return rc;
+  CK(h, cudaMemcpyAsync(col.data(), src, sizeof(float2) * WW, cudaMemcpyDeviceToHost, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  for (int ny = 0; ny < W; ++ny)
+    for (int nx = 0; nx < W; ++nx) row[(size_t)ny * W + nx] = col[(size_t)nx * W + ny];
+  CK(h, cudaMemcpyAsync(P, row.data(), sizeof(float2) * WW, cudaMemcpyDefault, h->st));
+  CK(h, cudaStreamSynchronize(h->st));
+  return leave(h);
+}
+}  // namespace
+
+int fpm_get_pupil(fpm_handle* h, float* P, int32_t* in_use) {
+  if (!h) return FPM_ERR_ARG;
+  if (in_use) *in_use = h->pupil_on ? 1 : 0;
+  if (!P) return FPM_OK;
+  return pupil_field_out(h, h->Pff, P);
+}
+
+int fpm_pupil_gradient(fpm_handle* h, float* g) {
+  if (!h || !g) return fail(h, FPM_ERR_ARG, "null argument");
+  if (!h->pupil_on) return fail(h, FPM_ERR_STATE, "no free-form pupil in the model");
+  return pupil_field_out(h, h->gPff, g);
+}
+
 int64_t fpm_state_size(const fpm_handle* h) {
   if (!h) return FPM_ERR_ARG;
-  return (int64_t)6 * h->N * h->N + 3LL * sp_size(h->n) + 4;
+  return (int64_t)6 * h->N * h->N + 3LL * sp_size(h->n) + 6LL * h->W * h->W + 6;
 }
 
 int fpm_get_state(fpm_handle* h, float* state) {
@@ -1112,11 +1297,17 @@ int fpm_get_state(fpm_handle* h, float* state) {
   float* sps[3] = {h->sp, h->msp, h->vsp};
   for (int q = 0; q < 3; ++q)
     if ((rc = copy_out(h, state + 6 * NN + (size_t)P * q, sps[q], sizeof(float) * P, &host))) return rc;
-  double tail[2];
+  const size_t WW = (size_t)h->W * h->W;
+  float* pst = state + 6 * NN + 3 * (size_t)P;
+  float2* pps[3] = {h->Pff, h->mPff, h->vPff};
+  for (int q = 0; q < 3; ++q)
+    if ((rc = copy_out(h, pst + 2 * WW * q, pps[q], sizeof(float2) * WW, &host))) return rc;
+  double tail[3];
   CK(h, cudaMemcpyAsync(&tail[1], h->epoch, sizeof(double), cudaMemcpyDeviceToHost, h->st));
   CK(h, cudaStreamSynchronize(h->st));
   tail[0] = (double)h->t_host;
-  CK(h, cudaMemcpyAsync(state + 6 * NN + 3 * (size_t)P, tail, sizeof tail, cudaMemcpyDefault, h->st));
+  tail[2] = h->pupil_on ? 1.0 : 0.0;
+  CK(h, cudaMemcpyAsync(pst + 6 * WW, tail, sizeof tail, cudaMemcpyDefault, h->st));
   CK(h, cudaStreamSynchronize(h->st));
   return leave(h);
 }
@@ -1136,10 +1327,20 @@ int fpm_set_state(fpm_handle* h, const float* state) {
   float* sps[3] = {h->sp, h->msp, h->vsp};
   for (int q = 0; q < 3; ++q)
     CK(h, cudaMemcpyAsync(sps[q], state + 6 * NN + (size_t)P * q, sizeof(float) * P, cudaMemcpyDefault, h->st));
-  double tail[2];
-  CK(h, cudaMemcpyAsync(tail, state + 6 * NN + 3 * (size_t)P, sizeof tail, cudaMemcpyDefault, h->st));
+  const size_t WW = (size_t)h->W * h->W;
+  const float* pst = state + 6 * NN + 3 * (size_t)P;
+  float2* pps[3] = {h->Pff, h->mPff, h->vPff};
+  for (int q = 0; q < 3; ++q)
+    CK(h, cudaMemcpyAsync(pps[q], pst + 2 * WW * q, sizeof(float2) * WW, cudaMemcpyDefault, h->st));
+  double tail[3];
+  CK(h, cudaMemcpyAsync(tail, pst + 6 * WW, sizeof tail, cudaMemcpyDefault, h->st));
   CK(h, cudaStreamSynchronize(h->st));
-  if (!(tail[0] >= 0.0) || !std::isfinite(tail[1])) return fail(h, FPM_ERR_ARG, "corrupt state tail");
+  if (!(tail[0] >= 0.0) || !std::isfinite(tail[1]) || !(tail[2] == 0.0 || tail[2] == 1.0))
+    return fail(h, FPM_ERR_ARG, "corrupt state tail");
+  if (tail[2] == 1.0 && h->hp.precision != FPM_PRECISION_FP32_FFT)
+    return fail(h, FPM_ERR_ARG, "the state holds a free-form pupil, which needs the FP32 FFT form");
+  if (h->pupil_on != (tail[2] == 1.0)) destroy_graphs(h);
+  h->pupil_on = tail[2] == 1.0;
   h->t_host = (long long)tail[0];
   CK(h, cudaMemcpyAsync(h->epoch, &tail[1], sizeof(double), cudaMemcpyHostToDevice, h->st));
   CK(h, cudaStreamSynchronize(h->st));

@@ -45,6 +45,12 @@ struct LedArgs {
   int hard_edge, loss, mode;
   int meas_is_amp;      // meas holds sqrt(max(I, 0)) (amplitude loss in MODE_LOSS)
   int* err;
+  // free-form pupil (nullable: none): node field [W][W], column-major like the
+  // boxes (node (ny, nx) at (nx + h) * W + ny + h); per-LED gradient boxes
+  // [B][W][W] and per-slot bilinear placement (fy, fx, ay, ax) for the update
+  const float2* pupil;
+  float2* pbox;
+  float4* pwt;
 };
 
 struct UpdArgs {
@@ -77,6 +83,17 @@ struct UpdArgs {
   int assemble;             // 1: write gradients (g_obj, g_sc) instead of updating
   float2* g_obj;            // [N][N] column-major, zeroed by the caller
   float* g_sc;              // [15 + 3 n_leds]
+  // free-form pupil (pupil_cols = 0: none): the node field, its moments, the
+  // per-LED gradient boxes and placements of the LED kernel, its gradient
+  // (assembling); learned under FPM_LEARN_PUPIL with rate lr_pupil
+  float2* Pff;
+  float2* mPff;
+  float2* vPff;
+  const float2* pbox;
+  const float4* pwt;
+  float2* g_pupil;
+  float lr_pupil;
+  int pupil_cols;
 };
 
 // ---- dataflow form of the step (step.cu), m = 256 ------------------------

@@ -178,6 +178,8 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
   if (tid == 0 && rank == 0 && !(fabsf(dly) <= FPM_OFFSET_BOUND_PX && fabsf(dlx) <= FPM_OFFSET_BOUND_PX))
     atomicOr(a.err, DERR_OFFSET);
   const PupilConst P{a.R, a.Rinv, a.inv_lambda, a.dk2, a.hard_edge};
+  const FreeForm ff = free_form(a.pupil, W, dly, dlx);  // (ff.P == nullptr: none)
+  if (a.pupil && a.pwt && tid == 0 && rank == 0) a.pwt[k] = make_float4(ff.fy, ff.fx, (float)ff.ay, (float)ff.ax);
   const int grp = tid / G, j = tid % G;
   float2* buf = fb + grp * FS;
   if (tid < 14) red[tid] = zc;   // the aberration coefficients, via the (still unused) reduction area
@@ -212,7 +214,10 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
       float rad;
       const float A = act ? pupil_amp_r2(r2, P, rad) : 0.f;
       float2 v = make_float2(0.f, 0.f);
-      if (A > 0.f) v = cmul(Oc[ky], pupil_col(qy, r2, A, P, cp, zdef));
+      if (A > 0.f) {
+        v = cmul(Oc[ky], pupil_col(qy, r2, A, P, cp, zdef));
+        if (ff.P) v = cmul(v, ff_value(ff, r, c));
+      }
       buf[bidx<M>(ky & (M - 1))] = v;
     }
     __syncwarp();
@@ -352,6 +357,7 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
   BoxAcc bacc;
   box_acc_zero(bacc);
   float2* gb = a.gbox + (size_t)k * W * W;
+  float2* pb = a.pupil ? a.pbox + (size_t)k * W * W : nullptr;
   for (int cb = c0; cb < c1; cb += NG) {
     const int c = cb + grp;
     const bool act = c < c1;
@@ -376,11 +382,12 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
         const float qy = (float)ky - dly, r2 = fmaf(qy, qy, qx2);
         float rad;
         const float A = pupil_amp_r2(r2, P, rad);
-        float2 out = make_float2(0.f, 0.f);
+        float2 out = make_float2(0.f, 0.f), Gp = out;
         if (A > 0.f)
           out = box_pixel_col(qy, qx, r2, A, rad, cscale(buf[bidx<M>(ky & (M - 1))], inv_m2), Oc[ky], P, cp, zdef, S,
-                              bacc);
+                              bacc, ff, r, c, &Gp);
         gb[(size_t)c * W + r] = out;
+        if (pb) pb[(size_t)c * W + r] = Gp;
       }
       col_fold(cp, S, bacc);
     }
@@ -498,7 +505,10 @@ static cudaError_t prepare_t(int W) {
     // the largest shared-memory carveout, so the SM configuration does not flip between kernels
     e = cudaFuncSetAttribute(fns[f], cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    const int dyn = f == 0 ? optin : optin - (int)sizeof(LedArgs);
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, fns[f]);
+    if (e != cudaSuccess) return e;
+    const int dyn = optin - (int)fa.sharedSizeBytes;  // room left beside the static shared memory
     e = cudaFuncSetAttribute(fns[f], cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return e;
   }

@@ -78,6 +78,48 @@ __device__ __forceinline__ float2 pupil_col(float qy, float r2, float A, const P
   return make_float2(A * cs, A * sn);
 }
 
+// ---- free-form pupil factor ------------------------------------------------
+// The node field P (box grid, column-major by box column, W x W) evaluated at
+// q = p - delta by bilinear interpolation. For one LED q - floor(q) is the
+// same at every pixel: f = -delta - floor(-delta), and the lower-left node of
+// box pixel (row r, column c) is (r + ay, c + ax) with a = floor(-delta).
+struct FreeForm {
+  const float2* P;  // nullptr: no free-form factor
+  int W, ay, ax;
+  float fy, fx;
+};
+
+__device__ __forceinline__ FreeForm free_form(const float2* P, int W, float dly, float dlx) {
+  FreeForm f;
+  f.P = P;
+  f.W = W;
+  const float by = floorf(-dly), bx = floorf(-dlx);
+  f.ay = (int)by;
+  f.ax = (int)bx;
+  f.fy = -dly - by;
+  f.fx = -dlx - bx;
+  return f;
+}
+
+// P~ at box pixel (r, c) of a support pixel, and (with d) its derivatives
+// along qy and qx. The node indices are clamped to the field (a support pixel
+// never needs the clamp).
+__device__ __forceinline__ float2 ff_value(const FreeForm& f, int r, int c, float2* dqy = nullptr,
+                                           float2* dqx = nullptr) {
+  const int rn = min(max(r + f.ay, 0), f.W - 2), cn = min(max(c + f.ax, 0), f.W - 2);
+  const float2* p = f.P + (size_t)cn * f.W + rn;
+  const float2 p00 = __ldg(p), p10 = __ldg(p + 1), p01 = __ldg(p + f.W), p11 = __ldg(p + f.W + 1);
+  const float gy = 1.f - f.fy, gx = 1.f - f.fx;
+  const float2 a0 = make_float2(fmaf(gx, p00.x, f.fx * p01.x), fmaf(gx, p00.y, f.fx * p01.y));  // row rn
+  const float2 a1 = make_float2(fmaf(gx, p10.x, f.fx * p11.x), fmaf(gx, p10.y, f.fx * p11.y));  // row rn + 1
+  if (dqy) *dqy = csub(a1, a0);
+  if (dqx) {
+    const float2 b0 = csub(p01, p00), b1 = csub(p11, p10);
+    *dqx = make_float2(fmaf(gy, b0.x, f.fy * b1.x), fmaf(gy, b0.y, f.fy * b1.y));
+  }
+  return make_float2(fmaf(gy, a0.x, f.fy * a1.x), fmaf(gy, a0.y, f.fy * a1.y));
+}
+
 // One pixel of an LED's support box at q = (qy, qx) = p - delta (A > 0, r2 =
 // |q|^2, rad = |q| for the anti-aliased edge) with the spectrum gradient gphi
 // and the object value o there: returns the object gradient conj(M) gphi and
@@ -85,9 +127,16 @@ __device__ __forceinline__ float2 pupil_col(float qy, float r2, float A, const P
 // from the column's polynomials (ColPoly); the monomial moments sum t x^a y^b
 // are kept as the column sums S[b] = sum t y^b and folded into acc.m by
 // col_fold once per column.
+//
+// With a free-form factor (ff.P != nullptr; r, c: the pixel's box row and
+// column) the pupil is M = A e^{i chi} P~(q): the object gradient and the
+// chi and A terms use it, *G receives dL/dP~ = conj(A e^{i chi}) conj(O) gPhi
+// (the pixel's entry of the pupil-gradient box), and the offsets gain
+// -Re(conj(G) dP~/dq).
 __device__ __forceinline__ float2 box_pixel_col(float qy, float qx, float r2, float A, float rad, float2 gphi, float2 o,
                                                 const PupilConst& P, const ColPoly& cp, float zdef, float (&S)[5],
-                                                BoxAcc& acc) {
+                                                BoxAcc& acc, const FreeForm& ff = FreeForm{nullptr, 0, 0, 0, 0.f, 0.f},
+                                                int r = 0, int c = 0, float2* G = nullptr) {
   const float y = qy * P.Rinv;
   const float th = col_theta(cp, y);
   float dthx, dthy;
@@ -96,11 +145,19 @@ __device__ __forceinline__ float2 box_pixel_col(float qy, float qx, float r2, fl
   const float kap = defocus_kappa(r2, P, &root);
   float sn, cs;
   sincos_phase(fmaf(zdef, kap, th), &sn, &cs);
-  const float2 e = make_float2(cs, sn);
-  const float2 Mv = cscale(e, A);
+  float2 e = make_float2(cs, sn);
+  float2 Mv = cscale(e, A);
   const float2 gM = cmulc(o, gphi);     // conj(O) gPhi
+  float2 dPy = make_float2(0.f, 0.f), dPx = dPy;
+  if (ff.P) {
+    const float2 M0 = Mv;
+    const float2 Pt = ff_value(ff, r, c, &dPy, &dPx);
+    Mv = cmul(M0, Pt);
+    e = cmul(e, Pt);
+    *G = cmulc(M0, gM);
+  }
   const float tt = -cmulc(gM, Mv).y;    // dL/dchi = Re(conj(gM) i M)
-  const float ee = cmulc(gM, e).x;      // dL/dA   = Re(conj(gM) e^{i chi})
+  const float ee = cmulc(gM, e).x;      // dL/dA   = Re(conj(gM) e^{i chi} P~)
   const float y2 = y * y;
   S[0] += tt;
   S[1] = fmaf(tt, y, S[1]);
@@ -118,6 +175,10 @@ __device__ __forceinline__ float2 box_pixel_col(float qy, float qx, float r2, fl
   }
   acc.dy -= fmaf(tt, dchiy, ee * dAy);
   acc.dx -= fmaf(tt, dchix, ee * dAx);
+  if (ff.P) {                           // P~ moves with q = p - delta
+    acc.dy -= cmulc(*G, dPy).x;
+    acc.dx -= cmulc(*G, dPx).x;
+  }
   return cmulc(Mv, gphi);               // conj(M) gPhi
 }
 

@@ -29,6 +29,7 @@
 #include <cstdio>
 #include <cmath>
 #include <cstring>
+#include <algorithm>
 #include <deque>
 #include <map>
 #include <memory>
@@ -82,6 +83,7 @@ struct Round {
 struct fpm_server {
   int64_t budget = 0, used = 0;
   int max_active = 0;
+  int admission = FPM_ADMIT_ARRIVAL;
   std::deque<Job*> queue;
   std::vector<Job*> active;
   std::map<int64_t, std::unique_ptr<Job>> jobs;
@@ -93,6 +95,12 @@ struct fpm_server {
 };
 
 namespace {
+
+// Expected work of a job: LED images x pixels x epochs at most (the stopping rule may end it sooner).
+double job_work(const Job* j) {
+  const double m = j->desc.geometry.m;
+  return (double)j->desc.geometry.n_leds * m * m * (double)j->desc.max_epochs;
+}
 
 double now(const fpm_server* s) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - s->t0).count();
@@ -420,6 +428,13 @@ void fpm_server_destroy(fpm_server* s) {
 
 const char* fpm_server_error(const fpm_server* s) { return s ? s->msg.c_str() : ""; }
 
+int fpm_server_set_admission(fpm_server* s, int32_t order) {
+  if (!s) return FPM_ERR_ARG;
+  if (order != FPM_ADMIT_ARRIVAL && order != FPM_ADMIT_SMALLEST) return srv_fail(s, FPM_ERR_ARG, "unknown admission order");
+  s->admission = order;
+  return FPM_OK;
+}
+
 double fpm_server_clock(const fpm_server* s) { return s ? now(s) : 0.0; }
 
 int fpm_server_submit(fpm_server* s, const fpm_job_desc* d, const float* stack, int64_t* job_id) {
@@ -480,9 +495,11 @@ int fpm_server_tick(fpm_server* s, int32_t* n_active, int32_t* n_queued) {
   for (Job* j : s->active)
     if (j->state == FPM_JOB_ACTIVE) still.push_back(j);
   s->active.swap(still);
-  // 2. admit queued jobs in arrival order, each one that fits the remaining
-  //    memory (first fit: a job too large for now does not hold back smaller
-  //    ones behind it), while slots allow
+  // 2. admit queued jobs in arrival order (or smallest expected work first),
+  //    each one that fits the remaining memory (first fit: a job too large for
+  //    now does not hold back smaller ones behind it), while slots allow
+  if (s->admission == FPM_ADMIT_SMALLEST)
+    std::stable_sort(s->queue.begin(), s->queue.end(), [](const Job* a, const Job* b) { return job_work(a) < job_work(b); });
   for (auto it = s->queue.begin(); it != s->queue.end() && (int)s->active.size() < s->max_active;) {
     Job* j = *it;
     if (s->used + j->footprint > s->budget) {

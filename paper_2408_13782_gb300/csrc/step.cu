@@ -246,6 +246,8 @@ __device__ void task_A(const StepArgs& s, const Sk& sm, int k, int ta) {
   if (tid == 0 && ta == 0 && !(fabsf(lv.dly) <= FPM_OFFSET_BOUND_PX && fabsf(lv.dlx) <= FPM_OFFSET_BOUND_PX))
     atomicOr(a.err, DERR_OFFSET);  // the box holds the support only within the bound
   const PupilConst P{a.R, a.Rinv, a.inv_lambda, a.dk2, a.hard_edge};
+  const FreeForm ff = free_form(a.pupil, W, lv.dly, lv.dlx);
+  if (a.pupil && a.pwt && tid == 0 && ta == 0) a.pwt[k] = make_float4(ff.fy, ff.fx, (float)ff.ay, (float)ff.ax);
   const float2* Oc = a.Ot + (lv.col0 + (act ? c : 0)) * N + lv.row0;  // index by ky
   const float qx = (float)(c - h) - lv.dlx, qx2 = qx * qx;
   const float rs2 = support_r2(P);
@@ -270,6 +272,7 @@ __device__ void task_A(const StepArgs& s, const Sk& sm, int k, int ta) {
       float rad;
       const float A = pupil_amp_r2(r2, P, rad);
       v[n] = A > 0.f ? cmul(v[n], pupil_col(qy, r2, A, P, cp, lv.zdef)) : make_float2(0.f, 0.f);
+      if (ff.P && A > 0.f) v[n] = cmul(v[n], ff_value(ff, b, c));
     }
   }
   float2* buf = sm.buf + grp * SK_FS;
@@ -459,6 +462,8 @@ __device__ void task_C(const StepArgs& s, const Sk& sm, int k, int tc) {
       box_acc_zero(bacc);
       float S[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
       float2* gb = a.gbox + ((size_t)k * W + c) * W;
+      float2* pb = a.pupil ? a.pbox + ((size_t)k * W + c) * W : nullptr;
+      const FreeForm ff = free_form(a.pupil, W, lv.dly, lv.dlx);
 #pragma unroll
       for (int n = 0; n < 16; ++n) {
         if (!maybe_box<PRUNE>(n)) continue;
@@ -467,10 +472,11 @@ __device__ void task_C(const StepArgs& s, const Sk& sm, int k, int tc) {
         const float qy = (float)(b - h) - lv.dly, r2 = fmaf(qy, qy, qx2);
         float rad;
         const float A = pupil_amp_r2(r2, P, rad);
-        float2 out = make_float2(0.f, 0.f);
+        float2 out = make_float2(0.f, 0.f), Gp = out;
         if (A > 0.f)
-          out = box_pixel_col(qy, qx, r2, A, rad, cscale(v[n], inv_m2), o[n], P, cp, lv.zdef, S, bacc);
+          out = box_pixel_col(qy, qx, r2, A, rad, cscale(v[n], inv_m2), o[n], P, cp, lv.zdef, S, bacc, ff, b, c, &Gp);
         gb[b] = out;
+        if (pb) pb[b] = Gp;
       }
       col_fold(cp, S, bacc);
 #pragma unroll
@@ -755,6 +761,32 @@ __device__ void task_column(const StepArgs& s, const Sk& sm, int xc, float4 bc) 
   }
 }
 
+// One node column of the free-form pupil: the gather of the pupil-gradient
+// boxes and the optimiser (see pupil_node).
+__device__ void task_pupil_column(const StepArgs& s, const Sk& sm, int cn, float4 bc) {
+  const UpdArgs& u = s.U;
+  const int W = u.W;
+  constexpr int PRE = 2;  // W <= 255 nodes: two per thread
+  float2 w[PRE], m[PRE], v[PRE];
+#pragma unroll
+  for (int i = 0; i < PRE; ++i) {
+    const int rn = threadIdx.x + SK_NT * i;
+    w[i] = m[i] = v[i] = make_float2(0.f, 0.f);
+    if (!u.assemble && rn < W) {
+      const size_t o = (size_t)cn * W + rn;
+      w[i] = __ldcg(u.Pff + o);
+      m[i] = __ldcg(u.mPff + o);
+      v[i] = __ldcg(u.vPff + o);
+    }
+  }
+  if (!cta_wait(s, &s.sync->c_all.v, (unsigned)(u.B * s.nC), sm.misc)) return;
+#pragma unroll
+  for (int i = 0; i < PRE; ++i) {
+    const int rn = threadIdx.x + SK_NT * i;
+    if (rn < W) pupil_node(u, cn, rn, w[i], m[i], v[i], bc);
+  }
+}
+
 // ------------------------------------------------------------ kernel -----
 template <bool PRUNE>
 __global__ void __launch_bounds__(SK_NT, 4) step_kernel(const StepArgs s) {
@@ -798,7 +830,8 @@ __global__ void __launch_bounds__(SK_NT, 4) step_kernel(const StepArgs s) {
   const int TDEC = decay ? SK_NDECAY : 0;
   const int TS = s.do_update ? SK_NSC : 0;
   const int TCOL = s.do_update && (u.assemble || (u.learn & 1u)) ? u.n_cols : 0;
-  const int total = TA + TB + TC + TDEC + TS + TCOL;
+  const int TPUP = s.do_update ? u.pupil_cols : 0;
+  const int total = TA + TB + TC + TDEC + TS + TCOL + TPUP;
   const float4 bc = s.do_update && u.coef ? u.coef[u.step_off] : make_float4(1.f, 1.f, 0.f, 0.f);
 
   if (tid == 0) sm.misc[0] = (int)atomicAdd(&s.sync->ticket.v, 1u);
@@ -817,8 +850,10 @@ __global__ void __launch_bounds__(SK_NT, 4) step_kernel(const StepArgs s) {
     } else if ((r -= TDEC) < TS) {
       if (r < 16) task_shared_scalar(s, sm, r, bc);
       else task_led_scalars(s, sm, bc);
+    } else if ((r -= TS) < TCOL) {
+      task_column(s, sm, r, bc);
     } else {
-      task_column(s, sm, r - TS, bc);
+      task_pupil_column(s, sm, r - TCOL, bc);
     }
     // the next ticket, taken once this task is done (a ticket taken earlier
     // would hold a task back behind this one)
@@ -859,7 +894,8 @@ int step_tasks(const StepArgs& s) {
   if (s.do_update) {
     const UpdArgs& u = s.U;
     const bool decay = u.opt == FPM_OPT_ADAMW && u.wd > 0.f && !u.assemble && (u.learn & 1u);
-    t += B * s.nC + (decay ? SK_NDECAY : 0) + SK_NSC + (u.assemble || (u.learn & 1u) ? u.n_cols : 0);
+    t += B * s.nC + (decay ? SK_NDECAY : 0) + SK_NSC + (u.assemble || (u.learn & 1u) ? u.n_cols : 0) +
+         u.pupil_cols;
   }
   return t;
 }

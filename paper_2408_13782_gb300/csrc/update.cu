@@ -189,6 +189,12 @@ __device__ void decay_outside(const UpdArgs& a, int q) {
   }
 }
 
+// AdamW's decay CTAs of a launch (0 or NDECAY).
+__host__ __device__ inline int update_decay_ctas(const UpdArgs& a) {
+  const bool decay = a.opt == FPM_OPT_ADAMW && a.wd > 0.f && !a.assemble && (a.learn & 1u);
+  return decay ? NDECAY : 0;
+}
+
 // CTA bid of the update of the job described by a.
 __device__ __forceinline__ void update_body(const UpdArgs& a, const int bid) {
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
@@ -207,6 +213,20 @@ __device__ __forceinline__ void update_body(const UpdArgs& a, const int bid) {
   if (bid < NSC) {  // the scalar parameters (the longest dependency chain)
     if (bid < 16) shared_scalar(a, bid, bc);
     else led_scalars(a, bc);
+    return;
+  }
+  if (bid >= NSC + a.n_cols + update_decay_ctas(a)) {  // free-form pupil: one CTA per node column
+    const int cn = bid - NSC - a.n_cols - update_decay_ctas(a);
+    float2 w0 = make_float2(0.f, 0.f), m0 = w0, v0 = w0;
+    const int rn = threadIdx.x;  // W <= 255 < UPD_NT: one node per thread
+    if (!a.assemble && rn < a.W) {
+      const size_t o = (size_t)cn * a.W + rn;
+      w0 = __ldcg(a.Pff + o);
+      m0 = __ldcg(a.mPff + o);
+      v0 = __ldcg(a.vPff + o);
+    }
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");  // pupil-gradient boxes of the LED kernel
+    if (rn < a.W) pupil_node(a, cn, rn, w0, m0, v0, bc);
     return;
   }
   if (bid >= NSC + a.n_cols) {  // AdamW only (see update_ctas)
@@ -314,10 +334,7 @@ __global__ void __launch_bounds__(UPD_NT) update_kernel_jobs(const UpdArgs* __re
   update_body(sa, q.y);
 }
 
-int update_ctas(const UpdArgs& a) {
-  const bool decay = a.opt == FPM_OPT_ADAMW && a.wd > 0.f && !a.assemble && (a.learn & 1u);
-  return a.n_cols + NSC + (decay ? NDECAY : 0);
-}
+int update_ctas(const UpdArgs& a) { return a.n_cols + NSC + update_decay_ctas(a) + a.pupil_cols; }
 
 cudaError_t update_prepare() {
   cudaError_t e = cudaFuncSetAttribute(update_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,

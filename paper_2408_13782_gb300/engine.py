@@ -22,7 +22,7 @@ ERRORS = {-1: "FPM_ERR_ARG", -2: "FPM_ERR_SHAPE", -3: "FPM_ERR_RANGE", -4: "FPM_
           -5: "FPM_ERR_NONFINITE", -6: "FPM_ERR_TIMEOUT", -7: "FPM_ERR_CUDA", -8: "FPM_ERR_STATE"}
 EDGE = {"aa": 0, "hard": 1}
 LOSS = {"amplitude": 0, "intensity": 1}
-LEARN = {"object": 1, "zernike": 2, "defocus": 4, "gamma": 8, "offset": 16}
+LEARN = {"object": 1, "zernike": 2, "defocus": 4, "gamma": 8, "offset": 16, "pupil": 32}
 # transform arithmetic: FP32 shared-memory FFTs, or the DFT as tensor-core
 # contractions with BF16 / TF32 operands (x3: hi + lo split, three products)
 PRECISION = {"fp32_fft": 0, "bf16": 1, "bf16x3": 2, "tf32": 3, "tf32x3": 4}
@@ -39,7 +39,9 @@ EXPORTS = ("fpm_create", "fpm_set_hparams", "fpm_get_hparams", "fpm_load", "fpm_
            "fpm_gradients_static", "fpm_job_footprint", "fpm_server_create", "fpm_server_submit",
            "fpm_server_tick", "fpm_server_status", "fpm_server_result", "fpm_server_clock", "fpm_server_stats",
            "fpm_server_error", "fpm_server_destroy", "fpm_destroy", "fpm_last_error",
-           "fpm_set_step_form", "fpm_get_step_form", "fpm_check_wait_timeout", "fpm_probe_fp32_fma")
+           "fpm_set_step_form", "fpm_get_step_form", "fpm_check_wait_timeout", "fpm_probe_fp32_fma",
+           "fpm_set_memory_limit", "fpm_memory_used", "fpm_server_set_admission",
+           "fpm_set_pupil", "fpm_get_pupil", "fpm_pupil_gradient")
 
 
 class FpmError(RuntimeError):
@@ -58,7 +60,7 @@ class Hparams(ctypes.Structure):
                 ("lr_gamma", ctypes.c_float), ("lr_offset", ctypes.c_float), ("beta1", ctypes.c_float),
                 ("beta2", ctypes.c_float), ("eps", ctypes.c_float), ("loss", ctypes.c_int32),
                 ("learn_mask", ctypes.c_uint32), ("precision", ctypes.c_int32), ("optimizer", ctypes.c_int32),
-                ("weight_decay", ctypes.c_float)]
+                ("weight_decay", ctypes.c_float), ("lr_pupil", ctypes.c_float)]
 
 
 _lib = None
@@ -101,6 +103,11 @@ def lib():
         "fpm_get_step_form": ([vp, vp, vp], i32),
         "fpm_check_wait_timeout": ([vp, vp, i32, ctypes.c_double], i32),
         "fpm_probe_fp32_fma": ([i32, i32, vp, vp], i32),
+        "fpm_set_memory_limit": ([vp, ctypes.c_int64], i32),
+        "fpm_set_pupil": ([vp, f32p], i32),
+        "fpm_get_pupil": ([vp, f32p, vp], i32),
+        "fpm_pupil_gradient": ([vp, f32p], i32),
+        "fpm_memory_used": ([vp], ctypes.c_int64),
         "fpm_destroy": ([vp], None),
         "fpm_last_error": ([vp], ctypes.c_char_p),
     }
@@ -216,7 +223,7 @@ class Engine:
     # -- API ---------------------------------------------------------------
     def set_hparams(self, lr=None, betas=(0.9, 0.999), eps=1e-8, loss="amplitude", learn=("object",),
                     precision="fp32_fft", optimizer="adam", weight_decay=0.0):
-        rates = dict(object=0.1, zernike=0.01, defocus=0.1, gamma=0.01, offset=0.01)
+        rates = dict(object=0.1, zernike=0.01, defocus=0.1, gamma=0.01, offset=0.01, pupil=0.01)
         rates.update(lr or {})
         lr = rates
         mask = 0
@@ -224,8 +231,15 @@ class Engine:
             mask |= LEARN[k]
         hp = Hparams(lr["object"], lr["zernike"], lr["defocus"], lr["gamma"], lr["offset"],
                      betas[0], betas[1], eps, LOSS[loss], mask, PRECISION[precision], OPTIMIZER[optimizer],
-                     weight_decay)
+                     weight_decay, lr["pupil"])
         self._check(lib().fpm_set_hparams(self._h, ctypes.byref(hp)))
+
+    def set_memory_limit(self, nbytes: int):
+        """Limit on the handle's device memory (bytes; <= 0: none)."""
+        self._check(lib().fpm_set_memory_limit(self._h, int(nbytes)))
+
+    def memory_used(self) -> int:
+        return int(lib().fpm_memory_used(self._h))
 
     def set_step_form(self, form: str = "auto"):
         """Kernels of a step: 'auto' / 'cluster' (per-LED clusters) or 'dataflow' (m = 256)."""
@@ -339,6 +353,27 @@ class Engine:
         g = None if gamma is None else _f32(gamma)
         o = None if offset is None else _f32(offset)
         self._check(lib().fpm_set(self._h, _ptr(O), _ptr(z), _ptr(d), _ptr(g), _ptr(o)))
+
+    def set_pupil(self, P):
+        """Free-form pupil field ([W, W] complex, node (ny, nx) at [ny + h, nx + h]); None removes it."""
+        if P is None:
+            self._check(lib().fpm_set_pupil(self._h, None))
+            return
+        arr = _f32(np.stack([np.real(P), np.imag(P)], -1)) if np.iscomplexobj(P) else _f32(P)
+        self._check(lib().fpm_set_pupil(self._h, _ptr(arr)))
+
+    def get_pupil(self):
+        """(field [W, W] complex, whether it is in the model)."""
+        out = np.empty((self.box, self.box, 2), np.float32)
+        on = ctypes.c_int32()
+        self._check(lib().fpm_get_pupil(self._h, out.ctypes.data, ctypes.byref(on)))
+        return out[..., 0] + 1j * out[..., 1].astype(np.float64), bool(on.value)
+
+    def pupil_gradient(self):
+        """Gradient of the field from the last backward ([W, W] complex)."""
+        out = np.empty((self.box, self.box, 2), np.float32)
+        self._check(lib().fpm_pupil_gradient(self._h, out.ctypes.data))
+        return out[..., 0] + 1j * out[..., 1].astype(np.float64)
 
     def set_object_field(self, o):
         arr = _f32(np.stack([np.real(o), np.imag(o)], -1))

@@ -44,6 +44,7 @@ def _declare(L):
         "fpm_server_stats": ([vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)],
                              i32),
         "fpm_server_error": ([vp], ctypes.c_char_p),
+        "fpm_server_set_admission": ([vp, i32], i32),
         "fpm_server_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
@@ -58,13 +59,14 @@ def job_desc(m, upsample, led_offset, pupil_radius, lambda_um, dk_per_um, edge="
              optimizer="adam", weight_decay=0.0):
     """A job description; keep the returned tuple alive until it has been submitted."""
     off = np.ascontiguousarray(np.asarray(led_offset, np.float32).reshape(-1, 2))
-    rates = dict(object=0.1, zernike=0.01, defocus=0.1, gamma=0.01, offset=0.01)
+    rates = dict(object=0.1, zernike=0.01, defocus=0.1, gamma=0.01, offset=0.01, pupil=0.01)
     rates.update(lr or {})
     mask = 0
     for k in learn:
         mask |= LEARN[k]
     hp = Hparams(rates["object"], rates["zernike"], rates["defocus"], rates["gamma"], rates["offset"],
-                 0.9, 0.999, 1e-8, LOSS[loss], mask, PRECISION[precision], OPTIMIZER[optimizer], weight_decay)
+                 0.9, 0.999, 1e-8, LOSS[loss], mask, PRECISION[precision], OPTIMIZER[optimizer], weight_decay,
+                 rates["pupil"])
     g = Geometry(m, off.shape[0], off.ctypes.data, lambda_um, dk_per_um, EDGE[edge])
     return JobDesc(g, pupil_radius, upsample, hp, batch, max_epochs, rel_tol, seed & ((1 << 64) - 1)), off
 
@@ -75,8 +77,11 @@ def footprint(desc) -> int:
     return int(L.fpm_job_footprint(ctypes.byref(desc[0])))
 
 
+ADMISSION = {"arrival": 0, "smallest": 1}
+
+
 class Server:
-    def __init__(self, hbm_budget_bytes: int, max_active: int = 64):
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 64, admission: str = "arrival"):
         L = lib()
         _declare(L)
         h = ctypes.c_void_p()
@@ -84,6 +89,7 @@ class Server:
         if rc:
             raise FpmError(rc, "server creation failed")
         self._h = h
+        self._check(L.fpm_server_set_admission(h, ADMISSION[admission]))
 
     def _check(self, rc):
         if rc:

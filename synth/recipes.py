@@ -129,6 +129,21 @@ def config(name: str) -> Config:
             "c4_x4": _c4_x4}[name]()
 
 
+RGB_WAVELENGTHS_UM = (0.470, 0.523, 0.623)   # the three LED colours of Section 3.3
+
+
+def rgb_job_configs(N: int, grid: int, seed: int, wavelengths=RGB_WAVELENGTHS_UM) -> list:
+    """The three colour channels of one field of view (Section 3.3) as serving jobs:
+    the 64-px recipe scaled to high-res side N at 0.532 um, then, per wavelength,
+    the pupil radius and the LED pitch in spectral px scaled by 0.532 / lambda (a
+    fixed numerical aperture and LED geometry on a fixed spectral grid). Same
+    stack shape for every channel; the same sample (object seed)."""
+    base = serving_job_config(N, grid, seed)
+    return [base.with_(name=f"{base.name}_{int(round(lam * 1000))}nm", lambda_um=lam,
+                       R=base.R * 0.532 / lam, pitch=base.pitch * 0.532 / lam)
+            for lam in wavelengths]
+
+
 def serving_job_config(N: int, grid: int, seed: int) -> Config:
     """One serving request: the 64-px recipe scaled to high-res side N."""
     m = N // 4

@@ -7,7 +7,8 @@ import numpy as np
 import pytest
 
 import oracle as orc
-from tests.gpu_common import engine_for, push, record, rel_l2
+from paper_2408_13782_gb300 import FpmError
+from tests.gpu_common import engine_for, multiparam_problem, push, record, rel_l2
 from tests.helpers import generic_params
 
 pytestmark = pytest.mark.gpu
@@ -121,3 +122,47 @@ def test_support_at_the_window_edge():
     out = eng.backward(idx)
     L, ref, _ = orc.loss_and_grad(O, prm, g, idx, meas.astype(np.float64), "amplitude")
     _check_grad("window", out, ref, idx)
+
+
+def test_memory_limit_refuses_growth_and_keeps_the_handle_usable():
+    """Failure injection on the host: a device-memory limit below what a larger
+    batch needs makes that step fail with FPM_ERR_OOM before any buffer is
+    touched; the handle then runs smaller batches, and after the limit is lifted
+    the larger one, with the same results as a handle that never failed."""
+    c, I, g, prm, O = multiparam_problem(m=64, grid=5, seed=81)
+    sched = [[0, 5, 9], [3, 1, 12, 7, 20, 24, 2, 8, 15, 11, 6, 4], [2, 22]]
+    ref = engine_for(g)
+    ref.load(I, init=True)
+    for b in sched:
+        ref.step(b)
+    eng = engine_for(g)
+    eng.load(I, init=True)
+    eng.step(sched[0])
+    used = eng.memory_used()
+    assert used > 0
+    eng.set_memory_limit(used + 1024)          # room for nothing larger than the 3-LED batch buffers
+    with pytest.raises(FpmError) as e:
+        eng.step(sched[1])
+    assert e.value.code == -4 and "limit" in str(e.value)
+    assert eng.memory_used() == used            # nothing was freed or allocated
+    eng.set_memory_limit(0)                     # lifted: the same step now runs
+    eng.step(sched[1])
+    eng.step(sched[2])
+    assert np.array_equal(eng.get_state(), ref.get_state())
+
+
+def test_intensity_factors_held_at_the_floor_like_the_oracle():
+    c, I, g, prm, O = multiparam_problem(m=64, grid=5, seed=83)
+    prm.gamma[:] = 0.5
+    I_dark = (orc.forward(O, prm, g, range(g.n_leds)) * 0.2).astype(np.float32)
+    hp = orc.Hparams(lr=dict(object=0.0, zernike=0.0, defocus=0.0, gamma=2.0, offset=0.0), learn=("gamma",))
+    rec = orc.Reconstruction(g, I_dark, hp, O0=O, prm=prm)
+    rec.step([0, 1, 2])
+    eng = engine_for(g)
+    eng.set_hparams(lr=dict(object=0.0, zernike=0.0, defocus=0.0, gamma=2.0, offset=0.0), learn=("gamma",))
+    eng.load(I_dark, init=False)
+    push(eng, O, prm)
+    eng.step([0, 1, 2])
+    got = eng.get()["gamma"]
+    assert np.all(got[[0, 1, 2]] == np.float32(1e-3))
+    np.testing.assert_allclose(got, rec.prm.gamma, rtol=1e-6)
