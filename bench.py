@@ -303,9 +303,9 @@ def serving_jobs(n_jobs: int, rate_hz: float, seed: int, shape=None):
     return jobs
 
 
-def serving_run(jobs, budget: int, max_active: int):
+def serving_run(jobs, budget: int, max_active: int, admission: str = "arrival"):
     from paper_2408_13782_gb300 import serve as sv
-    srv = sv.Server(budget, max_active)
+    srv = sv.Server(budget, max_active, admission)
     ids, st, wall = sv.run_arrivals(srv, [(d, s, t) for d, s, t, _, _ in jobs])
     stats = srv.stats()
     srv.close()
@@ -313,29 +313,62 @@ def serving_run(jobs, budget: int, max_active: int):
     upd = sum(x["led_updates"] for x in st)
     span = max(x["t_done"] for x in st) - min(x["t_submit"] for x in st)
     return {"p50_ttc_s": float(np.percentile(ttc, 50)), "p99_ttc_s": float(np.percentile(ttc, 99)),
-            "led_updates_per_s": upd / span, "jobs_done": int(sum(x["state"] == sv.JOB_DONE for x in st)),
-            "epochs": [int(x["epochs"]) for x in st], "makespan_s": span, "server": stats}
+            "mean_ttc_s": float(ttc.mean()), "led_updates_per_s": upd / span,
+            "jobs_done": int(sum(x["state"] == sv.JOB_DONE for x in st)),
+            "epochs_median": float(np.median([x["epochs"] for x in st])), "makespan_s": span,
+            "admission": admission, "max_active": max_active, "server": stats}
 
 
-def serving_section(n_jobs=16, rate_hz=40.0, seed=5):
+def rgb_section(budget: int, N=512, grid=11, seed=17):
+    """Section 3.3's colour workflow: three wavelengths of one field of view as three
+    jobs submitted together (co-scheduled) against the three run one after another."""
+    from paper_2408_13782_gb300 import Engine
+    from paper_2408_13782_gb300 import serve as sv
+    from synth import recipes as S
+    jobs = []
+    for c in S.rgb_job_configs(N, grid, seed):
+        nominal, truth = S.led_grid(c.grid, c.pitch, c.jitter, c.seed)
+        eng = Engine(c.m, c.s, truth, c.R, c.lambda_um, c.dk_per_um, c.edge)
+        eng.set_object_field(S.make_object(c.N, c.seed))
+        stack = np.concatenate([eng.forward(np.arange(i, min(i + 64, c.n_leds))) for i in range(0, c.n_leds, 64)])
+        eng.close()
+        desc = sv.job_desc(c.m, c.s, nominal, c.R, c.lambda_um, c.dk_per_um, c.edge, batch=c.B,
+                           max_epochs=c.epochs, rel_tol=1e-4, seed=c.seed, lr=dict(c.lr))
+        jobs.append((desc, stack, 0.0, N, grid))
+    out = {"what": f"three channels (470/523/623 nm) of one {N}^2 field, {grid}x{grid} LEDs, submitted together; "
+                   "time until all three are done", "wavelengths_um": list(S.RGB_WAVELENGTHS_UM)}
+    for name, act in (("co_scheduled", 3), ("serial", 1)):
+        r = serving_run(jobs, budget, max_active=act)
+        out[name] = {"all_done_s": r["makespan_s"], "led_updates_per_s": r["led_updates_per_s"],
+                     "epochs_median": r["epochs_median"]}
+    return out
+
+
+def serving_section(n_jobs=100, rate_hz=40.0, seed=5):
     import torch
     jobs = serving_jobs(n_jobs, rate_hz, seed)
     free, total = torch.cuda.mem_get_info()
     budget = int(0.6 * free)
-    run_serving = serving_run(jobs, budget, max_active=64)
-    run_serial = serving_run(jobs, budget, max_active=1)
-    same = serving_jobs(n_jobs, 1000.0, seed + 1, shape=(512, 11))
+    runs = {"continuous": serving_run(jobs, budget, max_active=64),
+            "continuous_smallest_first": serving_run(jobs, budget, max_active=64, admission="smallest"),
+            "continuous_8_active": serving_run(jobs, budget, max_active=8),
+            "serial": serving_run(jobs, budget, max_active=1)}
+    same = serving_jobs(16, 1000.0, seed + 1, shape=(512, 11))
     same_serving = serving_run(same, budget, max_active=64)
     same_serial = serving_run(same, budget, max_active=1)
+    mix = {}
+    for _, _, _, N, g in jobs:
+        mix[f"{N}^2/{g}x{g}"] = mix.get(f"{N}^2/{g}x{g}", 0) + 1
     return {"what": f"{n_jobs} jobs, Poisson arrivals {rate_hz:g}/s, ROI from {{256,512,1024,2048}}^2 at "
                     "upsample 4, LED grids {7,11,15}^2, stop at relative epoch-loss change < 1e-4 or 40 epochs; "
                     "continuous batching (jobs admitted by device-memory footprint, overlapping, same-shape "
-                    "jobs stepped together in one launch per step) vs the same jobs one at a time (FCFS) on "
+                    "jobs stepped together in one launch per step; admission in arrival order or smallest "
+                    "expected work first; at most 64 or 8 resident) vs the same jobs one at a time (FCFS) on "
                     "the same GPU",
-            "mix": [f"{N}^2/{g}x{g}" for _, _, _, N, g in jobs],
-            "hbm_budget_bytes": budget, "continuous": run_serving, "serial": run_serial,
-            "same_shape": {"what": f"{n_jobs} jobs of 512^2 / 11x11 arriving in a burst (Poisson 1000/s)",
-                           "continuous": same_serving, "serial": same_serial}}
+            "mix_counts": mix, "hbm_budget_bytes": budget, **runs,
+            "same_shape": {"what": "16 jobs of 512^2 / 11x11 arriving in a burst (Poisson 1000/s)",
+                           "continuous": same_serving, "serial": same_serial},
+            "rgb": rgb_section(budget)}
 
 
 # --------------------------------------------------------------------------
