@@ -10,6 +10,7 @@
 // and adjoint, then the batch-ordered gather with Adam).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -341,7 +342,8 @@ int ensure_batch(fpm_handle* h, int B) {
   }
   if (h->capB >= B) return FPM_OK;
   const size_t sz_box = sizeof(float2) * (size_t)B * h->W * h->W;
-  const size_t sz_part = sizeof(double) * (size_t)B * h->C * NPART;
+  // (room for the serving loop's mixed-size launch too, whose split of an LED may be finer)
+  const size_t sz_part = sizeof(double) * (size_t)B * std::max(h->C, led_mixed_cluster(h->m)) * NPART;
   const size_t sz_T = h->sync ? sizeof(float2) * (size_t)B * h->W * 256 : 0;
   const size_t sz_pB = h->sync ? sizeof(double) * (size_t)B * step_nB() * STEP_NPB : 0;
   const size_t sz_pC = h->sync ? sizeof(double) * (size_t)B * step_nA(h) * STEP_NPC : 0;

@@ -12,6 +12,10 @@ namespace fpmk {
 
 // Per-CTA partial sums written by the LED kernel (FP64).
 constexpr int NPART = 19;
+// The mixed-size per-LED launch of the serving loop: clusters of 16 CTAs of
+// 128 threads shared by LEDs of m = 64, 128 and 256 (4, 8 and 16 CTAs each).
+constexpr int LED_MIX_CLUSTER = 16;
+constexpr int LED_MIX_THREADS = 128;
 enum : int { P_LOSS = 0, P_GAMMA = 1, P_ZERN = 2, P_DEFOCUS = 16, P_DY = 17, P_DX = 18 };
 
 // Scalar parameter vector layout: [zernike 14][defocus 1][gamma n][delta n x (dy, dx)].
@@ -154,7 +158,16 @@ int engine_snapshot_loss(fpm_handle* h, double* pinned);
 // per-LED launch takes slot map[q].y of job map[q].x, CTA q of the update
 // launch is CTA map[q].y of job map[q].x's update.
 cudaError_t launch_led_jobs(int m, int C, const LedArgs* jobs, const int2* map, int n_clusters, int W_max,
-                            cudaStream_t s, bool pdl);
+                            cudaStream_t s, bool pdl, bool ff);  // ff: some job holds a free-form pupil field
+// Jobs of several low-res sizes in one launch: map[b] = (job, slot, rank among
+// the LED's CTAs, m) for each of n_ctas CTAs (a multiple of LED_MIX_CLUSTER;
+// job < 0: idle); smem = the largest led_mixed_smem_bytes of the jobs.
+int led_mixed_cluster(int m);  // CTAs per LED in the mixed launch, 0 if m is not offered there
+size_t led_mixed_smem_bytes(int m, int W);
+bool led_mixed_fits(int m, int W);  // the mixed launch can hold an LED of size m and box W
+cudaError_t led_mixed_prepare();
+cudaError_t launch_led_mixed(const LedArgs* jobs, const int4* map, int n_ctas, size_t smem, cudaStream_t s, bool pdl,
+                             bool ff);
 cudaError_t launch_update_jobs(const UpdArgs* jobs, const int2* map, int n_ctas, int B_max, cudaStream_t s,
                                bool pdl);
 int update_ctas(const UpdArgs& a);  // CTAs of one job's update launch

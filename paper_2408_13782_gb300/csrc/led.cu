@@ -11,15 +11,17 @@
 // CTA r of the cluster owns a slice of box columns (phases A and C) and a
 // slice of image rows (phase B). T / U live in the owners' shared memory and
 // are gathered / scattered through distributed shared memory in phase B.
-// The CTA's slice of O (support pixels only) and its rows of the measured
-// image are copied into shared memory with cp.async at the start, so each
-// kernel exposes global-memory latency about once.
+// The CTA's slice of O (a disk holding every support, one contiguous run per
+// box column) and its rows of the measured image are copied into shared memory
+// at the start by bulk copies (the TMA engine) that complete on two mbarriers,
+// so each kernel exposes global-memory latency about once.
 #include <cooperative_groups.h>
 
 #include "../../include/fpm.h"
 #include "device.cuh"
 #include "internal.h"
 #include "pixel.cuh"
+#include "tc.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -40,9 +42,9 @@ template <int M, int C>
 constexpr int led_threads() { return (M == 256 && C == 16) ? 128 : LedCfg<M>::NT; }
 
 
-template <int M, int C>
+template <int M, int C, int NT_ = led_threads<M, C>()>
 struct LedLayout {
-  static constexpr int NT = led_threads<M, C>();
+  static constexpr int NT = NT_;
   static constexpr int G = FftBuf<M>::G;           // threads per transform
   static constexpr int NG = NT / G;                // transform groups per CTA
   static constexpr int ROWS = M / C;               // image rows per CTA
@@ -60,9 +62,9 @@ struct LedLayout {
   static size_t bytes(int W) {
     const int chunk = (W + C - 1) / C;
     return sizeof(float) * (size_t)ROWS * M +
-           sizeof(float2) * ((size_t)chunk * TS + (size_t)NG * FS + M + NTW2 + (size_t)chunk * W +
-                             (PUSH ? (size_t)RS * W + 1 : 0)) +   // + 1: 16-byte alignment of the staging rows
-           sizeof(float) * (NPOLY + 14 * 15 + 2 + (size_t)NW * NACC) + sizeof(double) * 16;
+           sizeof(float2) * ((size_t)chunk * TS + (size_t)NG * FS + M + NTW2 + (size_t)chunk * (W + 1) + 1 +
+                             (PUSH ? (size_t)RS * W + 1 : 0)) +   // + 1s: 16-byte alignment of O and the staging rows
+           sizeof(float) * (NPOLY + 14 * 15 + 2 + (size_t)NW * NACC) + sizeof(double) * 16 + sizeof(uint64_t) * 2;
   }
 };
 
@@ -83,6 +85,10 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Bound of the waits for the prologue's bulk copies (a wait that gives up sets
+// DERR_TIMEOUT; the host reports FPM_ERR_TIMEOUT).
+constexpr unsigned long long LED_WAIT_NS = 200000000ull;
+
 // Programmatic dependent launch: let the next kernel in the stream be
 // scheduled early / wait here until the previous kernel's writes are visible.
 __device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
@@ -99,13 +105,20 @@ __device__ __forceinline__ void transform(float2* buf, const FftTw<(M >= 256) ? 
 
 // The per-LED step for batch slot k of the job described by a (run by every
 // thread of the slot's cluster).
-template <int M, int C>
-__device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
-  using L = LedLayout<M, C>;
+// FF: the free-form pupil field is in the model (a separate instantiation, so
+// the parametric kernels carry none of its registers). NT_: threads per CTA.
+// SUB: the LED's C CTAs are CTAs base .. base + C - 1 of a larger cluster
+// (sub_rank = this CTA's rank among them), which calls its two cluster
+// barriers together with the other LEDs of the cluster.
+template <int M, int C, bool FF, int NT_ = led_threads<M, C>(), bool SUB = false>
+__device__ __forceinline__ void led_body(const LedArgs& a, const int k, const int sub_rank = 0) {
+  using L = LedLayout<M, C, NT_>;
   constexpr int NT = L::NT, G = L::G, NG = L::NG, ROWS = L::ROWS, TS = L::TS, FS = L::FS;
   constexpr int NW = L::NW;
   cg::cluster_group cluster = cg::this_cluster();
-  const int rank = (int)cluster.block_rank();
+  const int crank = (int)cluster.block_rank();
+  const int rank = SUB ? sub_rank : crank;
+  const int base = crank - rank;  // the LED's first CTA in the cluster
   const int W = a.W, h = a.h, N = a.N;
   const int chunk = (W + C - 1) / C;
   const int c0 = rank * chunk, c1 = min(W, c0 + chunk);
@@ -118,20 +131,29 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
   float2* fb = T + (size_t)chunk * TS;                    // [NG][FS] transform buffers
   float2* tws = fb + NG * FS;                             // [M] twiddle table
   float2* tw2 = tws + M;                                  // [15][16] second-pass twiddles (M = 256)
-  float2* Ob = tw2 + L::NTW2;                             // [chunk][W] O on this CTA's box columns
+  // [chunk][WS] O on this CTA's box columns (16-byte aligned for the bulk copies;
+  // the even stride WS and a shift of one element keep each column's run on
+  // 16-byte boundaries in both memories)
+  const int WS = W + 1;
+  float2* Ob = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(tw2 + L::NTW2) + 15) & ~(uintptr_t)15);
   // [W][RS] this CTA's rows of T by box column (push form), 16-byte aligned
-  float2* Rw = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(Ob + (size_t)chunk * W) + 15) & ~(uintptr_t)15);
+  float2* Rw = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(Ob + (size_t)chunk * WS) + 15) & ~(uintptr_t)15);
   float* poly = L::PUSH ? reinterpret_cast<float*>(Rw + (size_t)L::RS * W)      // K[15] Dx[10] Dy[10]
-                        : reinterpret_cast<float*>(Ob + (size_t)chunk * W);
+                        : reinterpret_cast<float*>(Ob + (size_t)chunk * WS);
   float* zmt = poly + L::NPOLY;                           // [14 * 15] Zernike -> monomial table
   float* red = zmt + 14 * 15 + 2;                         // [NW][NACC]
   double* dsum = reinterpret_cast<double*>(red + NW * NACC);  // [16] (8-byte aligned: float counts are even)
+  uint64_t* bar = reinterpret_cast<uint64_t*>(dsum + 16);     // [2] mbarriers: O slice, image rows
 
   const int tid = threadIdx.x;
   const int4 slot = a.slot[k];  // (LED, crop row, crop col): one load gives every address
   const int led = slot.x;
-  if (led < 0 || led >= a.n_leds) {  // the same for every CTA of the cluster: uniform exit
+  if (led < 0 || led >= a.n_leds) {  // the same for every CTA of the LED: uniform exit
     if (tid == 0 && rank == 0) atomicOr(a.err, DERR_INDEX);
+    if constexpr (SUB) {  // the cluster's other LEDs still pass both barriers
+      cluster.sync();
+      cluster.sync();
+    }
     return;
   }
   // constant tables by cp.async (group 0): no stall before the O copies below
@@ -147,25 +169,52 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
   // and row ky of it sits at offset N/2 + n_row + ky
   const size_t col0 = (size_t)(N / 2 + slot.z - h);
   const int row0 = N / 2 + slot.y;
-  {
-    // O on a disk that contains the support for every admissible delta
-    // (|delta| <= sqrt(2) * bound), so the copy does not wait for delta
-    const float rs = (a.hard_edge ? a.R : a.R + 0.5f) + 1.41422f * FPM_OFFSET_BOUND_PX + 1e-3f;
-    const int ncol = c1 > c0 ? c1 - c0 : 0;
-    for (int q = tid; q < ncol * W; q += NT) {
-      const int cl = q / W, r = q - cl * W;
-      const float px = (float)(c0 + cl - h), py = (float)(r - h);
-      if (px * px + py * py <= rs * rs)
-        cp_async8(Ob + q, a.Ot + (col0 + c0 + cl) * N + (row0 - h + r));
-    }
-  }
-  cp_async_commit();  // group 1: O (needed by phase A)
-  // group 2: this CTA's image rows (needed by phase B), arriving during phase A
+  // element (column cl, box row r) of the O slice sits at Ob[cl * WS + sh + r]:
+  // sh is the parity of the box's first spectrum row, so an element has the
+  // same parity (16-byte position) in global and shared memory (N, WS even)
+  const int sh = (row0 - h) & 1;
   const bool fwd_only = a.mode == MODE_FORWARD || a.mode == MODE_FORWARD_STORE;
   const bool stored = a.mode == MODE_UPSTREAM_STORED;  // psi comes from memory: no inverse transforms
   const float* rows_src = a.mode == MODE_LOSS ? a.meas + ((size_t)led * M + y0) * M
                         : (a.mode == MODE_UPSTREAM || stored) ? a.dLdI + ((size_t)k * M + y0) * M : nullptr;
-  if (rows_src)
+  // the image rows go by one bulk copy when the caller's rows are 16-byte
+  // aligned (always for the stack; an upstream dL/dI may be a view), else by cp.async
+  const bool bulk_rows = rows_src && ((reinterpret_cast<uintptr_t>(rows_src) & 15) == 0);
+  if (tid == 0) {
+    // O on a disk that contains the support for every admissible delta
+    // (|delta| <= sqrt(2) * bound), so the copy does not wait for delta: per
+    // box column one run of rows [r0, r1], rounded out to 16-byte boundaries
+    // (an even number of elements). Rows 0 and W - 1 are never in a support
+    // (h exceeds the disk's radius), so the rounding may step back from them.
+    const float rs = (a.hard_edge ? a.R : a.R + 0.5f) + 1.41422f * FPM_OFFSET_BOUND_PX + 1e-3f;
+    const int ncol = c1 > c0 ? c1 - c0 : 0;
+    tc::mbar_init(bar, 1);
+    tc::mbar_init(bar + 1, 1);
+    tc::mbar_fence_init();
+    uint32_t bytes = 0;
+    for (int pass = 0; pass < 2; ++pass) {
+      if (pass == 1) tc::mbar_expect_tx(bar, bytes);  // arrives once: the phase completes with the bytes
+      for (int cl = 0; cl < ncol; ++cl) {
+        const float px = (float)(c0 + cl - h), d2 = rs * rs - px * px;
+        if (d2 < 0.f) continue;
+        const int d = (int)sqrtf(d2) + 1;  // one row of margin against rounding of the disk test
+        int r0 = max(0, h - d), r1 = min(W - 1, h + d);
+        r0 -= (sh + r0) & 1;
+        r1 += (sh + r1 + 1) & 1;
+        if (r0 < 0) r0 += 2;
+        if (r1 > W - 1) r1 -= 2;
+        if (r1 < r0) continue;
+        const uint32_t nb = 8u * (uint32_t)(r1 - r0 + 1);
+        if (pass == 0)
+          bytes += nb;
+        else
+          tc::bulk_g2s(Ob + (size_t)cl * WS + sh + r0, a.Ot + (col0 + c0 + cl) * N + (row0 - h + r0), nb, bar);
+      }
+    }
+    tc::mbar_expect_tx(bar + 1, bulk_rows ? (uint32_t)(sizeof(float) * ROWS * M) : 0u);
+    if (bulk_rows) tc::bulk_g2s(ms, rows_src, (uint32_t)(sizeof(float) * ROWS * M), bar + 1);
+  }
+  if (rows_src && !bulk_rows)  // group 1: this CTA's image rows, arriving during phase A
     for (int q = tid; q < ROWS * M / 4; q += NT) cp_async16(ms + 4 * q, rows_src + 4 * q);
   cp_async_commit();
   float zc = 0.f;
@@ -178,13 +227,13 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
   if (tid == 0 && rank == 0 && !(fabsf(dly) <= FPM_OFFSET_BOUND_PX && fabsf(dlx) <= FPM_OFFSET_BOUND_PX))
     atomicOr(a.err, DERR_OFFSET);
   const PupilConst P{a.R, a.Rinv, a.inv_lambda, a.dk2, a.hard_edge};
-  const FreeForm ff = free_form(a.pupil, W, dly, dlx);  // (ff.P == nullptr: none)
-  if (a.pupil && a.pwt && tid == 0 && rank == 0) a.pwt[k] = make_float4(ff.fy, ff.fx, (float)ff.ay, (float)ff.ax);
+  const FreeForm ff = FF ? free_form(a.pupil, W, dly, dlx) : FreeForm{nullptr, 0, 0, 0, 0.f, 0.f};  // (ff.P == nullptr: none)
+  if (FF && a.pupil && a.pwt && tid == 0 && rank == 0) a.pwt[k] = make_float4(ff.fy, ff.fx, (float)ff.ay, (float)ff.ax);
   const int grp = tid / G, j = tid % G;
   float2* buf = fb + grp * FS;
   if (tid < 14) red[tid] = zc;   // the aberration coefficients, via the (still unused) reduction area
-  cp_async_wait<2>();  // group 0: the constant tables
-  __syncthreads();
+  cp_async_wait<1>();  // group 0: the constant tables
+  __syncthreads();     // (also orders the mbarriers' initialisation before every wait on them)
   if (tid < 35) poly[tid] = theta_poly_entry_tab(red, zmt, tid);  // aberration phase as monomials of q/R
   FftTw<(M >= 256) ? 128 : M> TW;  // radix-8 path: per-thread twiddles in registers
   __syncthreads();                // twiddle table
@@ -195,14 +244,16 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
   } else {
     fft_twiddles<M>(tws, j, TW);
   }
-  cp_async_wait<1>();  // all but the most recent group: the O slice
+  // the O slice (a wait that gives up flags the launch; the kernel runs on, so
+  // the CTA stays resident while the copies could still land)
+  if (!tc::mbar_wait(bar, 0, LED_WAIT_NS) && tid == 0) atomicOr(a.err, DERR_TIMEOUT);
   __syncthreads();     // O slice in shared memory
 
   // ---------------- phase A: column inverse transforms over ky -------------
   for (int cb = c0; cb < (stored ? c0 : c1); cb += NG) {
     const int c = cb + grp;
     const bool act = c < c1;
-    const float2* Oc = Ob + (size_t)(act ? c - c0 : 0) * W + h;   // index by ky
+    const float2* Oc = Ob + (size_t)(act ? c - c0 : 0) * WS + sh + h;   // index by ky
     const float qx = (float)(c - h) - dlx, qx2 = qx * qx;
     ColPoly cp;  // the aberration phase along this column
     col_poly(qx * P.Rinv, poly, cp);
@@ -216,7 +267,7 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
       float2 v = make_float2(0.f, 0.f);
       if (A > 0.f) {
         v = cmul(Oc[ky], pupil_col(qy, r2, A, P, cp, zdef));
-        if (ff.P) v = cmul(v, ff_value(ff, r, c));
+        if (FF && ff.P) v = cmul(v, ff_value(ff, r, c));
       }
       buf[bidx<M>(ky & (M - 1))] = v;
     }
@@ -236,7 +287,7 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
         // rows t, t + 1 of T belong to CTA t / ROWS: one 16-byte remote store per pair
         for (int t = 2 * j; t < M; t += 2 * G) {
           const float2 u0 = buf[bidx<M>(t)], u1 = buf[bidx<M>(t + 1)];
-          float4* dst = reinterpret_cast<float4*>(cluster.map_shared_rank(Rw, t / ROWS) + (size_t)c * L::RS + t % ROWS);
+          float4* dst = reinterpret_cast<float4*>(cluster.map_shared_rank(Rw, base + t / ROWS) + (size_t)c * L::RS + t % ROWS);
           *dst = make_float4(u0.x, u0.y, u1.x, u1.y);
         }
       } else {
@@ -245,7 +296,11 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
     }
     __syncwarp();
   }
-  cp_async_wait<0>();  // image rows
+  if (bulk_rows) {  // image rows
+    if (!tc::mbar_wait(bar + 1, 0, LED_WAIT_NS) && tid == 0) atomicOr(a.err, DERR_TIMEOUT);
+  } else {
+    cp_async_wait<0>();
+  }
   cluster.sync();      // (also a block-wide barrier for the rows)
 
   // ---------------- phase B: rows: psi, residual, adjoint row transform ----
@@ -283,7 +338,7 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
           v[u] = make_float2(0.f, 0.f);
           if (act && c < W) {
             const int own = c / chunk, lc = c - own * chunk;
-            v[u] = cluster.map_shared_rank(T, own)[lc * TS + y];
+            v[u] = cluster.map_shared_rank(T, base + own)[lc * TS + y];
           }
         }
 #pragma unroll
@@ -344,7 +399,7 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
       if (act)
         for (int c = j; c < W; c += G) {
           const int kx = c - h, own = c / chunk, lc = c - own * chunk;
-          float2* Tr = cluster.map_shared_rank(T, own);
+          float2* Tr = cluster.map_shared_rank(T, base + own);
           Tr[lc * TS + y] = buf[bidx<M>(kx & (M - 1))];
         }
       __syncwarp();
@@ -357,7 +412,7 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
   BoxAcc bacc;
   box_acc_zero(bacc);
   float2* gb = a.gbox + (size_t)k * W * W;
-  float2* pb = a.pupil ? a.pbox + (size_t)k * W * W : nullptr;
+  float2* pb = (FF && a.pupil) ? a.pbox + (size_t)k * W * W : nullptr;
   for (int cb = c0; cb < c1; cb += NG) {
     const int c = cb + grp;
     const bool act = c < c1;
@@ -372,7 +427,7 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
       transform<M, -1>(buf, TW, tws, tw2, j);
     }
     if (act) {
-      const float2* Oc = Ob + (size_t)(c - c0) * W + h;
+      const float2* Oc = Ob + (size_t)(c - c0) * WS + sh + h;
       const float qx = (float)(c - h) - dlx, qx2 = qx * qx;
       ColPoly cp;  // the aberration phase along this column
       col_poly(qx * P.Rinv, poly, cp);
@@ -387,7 +442,7 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
           out = box_pixel_col(qy, qx, r2, A, rad, cscale(buf[bidx<M>(ky & (M - 1))], inv_m2), Oc[ky], P, cp, zdef, S,
                               bacc, ff, r, c, &Gp);
         gb[(size_t)c * W + r] = out;
-        if (pb) pb[(size_t)c * W + r] = Gp;
+        if (FF && pb) pb[(size_t)c * W + r] = Gp;
       }
       col_fold(cp, S, bacc);
     }
@@ -400,21 +455,46 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k) {
 }
 
 // One job: cluster k takes batch slot k.
-template <int M, int C>
+template <int M, int C, bool FF>
 __global__ void __launch_bounds__(led_threads<M, C>(), M == 512 ? 1 : 2) led_kernel(const LedArgs a) {
-  led_body<M, C>(a, (int)(blockIdx.x / C));
+  led_body<M, C, FF>(a, (int)(blockIdx.x / C));
 }
 
 // Several jobs in one launch (the serving loop): cluster q takes slot
 // map[q].y of job map[q].x, whose arguments are copied to shared memory.
-template <int M, int C>
+template <int M, int C, bool FF>
 __global__ void __launch_bounds__(led_threads<M, C>(), M == 512 ? 1 : 2)
     led_kernel_jobs(const LedArgs* __restrict__ jobs, const int2* __restrict__ map) {
   __shared__ LedArgs sa;
   const int2 q = map[blockIdx.x / C];
   if (threadIdx.x == 0) sa = jobs[q.x];
   __syncthreads();
-  led_body<M, C>(sa, q.y);
+  led_body<M, C, FF>(sa, q.y);
+}
+
+// Jobs of different low-res sizes in one launch (the serving loop's mixed
+// rounds): clusters of LED_MIX_CLUSTER CTAs of LED_MIX_THREADS threads, in
+// which an LED of size m takes C(m) = m / 16 consecutive CTAs (m = 64, 128,
+// 256: 4, 8, 16), so a cluster holds 4, 2 or 1 LEDs, of one job or several.
+// map[b] = (job, batch slot, rank among the LED's CTAs, m) for CTA b; job < 0
+// marks an idle CTA, which passes the cluster's two barriers and exits.
+template <bool FF>
+__global__ void __launch_bounds__(LED_MIX_THREADS, 2)
+    led_kernel_mixed(const LedArgs* __restrict__ jobs, const int4* __restrict__ map) {
+  __shared__ LedArgs sa;
+  const int4 q = map[blockIdx.x];
+  if (q.x >= 0 && threadIdx.x == 0) sa = jobs[q.x];
+  __syncthreads();
+  switch (q.x < 0 ? 0 : q.w) {
+    case 64: led_body<64, 4, FF, LED_MIX_THREADS, true>(sa, q.y, q.z); break;
+    case 128: led_body<128, 8, FF, LED_MIX_THREADS, true>(sa, q.y, q.z); break;
+    case 256: led_body<256, 16, FF, LED_MIX_THREADS, true>(sa, q.y, q.z); break;
+    default: {
+      cg::cluster_group cluster = cg::this_cluster();
+      cluster.sync();
+      cluster.sync();
+    }
+  }
 }
 
 // Cluster sizes built for each low-res size (CTAs cooperating on one LED).
@@ -430,7 +510,7 @@ int led_cluster_size(int m) {
 }
 
 template <int M, int C>
-static const void* kernel_ptr() { return (const void*)led_kernel<M, C>; }
+static const void* kernel_ptr() { return (const void*)led_kernel<M, C, false>; }
 
 template <int M, int C>
 static cudaError_t prepare_t(int W);
@@ -494,10 +574,12 @@ static cudaError_t prepare_t(int W) {
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   if (LedLayout<M, C>::bytes(W) > (size_t)optin) return cudaErrorInvalidValue;
-  // both entry points (one job, several jobs); the latter also holds a copy
-  // of its job's arguments in static shared memory
-  const void* fns[2] = {(const void*)led_kernel<M, C>, (const void*)led_kernel_jobs<M, C>};
-  for (int f = 0; f < 2; ++f) {
+  // both entry points (one job, several jobs; the latter also holds a copy
+  // of its job's arguments in static shared memory), with and without the
+  // free-form field
+  const void* fns[4] = {(const void*)led_kernel<M, C, false>, (const void*)led_kernel_jobs<M, C, false>,
+                        (const void*)led_kernel<M, C, true>, (const void*)led_kernel_jobs<M, C, true>};
+  for (int f = 0; f < 4; ++f) {
     if (C > 8) {
       e = cudaFuncSetAttribute(fns[f], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       if (e != cudaSuccess) return e;
@@ -541,12 +623,12 @@ static cudaError_t launch_t(const LedArgs& a, cudaStream_t s, bool pdl) {
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = pdl ? 2 : 1;
-  return cudaLaunchKernelEx(&cfg, led_kernel<M, C>, a);
+  return a.pupil ? cudaLaunchKernelEx(&cfg, led_kernel<M, C, true>, a) : cudaLaunchKernelEx(&cfg, led_kernel<M, C, false>, a);
 }
 
 template <int M, int C>
 static cudaError_t launch_jobs_t(const LedArgs* jobs, const int2* map, int n_clusters, int W_max, cudaStream_t s,
-                                 bool pdl) {
+                                 bool pdl, bool ff) {
   using L = LedLayout<M, C>;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(n_clusters * C), 1, 1);
@@ -562,20 +644,85 @@ static cudaError_t launch_jobs_t(const LedArgs* jobs, const int2* map, int n_clu
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = pdl ? 2 : 1;
-  return cudaLaunchKernelEx(&cfg, led_kernel_jobs<M, C>, jobs, map);
+  return ff ? cudaLaunchKernelEx(&cfg, led_kernel_jobs<M, C, true>, jobs, map)
+            : cudaLaunchKernelEx(&cfg, led_kernel_jobs<M, C, false>, jobs, map);
 }
 
 cudaError_t launch_led_jobs(int m, int C, const LedArgs* jobs, const int2* map, int n_clusters, int W_max,
-                            cudaStream_t s, bool pdl) {
+                            cudaStream_t s, bool pdl, bool ff) {
   if (n_clusters < 1) return cudaErrorInvalidValue;
-  if (m == 32) return launch_jobs_t<32, 2>(jobs, map, n_clusters, W_max, s, pdl);
-  if (m == 64) return launch_jobs_t<64, 4>(jobs, map, n_clusters, W_max, s, pdl);
-  if (m == 128) return launch_jobs_t<128, 8>(jobs, map, n_clusters, W_max, s, pdl);
+  if (m == 32) return launch_jobs_t<32, 2>(jobs, map, n_clusters, W_max, s, pdl, ff);
+  if (m == 64) return launch_jobs_t<64, 4>(jobs, map, n_clusters, W_max, s, pdl, ff);
+  if (m == 128) return launch_jobs_t<128, 8>(jobs, map, n_clusters, W_max, s, pdl, ff);
   if (m == 256)
-    return C == 16 ? launch_jobs_t<256, 16>(jobs, map, n_clusters, W_max, s, pdl)
-                   : launch_jobs_t<256, 8>(jobs, map, n_clusters, W_max, s, pdl);
-  if (m == 512 && C == 16) return launch_jobs_t<512, 16>(jobs, map, n_clusters, W_max, s, pdl);
+    return C == 16 ? launch_jobs_t<256, 16>(jobs, map, n_clusters, W_max, s, pdl, ff)
+                   : launch_jobs_t<256, 8>(jobs, map, n_clusters, W_max, s, pdl, ff);
+  if (m == 512 && C == 16) return launch_jobs_t<512, 16>(jobs, map, n_clusters, W_max, s, pdl, ff);
   return cudaErrorInvalidValue;
+}
+
+int led_mixed_cluster(int m) { return (m == 64 || m == 128 || m == 256) ? m / 16 : 0; }
+
+size_t led_mixed_smem_bytes(int m, int W) {
+  if (m == 64) return LedLayout<64, 4, LED_MIX_THREADS>::bytes(W);
+  if (m == 128) return LedLayout<128, 8, LED_MIX_THREADS>::bytes(W);
+  if (m == 256) return LedLayout<256, 16, LED_MIX_THREADS>::bytes(W);
+  return 0;
+}
+
+bool led_mixed_fits(int m, int W) {
+  static int room = -1;  // opt-in shared memory beside the kernel's static shared memory
+  if (room < 0) {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, (const void*)led_kernel_mixed<true>) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    room = optin - (int)fa.sharedSizeBytes;
+  }
+  const size_t b = led_mixed_smem_bytes(m, W);
+  return b > 0 && b <= (size_t)room;
+}
+
+cudaError_t led_mixed_prepare() {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  const void* fns[2] = {(const void*)led_kernel_mixed<false>, (const void*)led_kernel_mixed<true>};
+  for (int f = 0; f < 2 && e == cudaSuccess; ++f) {
+    e = cudaFuncSetAttribute(fns[f], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fns[f], cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, fns[f]);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fns[f], cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+  }
+  return e;
+}
+
+cudaError_t launch_led_mixed(const LedArgs* jobs, const int4* map, int n_ctas, size_t smem, cudaStream_t s, bool pdl,
+                             bool ff) {
+  if (n_ctas < 1 || n_ctas % LED_MIX_CLUSTER) return cudaErrorInvalidValue;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)n_ctas, 1, 1);
+  cfg.blockDim = dim3(LED_MIX_THREADS, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = LED_MIX_CLUSTER;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 2 : 1;
+  return ff ? cudaLaunchKernelEx(&cfg, led_kernel_mixed<true>, jobs, map)
+            : cudaLaunchKernelEx(&cfg, led_kernel_mixed<false>, jobs, map);
 }
 
 cudaError_t launch_led(int m, int C, const LedArgs& a, cudaStream_t s, bool pdl) {

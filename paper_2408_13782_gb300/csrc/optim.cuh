@@ -17,10 +17,12 @@ __device__ __forceinline__ void adam1(float& w, float& m, float& v, float g, flo
 }
 
 // One step of the handle's optimiser on one real component with learning rate
-// lr and this step's coefficients k (see UpdArgs::coef). The branch is the
+// lr and this step's coefficients k (see UpdArgs::coef). OPT >= 0 fixes the
+// rule at compile time (it must equal a.opt); OPT < 0 branches on a.opt, the
 // same for every thread of a launch.
+template <int OPT = -1>
 __device__ __forceinline__ void opt1(const UpdArgs& a, float& w, float& m, float& v, float g, float lr, float4 k) {
-  switch (a.opt) {
+  switch (OPT >= 0 ? OPT : a.opt) {
     case FPM_OPT_ADAMW:
       w *= 1.f - lr * a.wd;
       adam1(w, m, v, g, lr * k.x, k.y, a.b1, a.b2, a.eps);

@@ -8,11 +8,13 @@
 // it finishes.
 //
 // Work is issued in rounds of one epoch (a fresh random permutation chopped
-// into batches, Eq. 13-14) per job. Jobs with the same kernel configuration
-// and epoch shape (low-res size, cluster, crop box, LED count, batch size;
-// FP32 FFT form) share a round: step s of the round is one per-LED launch and one
-// update launch covering step s of every job in it, the jobs' arguments read
-// from device tables. A round is captured once as a CUDA graph (kept while
+// into batches, Eq. 13-14) per job. FP32 FFT-form jobs with the same number
+// of steps per epoch share a round: step s of the round is one per-LED launch
+// and one update launch covering step s of every job in it, the jobs'
+// arguments read from device tables. Jobs of low-res size 64, 128 and 256 go
+// to one mixed-size launch (clusters of 16 CTAs shared by their LEDs, 4, 8 or
+// 16 CTAs each), whatever their crop box, LED count and batch size; other
+// sizes share a round only with jobs of the same kernel configuration. A round is captured once as a CUDA graph (kept while
 // its jobs are resident) and relaunched every epoch with the new schedules
 // and Adam coefficients copied from pinned staging inside the graph. Rounds
 // of different groups run on their own streams, so all admitted jobs overlap
@@ -71,7 +73,8 @@ struct Round {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
   cudaGraphExec_t exec = nullptr;
-  int steps = 0, B = 0, nfull = 0, rem = 0;
+  int steps = 0;
+  bool mixed = false;            // the mixed-size per-LED launch
   std::vector<int4*> h_slots;    // pinned, per job: the epoch's slot table
   std::vector<float4*> h_coef;   // pinned, per job: optimiser coefficients per step
   unsigned char* d_tables = nullptr;  // LedArgs / UpdArgs tables and maps of all steps
@@ -240,47 +243,85 @@ int retire_epoch(fpm_server* s, Job* j) {
 
 // ---------------------------------------------------------------- rounds
 
+bool groupable(const Job* j) { return j->er.fft != 0; }
+
+int epoch_steps(const Job* j) { return (j->er.n_leds + j->desc.batch - 1) / j->desc.batch; }
+
+// Jobs the mixed-size launch takes (sizes 64, 128, 256 whose box fits it). Its
+// split of an LED (led_mixed_cluster) may differ from the handle's own at
+// m = 256; the handle's partials have room for both.
+bool mixable(const Job* j) { return groupable(j) && led_mixed_cluster(j->er.m) > 0 && led_mixed_fits(j->er.m, j->er.W); }
+
 std::string group_key(const Job* j) {
   char b[96];
-  std::snprintf(b, sizeof b, "m%d C%d W%d n%d B%d", j->er.m, j->er.C, j->er.W, j->er.n_leds, j->desc.batch);
+  if (mixable(j))
+    std::snprintf(b, sizeof b, "mix S%d", epoch_steps(j));
+  else
+    std::snprintf(b, sizeof b, "m%d C%d W%d n%d B%d", j->er.m, j->er.C, j->er.W, j->er.n_leds, j->desc.batch);
   return b;
 }
 
-bool groupable(const Job* j) { return j->er.fft != 0; }
-
-// Build the round of jobs js (same group): tables, staging, and its graph.
+// Build the round of jobs js (same group: the same number of steps per
+// epoch): tables, staging, and its graph.
 int build_round(Round* r, const std::vector<Job*>& js) {
   r->jobs = js;
   const Job* j0 = js[0];
-  const int n = j0->er.n_leds, B = j0->desc.batch, m = j0->er.m, C = j0->er.C;
-  r->B = B;
-  r->nfull = n / B;
-  r->rem = n - r->nfull * B;
-  r->steps = r->nfull + (r->rem ? 1 : 0);
+  const int m = j0->er.m, C = j0->er.C;
+  r->mixed = mixable(j0);
+  r->steps = epoch_steps(j0);
   const int J = (int)js.size(), S = r->steps;
+  if (r->mixed && led_mixed_prepare() != cudaSuccess) return FPM_ERR_CUDA;
   if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess)
     return FPM_ERR_CUDA;
   r->h_slots.assign(J, nullptr);
   r->h_coef.assign(J, nullptr);
   for (int q = 0; q < J; ++q)
-    if (cudaMallocHost(&r->h_slots[q], sizeof(int4) * n) != cudaSuccess ||
+    if (cudaMallocHost(&r->h_slots[q], sizeof(int4) * js[q]->er.n_leds) != cudaSuccess ||
         cudaMallocHost(&r->h_coef[q], sizeof(float4) * S) != cudaSuccess)
       return FPM_ERR_OOM;
-  // per step: J LedArgs, J UpdArgs, the cluster map and the update-CTA map
+  // per step: J LedArgs, J UpdArgs, the per-LED map and the update-CTA map.
+  // Same-configuration rounds map each cluster to (job, slot); the mixed
+  // launch maps each CTA to (job, slot, rank among the LED's CTAs, m), the
+  // LEDs ordered by CTAs per LED, largest first, so that none straddles a
+  // cluster (every split divides 16), and the last cluster filled with idle CTAs.
   std::vector<LedArgs> led((size_t)S * J);
   std::vector<UpdArgs> upd((size_t)S * J);
-  std::vector<std::vector<int2>> lmap(S), umap(S);
+  std::vector<std::vector<int4>> lmap(S);
+  std::vector<std::vector<int2>> umap(S);
+  std::vector<int> bmax(S, 0);
+  size_t smem = 0;
+  bool ff = false;  // some job models a free-form pupil field: the instantiation that has it
   for (int st = 0; st < S; ++st) {
-    const int Bs = st < r->nfull ? B : r->rem;
     for (int q = 0; q < J; ++q) {
       Job* j = js[q];
+      const int B = j->desc.batch, nfull = j->er.n_leds / B;
+      const int Bs = st < nfull ? B : j->er.n_leds - nfull * B;
       const int4* sl = j->er.slots + (size_t)st * B;
-      led[(size_t)st * J + q] = engine_led_args(j->h, sl, Bs);
-      upd[(size_t)st * J + q] = engine_upd_args(j->h, sl, Bs, st, j->er.losses + st);
-      for (int k = 0; k < Bs; ++k) lmap[st].push_back(make_int2(q, k));
+      LedArgs& la = led[(size_t)st * J + q];
+      la = engine_led_args(j->h, sl, Bs);
+      UpdArgs& ua = upd[(size_t)st * J + q];
+      ua = engine_upd_args(j->h, sl, Bs, st, j->er.losses + st);
+      if (r->mixed) ua.C = led_mixed_cluster(j->er.m);  // partials per LED in the mixed launch
+      ff = ff || la.pupil != nullptr;
+      bmax[st] = std::max(bmax[st], Bs);
+      if (r->mixed) smem = std::max(smem, led_mixed_smem_bytes(j->er.m, j->er.W));
+      if (!r->mixed)
+        for (int k = 0; k < Bs; ++k) lmap[st].push_back(make_int4(q, k, 0, 0));
       const int nc = update_ctas(upd[(size_t)st * J + q]);
       for (int b = 0; b < nc; ++b) umap[st].push_back(make_int2(q, b));
+    }
+    if (r->mixed) {
+      for (int c = LED_MIX_CLUSTER; c >= 1; c /= 2)
+        for (int q = 0; q < J; ++q) {
+          Job* j = js[q];
+          if (led_mixed_cluster(j->er.m) != c) continue;
+          const int B = j->desc.batch, nfull = j->er.n_leds / B;
+          const int Bs = st < nfull ? B : j->er.n_leds - nfull * B;
+          for (int k = 0; k < Bs; ++k)
+            for (int t = 0; t < c; ++t) lmap[st].push_back(make_int4(q, k, t, j->er.m));
+        }
+      while (lmap[st].size() % LED_MIX_CLUSTER) lmap[st].push_back(make_int4(-1, 0, 0, 0));
     }
   }
   size_t lm = 0, um = 0;
@@ -288,39 +329,57 @@ int build_round(Round* r, const std::vector<Job*>& js) {
     lm += lmap[st].size();
     um += umap[st].size();
   }
-  const size_t bytes = sizeof(LedArgs) * led.size() + sizeof(UpdArgs) * upd.size() + sizeof(int2) * (lm + um);
+  // four tables, each starting on a 256-byte boundary
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  const size_t o_upd = up(sizeof(LedArgs) * led.size()), o_lmap = o_upd + up(sizeof(UpdArgs) * upd.size());
+  const size_t o_umap = o_lmap + up(sizeof(int4) * lm), bytes = o_umap + sizeof(int2) * um;
   if (cudaMalloc(&r->d_tables, bytes) != cudaSuccess) return FPM_ERR_OOM;
   LedArgs* d_led = reinterpret_cast<LedArgs*>(r->d_tables);
-  UpdArgs* d_upd = reinterpret_cast<UpdArgs*>(d_led + led.size());
-  int2* d_map = reinterpret_cast<int2*>(d_upd + upd.size());
-  std::vector<int2> maps;
-  maps.reserve(lm + um);
+  UpdArgs* d_upd = reinterpret_cast<UpdArgs*>(r->d_tables + o_upd);
+  int4* d_lmap = reinterpret_cast<int4*>(r->d_tables + o_lmap);
+  int2* d_umap = reinterpret_cast<int2*>(r->d_tables + o_umap);
+  std::vector<int4> lmaps;
+  std::vector<int2> umaps;
+  lmaps.reserve(lm);
+  umaps.reserve(um);
   std::vector<size_t> loff(S), uoff(S);
   for (int st = 0; st < S; ++st) {
-    loff[st] = maps.size();
-    maps.insert(maps.end(), lmap[st].begin(), lmap[st].end());
-    uoff[st] = maps.size();
-    maps.insert(maps.end(), umap[st].begin(), umap[st].end());
+    loff[st] = lmaps.size();
+    lmaps.insert(lmaps.end(), lmap[st].begin(), lmap[st].end());
+    uoff[st] = umaps.size();
+    umaps.insert(umaps.end(), umap[st].begin(), umap[st].end());
   }
+  // the same-configuration launch reads (job, slot) pairs
+  std::vector<int2> lpairs;
+  if (!r->mixed)
+    for (const int4& e : lmaps) lpairs.push_back(make_int2(e.x, e.y));
   if (cudaMemcpy(d_led, led.data(), sizeof(LedArgs) * led.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(d_upd, upd.data(), sizeof(UpdArgs) * upd.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(d_map, maps.data(), sizeof(int2) * maps.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      (r->mixed ? cudaMemcpy(d_lmap, lmaps.data(), sizeof(int4) * lm, cudaMemcpyHostToDevice)
+                : cudaMemcpy(d_lmap, lpairs.data(), sizeof(int2) * lm, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      cudaMemcpy(d_umap, umaps.data(), sizeof(int2) * um, cudaMemcpyHostToDevice) != cudaSuccess)
     return FPM_ERR_CUDA;
   // the graph: schedules and coefficients in, S steps of two launches, losses out
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(r->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return FPM_ERR_CUDA;
   cudaError_t e = cudaSuccess;
   for (int q = 0; q < J && e == cudaSuccess; ++q) {
-    e = cudaMemcpyAsync(js[q]->er.slots, r->h_slots[q], sizeof(int4) * n, cudaMemcpyHostToDevice, r->stream);
+    e = cudaMemcpyAsync(js[q]->er.slots, r->h_slots[q], sizeof(int4) * js[q]->er.n_leds, cudaMemcpyHostToDevice,
+                        r->stream);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(js[q]->er.coef, r->h_coef[q], sizeof(float4) * S, cudaMemcpyHostToDevice, r->stream);
   }
+  const int2* d_lpairs = reinterpret_cast<const int2*>(d_lmap);
   for (int st = 0; st < S && e == cudaSuccess; ++st) {
-    const int Bs = st < r->nfull ? B : r->rem;
-    e = launch_led_jobs(m, C, d_led + (size_t)st * J, d_map + loff[st], (int)lmap[st].size(), j0->er.W, r->stream,
-                        st > 0);
+    if (r->mixed)
+      e = launch_led_mixed(d_led + (size_t)st * J, d_lmap + loff[st], (int)lmap[st].size(), smem, r->stream, st > 0,
+                           ff);
+    else
+      e = launch_led_jobs(m, C, d_led + (size_t)st * J, d_lpairs + loff[st], (int)lmap[st].size(), j0->er.W,
+                          r->stream, st > 0, ff);
     if (e == cudaSuccess)
-      e = launch_update_jobs(d_upd + (size_t)st * J, d_map + uoff[st], (int)umap[st].size(), Bs, r->stream, true);
+      e = launch_update_jobs(d_upd + (size_t)st * J, d_umap + uoff[st], (int)umap[st].size(), bmax[st], r->stream,
+                             true);
   }
   for (int q = 0; q < J && e == cudaSuccess; ++q)
     e = cudaMemcpyAsync(js[q]->pinned, js[q]->er.epoch, sizeof(double), cudaMemcpyDeviceToHost, r->stream);

@@ -195,7 +195,9 @@ __host__ __device__ inline int update_decay_ctas(const UpdArgs& a) {
   return decay ? NDECAY : 0;
 }
 
-// CTA bid of the update of the job described by a.
+// CTA bid of the update of the job described by a. OPT: the optimiser fixed at
+// compile time for the object elements (a.opt), or -1 to branch on a.opt.
+template <int OPT>
 __device__ __forceinline__ void update_body(const UpdArgs& a, const int bid) {
   asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
   // the launch's dynamic shared memory (3 B doubles) holds, in the column
@@ -313,15 +315,17 @@ __device__ __forceinline__ void update_body(const UpdArgs& a, const int bid) {
       a.g_obj[o] = g;
       continue;
     }
-    opt1(a, w.x, m.x, v.x, g.x, a.lr_obj, bc);
-    opt1(a, w.y, m.y, v.y, g.y, a.lr_obj, bc);
+    opt1<OPT>(a, w.x, m.x, v.x, g.x, a.lr_obj, bc);
+    opt1<OPT>(a, w.y, m.y, v.y, g.y, a.lr_obj, bc);
     a.Ot[o] = w;
     a.mO[o] = m;
     a.vO[o] = v;
   }
 }
 
-__global__ void __launch_bounds__(UPD_NT) update_kernel(const UpdArgs a) { update_body(a, (int)blockIdx.x); }
+// One job; one instantiation per optimiser, so the element loop carries only its rule.
+template <int OPT>
+__global__ void __launch_bounds__(UPD_NT) update_kernel(const UpdArgs a) { update_body<OPT>(a, (int)blockIdx.x); }
 
 // Several jobs in one launch (the serving loop): CTA q is CTA map[q].y of the
 // update of job map[q].x, whose arguments are copied to shared memory.
@@ -331,15 +335,19 @@ __global__ void __launch_bounds__(UPD_NT) update_kernel_jobs(const UpdArgs* __re
   const int2 q = map[blockIdx.x];
   if (threadIdx.x == 0) sa = jobs[q.x];
   __syncthreads();
-  update_body(sa, q.y);
+  update_body<-1>(sa, q.y);
 }
 
 int update_ctas(const UpdArgs& a) { return a.n_cols + NSC + update_decay_ctas(a) + a.pupil_cols; }
 
 cudaError_t update_prepare() {
-  cudaError_t e = cudaFuncSetAttribute(update_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                       cudaSharedmemCarveoutMaxShared);
-  if (e != cudaSuccess) return e;
+  const void* fns[4] = {(const void*)update_kernel<FPM_OPT_ADAM>, (const void*)update_kernel<FPM_OPT_ADAMW>,
+                        (const void*)update_kernel<FPM_OPT_NADAM>, (const void*)update_kernel<FPM_OPT_RMSPROP>};
+  for (const void* f : fns) {
+    const cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                               cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+  }
   return cudaFuncSetAttribute(update_kernel_jobs, cudaFuncAttributePreferredSharedMemoryCarveout,
                               cudaSharedmemCarveoutMaxShared);
 }
@@ -372,7 +380,12 @@ cudaError_t launch_update(const UpdArgs& a, cudaStream_t s, bool pdl) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = pdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, update_kernel, a);
+  switch (a.opt) {
+    case FPM_OPT_ADAMW: return cudaLaunchKernelEx(&cfg, update_kernel<FPM_OPT_ADAMW>, a);
+    case FPM_OPT_NADAM: return cudaLaunchKernelEx(&cfg, update_kernel<FPM_OPT_NADAM>, a);
+    case FPM_OPT_RMSPROP: return cudaLaunchKernelEx(&cfg, update_kernel<FPM_OPT_RMSPROP>, a);
+    default: return cudaLaunchKernelEx(&cfg, update_kernel<FPM_OPT_ADAM>, a);
+  }
 }
 
 }  // namespace fpmk
