@@ -303,9 +303,9 @@ def serving_jobs(n_jobs: int, rate_hz: float, seed: int, shape=None):
     return jobs
 
 
-def serving_run(jobs, budget: int, max_active: int, admission: str = "arrival"):
+def serving_run(jobs, budget: int, max_active: int, admission: str = "arrival", grouping: str = "size"):
     from paper_2408_13782_gb300 import serve as sv
-    srv = sv.Server(budget, max_active, admission)
+    srv = sv.Server(budget, max_active, admission, grouping)
     ids, st, wall = sv.run_arrivals(srv, [(d, s, t) for d, s, t, _, _ in jobs])
     stats = srv.stats()
     srv.close()
@@ -313,7 +313,7 @@ def serving_run(jobs, budget: int, max_active: int, admission: str = "arrival"):
     upd = sum(x["led_updates"] for x in st)
     span = max(x["t_done"] for x in st) - min(x["t_submit"] for x in st)
     return {"p50_ttc_s": float(np.percentile(ttc, 50)), "p99_ttc_s": float(np.percentile(ttc, 99)),
-            "mean_ttc_s": float(ttc.mean()), "led_updates_per_s": upd / span,
+            "mean_ttc_s": float(ttc.mean()), "led_updates_per_s": upd / span, "grouping": grouping,
             "jobs_done": int(sum(x["state"] == sv.JOB_DONE for x in st)),
             "epochs_median": float(np.median([x["epochs"] for x in st])), "makespan_s": span,
             "admission": admission, "max_active": max_active, "server": stats}
@@ -352,6 +352,8 @@ def serving_section(n_jobs=100, rate_hz=40.0, seed=5):
     runs = {"continuous": serving_run(jobs, budget, max_active=64),
             "continuous_smallest_first": serving_run(jobs, budget, max_active=64, admission="smallest"),
             "continuous_8_active": serving_run(jobs, budget, max_active=8),
+            "continuous_group_by_config": serving_run(jobs, budget, max_active=64, grouping="config"),
+            "continuous_sizes_mixed": serving_run(jobs, budget, max_active=64, grouping="mixed"),
             "serial": serving_run(jobs, budget, max_active=1)}
     same = serving_jobs(16, 1000.0, seed + 1, shape=(512, 11))
     same_serving = serving_run(same, budget, max_active=64)
@@ -361,10 +363,11 @@ def serving_section(n_jobs=100, rate_hz=40.0, seed=5):
         mix[f"{N}^2/{g}x{g}"] = mix.get(f"{N}^2/{g}x{g}", 0) + 1
     return {"what": f"{n_jobs} jobs, Poisson arrivals {rate_hz:g}/s, ROI from {{256,512,1024,2048}}^2 at "
                     "upsample 4, LED grids {7,11,15}^2, stop at relative epoch-loss change < 1e-4 or 40 epochs; "
-                    "continuous batching (jobs admitted by device-memory footprint, overlapping, same-shape "
-                    "jobs stepped together in one launch per step; admission in arrival order or smallest "
-                    "expected work first; at most 64 or 8 resident) vs the same jobs one at a time (FCFS) on "
-                    "the same GPU",
+                    "continuous batching (jobs admitted by device-memory footprint, overlapping; jobs with "
+                    "the same steps per epoch stepped together in one launch per step, grouped by low-res size "
+                    "(default), by kernel configuration, or with sizes 64/128/256 mixed in one launch; admission "
+                    "in arrival order or smallest expected work first; at most 64 or 8 resident) vs the same "
+                    "jobs one at a time (FCFS) on the same GPU",
             "mix_counts": mix, "hbm_budget_bytes": budget, **runs,
             "same_shape": {"what": "16 jobs of 512^2 / 11x11 arriving in a burst (Poisson 1000/s)",
                            "continuous": same_serving, "serial": same_serial},

@@ -389,11 +389,12 @@ int fpm_probe_fp32_fma(int32_t iters, int32_t reps, double* tflops_out, double* 
  * batch size from the available GPU memory, Section 2.2; here memory decides
  * which jobs are resident). An admitted job keeps its object spectrum, pupil,
  * defocus, LED parameters and Adam state resident on the device. Each epoch
- * is a fresh random batch order (Eq. 13-14, seed = job seed). Resident jobs of
- * the same low-res size, LED count and batch size (FP32 FFT form) run their
- * epochs together in rounds: each step of a round is one per-LED launch and
- * one update launch covering all of them, and a round is one CUDA graph,
- * captured once per set of jobs. Rounds of different sets run on their own
+ * is a fresh random batch order (Eq. 13-14, seed = job seed). Resident jobs
+ * (FP32 FFT form) with the same number of steps per epoch run their epochs
+ * together in rounds, grouped as fpm_server_set_grouping says: each step of a
+ * round is one per-LED launch and one update launch covering all of them, and
+ * a round is one CUDA graph, captured once per set of jobs. Rounds of different
+ * sets run on their own
  * streams, so all resident jobs overlap on the GPU; each job's arithmetic is
  * the same alone or in a round, so its result is too (bit for bit). A job
  * stops when the relative change of its epoch loss drops below rel_tol, or
@@ -437,6 +438,23 @@ typedef struct fpm_job_status {
 #define FPM_ADMIT_ARRIVAL  0
 #define FPM_ADMIT_SMALLEST 1
 int fpm_server_set_admission(fpm_server* s, int32_t order);
+
+/* Which resident jobs share a round (all with the same number of steps per
+ * epoch, FP32 FFT form):
+ * FPM_GROUP_CONFIG  the same low-res size, crop box, LED count and batch size;
+ * FPM_GROUP_SIZE    (default) the same low-res size; sizes 64, 128 and 256 use
+ *                   the mixed per-LED launch, which takes any crop box (up to
+ *                   h < 64 at 256), LED count and batch size;
+ * FPM_GROUP_MIXED   sizes 64, 128 and 256 together in one mixed launch (their
+ *                   LEDs share clusters of 16 CTAs), other sizes as SIZE.
+ * A round steps at the pace of its slowest job, so mixing sizes trades the
+ * small jobs' time to converge for fewer launches. A job's result does not
+ * depend on the other jobs of its round; at m = 64 it also equals a direct run
+ * bit for bit (the same CTA layout), at m = 128 and 256 within rounding. */
+#define FPM_GROUP_CONFIG 0
+#define FPM_GROUP_SIZE   1
+#define FPM_GROUP_MIXED  2
+int fpm_server_set_grouping(fpm_server* s, int32_t grouping);
 
 /* Device bytes a job holds while resident (its admission size). */
 int64_t fpm_job_footprint(const fpm_job_desc* d);

@@ -589,6 +589,36 @@ __device__ __forceinline__ void fft256_group_in(float2 (&v)[16], float2* __restr
   r16_store(buf, j, 1, v);
   __syncwarp();
 }
+// Pruned 256-point transforms for a box |t| <= h < 64 (t mod 256): ZIN, the
+// first pass's inputs are zero outside the box (points j + 16 n, n = 4..11);
+// ZOUT, only the outputs in the box are wanted (j + 16 r, r = 0..3, 12..15),
+// and only those are stored. The inputs of the first pass are in registers
+// (points j + 16 r, as fft256_group_in takes them) or in buf.
+template <int DIR, bool ZIN, bool ZOUT>
+__device__ __forceinline__ void fft256_inreg_p(float2 (&v)[16], float2* __restrict__ buf,
+                                               const float2* __restrict__ tw2, int j) {
+  dft16p<DIR, ZIN, false>(v);
+  __syncwarp();
+  r16_store(buf, j, 0, v);
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = buf[pidx16(j + 16 * r)];
+#pragma unroll
+  for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw_dir<DIR>(tw2[(r - 1) * 16 + j]));
+  dft16p<DIR, false, ZOUT>(v);
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 16; ++r)
+    if (!ZOUT || r < 4 || r >= 12) buf[pidx16(j + 16 * r)] = v[r];
+  __syncwarp();
+}
+template <int DIR, bool ZOUT>
+__device__ __forceinline__ void fft256_group_p(float2* __restrict__ buf, const float2* __restrict__ tw2, int j) {
+  float2 v[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) v[r] = buf[pidx16(j + 16 * r)];
+  fft256_inreg_p<DIR, false, ZOUT>(v, buf, tw2, j);
+}
 #endif
 
 // Box column (or row) stored at transform index t when a box of half-width h

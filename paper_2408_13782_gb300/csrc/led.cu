@@ -109,9 +109,12 @@ __device__ __forceinline__ void transform(float2* buf, const FftTw<(M >= 256) ? 
 // the parametric kernels carry none of its registers). NT_: threads per CTA.
 // SUB: the LED's C CTAs are CTAs base .. base + C - 1 of a larger cluster
 // (sub_rank = this CTA's rank among them), which calls its two cluster
-// barriers together with the other LEDs of the cluster.
-template <int M, int C, bool FF, int NT_ = led_threads<M, C>(), bool SUB = false>
+// barriers together with the other LEDs of the cluster. PR (m = 256 with a
+// box half-width h < 64): the transforms skip the first-pass arithmetic on
+// inputs known to be zero outside the box and the last-pass outputs outside it.
+template <int M, int C, bool FF, int NT_ = led_threads<M, C>(), bool SUB = false, bool PR = false>
 __device__ __forceinline__ void led_body(const LedArgs& a, const int k, const int sub_rank = 0) {
+  static_assert(!PR || M == 256, "pruned transforms are the 256-point ones");
   using L = LedLayout<M, C, NT_>;
   constexpr int NT = L::NT, G = L::G, NG = L::NG, ROWS = L::ROWS, TS = L::TS, FS = L::FS;
   constexpr int NW = L::NW;
@@ -278,7 +281,8 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k, const in
 #pragma unroll
       for (int r = 0; r < 16; ++r)
         v[r] = box_index(j + 16 * r, M, h) >= 0 ? buf[bidx<M>(j + 16 * r)] : make_float2(0.f, 0.f);
-      fft256_group_in<+1>(v, buf, tw2, j);
+      if constexpr (PR) fft256_inreg_p<+1, true, false>(v, buf, tw2, j);
+      else fft256_group_in<+1>(v, buf, tw2, j);
     } else {
       transform<M, +1>(buf, TW, tws, tw2, j);
     }
@@ -322,7 +326,8 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k, const in
         const int c = box_index(j + 16 * r, M, h);
         v[r] = (act && c >= 0) ? Rw[(size_t)c * L::RS + yl] : make_float2(0.f, 0.f);
       }
-      fft256_group_in<+1>(v, buf, tw2, j);
+      if constexpr (PR) fft256_inreg_p<+1, true, false>(v, buf, tw2, j);
+      else fft256_group_in<+1>(v, buf, tw2, j);
     } else {
       for (int t = h + 1 + j; t < M - h; t += G) buf[bidx<M>(t)] = make_float2(0.f, 0.f);  // outside the box
       if constexpr (L::PUSH) {
@@ -395,7 +400,8 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k, const in
     }
     __syncwarp();
     if (!fwd_only) {
-      transform<M, -1>(buf, TW, tws, tw2, j);
+      if constexpr (PR) fft256_group_p<-1, true>(buf, tw2, j);  // only the box columns are kept
+      else transform<M, -1>(buf, TW, tws, tw2, j);
       if (act)
         for (int c = j; c < W; c += G) {
           const int kx = c - h, own = c / chunk, lc = c - own * chunk;
@@ -420,7 +426,8 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k, const in
       float2 v[16];
 #pragma unroll
       for (int r = 0; r < 16; ++r) v[r] = act ? T[(c - c0) * TS + j + 16 * r] : make_float2(0.f, 0.f);
-      fft256_group_in<-1>(v, buf, tw2, j);
+      if constexpr (PR) fft256_inreg_p<-1, false, true>(v, buf, tw2, j);  // only the box rows are kept
+      else fft256_group_in<-1>(v, buf, tw2, j);
     } else {
       for (int t = j; t < M; t += G) buf[bidx<M>(t)] = act ? T[(c - c0) * TS + t] : make_float2(0.f, 0.f);
       __syncwarp();
@@ -455,21 +462,21 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k, const in
 }
 
 // One job: cluster k takes batch slot k.
-template <int M, int C, bool FF>
+template <int M, int C, bool FF, bool PR = false>
 __global__ void __launch_bounds__(led_threads<M, C>(), M == 512 ? 1 : 2) led_kernel(const LedArgs a) {
-  led_body<M, C, FF>(a, (int)(blockIdx.x / C));
+  led_body<M, C, FF, led_threads<M, C>(), false, PR>(a, (int)(blockIdx.x / C));
 }
 
 // Several jobs in one launch (the serving loop): cluster q takes slot
 // map[q].y of job map[q].x, whose arguments are copied to shared memory.
-template <int M, int C, bool FF>
+template <int M, int C, bool FF, bool PR = false>
 __global__ void __launch_bounds__(led_threads<M, C>(), M == 512 ? 1 : 2)
     led_kernel_jobs(const LedArgs* __restrict__ jobs, const int2* __restrict__ map) {
   __shared__ LedArgs sa;
   const int2 q = map[blockIdx.x / C];
   if (threadIdx.x == 0) sa = jobs[q.x];
   __syncthreads();
-  led_body<M, C, FF>(sa, q.y);
+  led_body<M, C, FF, led_threads<M, C>(), false, PR>(sa, q.y);
 }
 
 // Jobs of different low-res sizes in one launch (the serving loop's mixed
@@ -488,7 +495,7 @@ __global__ void __launch_bounds__(LED_MIX_THREADS, 2)
   switch (q.x < 0 ? 0 : q.w) {
     case 64: led_body<64, 4, FF, LED_MIX_THREADS, true>(sa, q.y, q.z); break;
     case 128: led_body<128, 8, FF, LED_MIX_THREADS, true>(sa, q.y, q.z); break;
-    case 256: led_body<256, 16, FF, LED_MIX_THREADS, true>(sa, q.y, q.z); break;
+    case 256: led_body<256, 16, FF, LED_MIX_THREADS, true, true>(sa, q.y, q.z); break;  // h < 64 (led_mixed_fits)
     default: {
       cg::cluster_group cluster = cg::this_cluster();
       cluster.sync();
@@ -510,7 +517,11 @@ int led_cluster_size(int m) {
 }
 
 template <int M, int C>
-static const void* kernel_ptr() { return (const void*)led_kernel<M, C, false>; }
+static const void* kernel_ptr(int W) {  // the parametric kernel a launch with box W uses
+  if constexpr (M == 256)
+    if ((W - 1) / 2 < 64) return (const void*)led_kernel<M, C, false, true>;
+  return (const void*)led_kernel<M, C, false>;
+}
 
 template <int M, int C>
 static cudaError_t prepare_t(int W);
@@ -529,7 +540,7 @@ static int max_active_clusters(int W) {
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   int n = 0;
-  if (cudaOccupancyMaxActiveClusters(&n, kernel_ptr<M, C>(), &cfg) != cudaSuccess) {
+  if (cudaOccupancyMaxActiveClusters(&n, kernel_ptr<M, C>(W), &cfg) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -577,9 +588,12 @@ static cudaError_t prepare_t(int W) {
   // both entry points (one job, several jobs; the latter also holds a copy
   // of its job's arguments in static shared memory), with and without the
   // free-form field
-  const void* fns[4] = {(const void*)led_kernel<M, C, false>, (const void*)led_kernel_jobs<M, C, false>,
-                        (const void*)led_kernel<M, C, true>, (const void*)led_kernel_jobs<M, C, true>};
-  for (int f = 0; f < 4; ++f) {
+  // and, at m = 256, in the pruned forms for boxes with h < 64
+  const void* fns[8] = {(const void*)led_kernel<M, C, false>, (const void*)led_kernel_jobs<M, C, false>,
+                        (const void*)led_kernel<M, C, true>, (const void*)led_kernel_jobs<M, C, true>,
+                        (const void*)led_kernel<M, C, false, M == 256>, (const void*)led_kernel_jobs<M, C, false, M == 256>,
+                        (const void*)led_kernel<M, C, true, M == 256>, (const void*)led_kernel_jobs<M, C, true, M == 256>};
+  for (int f = 0; f < (M == 256 ? 8 : 4); ++f) {
     if (C > 8) {
       e = cudaFuncSetAttribute(fns[f], cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       if (e != cudaSuccess) return e;
@@ -623,6 +637,9 @@ static cudaError_t launch_t(const LedArgs& a, cudaStream_t s, bool pdl) {
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = pdl ? 2 : 1;
+  if (M == 256 && a.h < 64)
+    return a.pupil ? cudaLaunchKernelEx(&cfg, led_kernel<M, C, true, M == 256>, a)
+                   : cudaLaunchKernelEx(&cfg, led_kernel<M, C, false, M == 256>, a);
   return a.pupil ? cudaLaunchKernelEx(&cfg, led_kernel<M, C, true>, a) : cudaLaunchKernelEx(&cfg, led_kernel<M, C, false>, a);
 }
 
@@ -644,6 +661,9 @@ static cudaError_t launch_jobs_t(const LedArgs* jobs, const int2* map, int n_clu
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = pdl ? 2 : 1;
+  if (M == 256 && (W_max - 1) / 2 < 64)  // the jobs of a same-configuration round share their box
+    return ff ? cudaLaunchKernelEx(&cfg, led_kernel_jobs<M, C, true, M == 256>, jobs, map)
+              : cudaLaunchKernelEx(&cfg, led_kernel_jobs<M, C, false, M == 256>, jobs, map);
   return ff ? cudaLaunchKernelEx(&cfg, led_kernel_jobs<M, C, true>, jobs, map)
             : cudaLaunchKernelEx(&cfg, led_kernel_jobs<M, C, false>, jobs, map);
 }
@@ -684,7 +704,7 @@ bool led_mixed_fits(int m, int W) {
     room = optin - (int)fa.sharedSizeBytes;
   }
   const size_t b = led_mixed_smem_bytes(m, W);
-  return b > 0 && b <= (size_t)room;
+  return b > 0 && b <= (size_t)room && (m != 256 || (W - 1) / 2 < 64);  // m = 256: the pruned body only
 }
 
 cudaError_t led_mixed_prepare() {

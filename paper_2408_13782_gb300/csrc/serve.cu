@@ -9,12 +9,14 @@
 //
 // Work is issued in rounds of one epoch (a fresh random permutation chopped
 // into batches, Eq. 13-14) per job. FP32 FFT-form jobs with the same number
-// of steps per epoch share a round: step s of the round is one per-LED launch
-// and one update launch covering step s of every job in it, the jobs'
-// arguments read from device tables. Jobs of low-res size 64, 128 and 256 go
-// to one mixed-size launch (clusters of 16 CTAs shared by their LEDs, 4, 8 or
-// 16 CTAs each), whatever their crop box, LED count and batch size; other
-// sizes share a round only with jobs of the same kernel configuration. A round is captured once as a CUDA graph (kept while
+// of steps per epoch share a round (grouped by the server's policy: the same
+// kernel configuration, the same low-res size, or sizes 64, 128 and 256
+// together): step s of the round is one per-LED launch and one update launch
+// covering step s of every job in it, the jobs' arguments read from device
+// tables. Jobs of size 64, 128 and 256 grouped by size or mixed use the
+// mixed-size launch (clusters of 16 CTAs shared by their LEDs, 4, 8 or 16 CTAs
+// each), whatever their crop box, LED count and batch size; other jobs use the
+// same-configuration launch. A round is captured once as a CUDA graph (kept while
 // its jobs are resident) and relaunched every epoch with the new schedules
 // and Adam coefficients copied from pinned staging inside the graph. Rounds
 // of different groups run on their own streams, so all admitted jobs overlap
@@ -87,6 +89,7 @@ struct fpm_server {
   int64_t budget = 0, used = 0;
   int max_active = 0;
   int admission = FPM_ADMIT_ARRIVAL;
+  int grouping = FPM_GROUP_SIZE;
   std::deque<Job*> queue;
   std::vector<Job*> active;
   std::map<int64_t, std::unique_ptr<Job>> jobs;
@@ -252,10 +255,14 @@ int epoch_steps(const Job* j) { return (j->er.n_leds + j->desc.batch - 1) / j->d
 // m = 256; the handle's partials have room for both.
 bool mixable(const Job* j) { return groupable(j) && led_mixed_cluster(j->er.m) > 0 && led_mixed_fits(j->er.m, j->er.W); }
 
-std::string group_key(const Job* j) {
+// The round a job joins under the server's grouping (a key starting "mix"
+// marks the mixed-size launch).
+std::string group_key(const fpm_server* s, const Job* j) {
   char b[96];
-  if (mixable(j))
+  if (s->grouping == FPM_GROUP_MIXED && mixable(j))
     std::snprintf(b, sizeof b, "mix S%d", epoch_steps(j));
+  else if (s->grouping == FPM_GROUP_SIZE && mixable(j))
+    std::snprintf(b, sizeof b, "mix S%d m%d", epoch_steps(j), j->er.m);
   else
     std::snprintf(b, sizeof b, "m%d C%d W%d n%d B%d", j->er.m, j->er.C, j->er.W, j->er.n_leds, j->desc.batch);
   return b;
@@ -263,11 +270,11 @@ std::string group_key(const Job* j) {
 
 // Build the round of jobs js (same group: the same number of steps per
 // epoch): tables, staging, and its graph.
-int build_round(Round* r, const std::vector<Job*>& js) {
+int build_round(Round* r, const std::vector<Job*>& js, bool mixed) {
   r->jobs = js;
   const Job* j0 = js[0];
   const int m = j0->er.m, C = j0->er.C;
-  r->mixed = mixable(j0);
+  r->mixed = mixed;
   r->steps = epoch_steps(j0);
   const int J = (int)js.size(), S = r->steps;
   if (r->mixed && led_mixed_prepare() != cudaSuccess) return FPM_ERR_CUDA;
@@ -391,7 +398,7 @@ int build_round(Round* r, const std::vector<Job*>& js) {
 
 // Launch one epoch of every job of a group as one round.
 int launch_round(fpm_server* s, const std::vector<Job*>& js) {
-  std::string key = group_key(js[0]);
+  std::string key = group_key(s, js[0]);
   for (const Job* j : js) {
     char b[32];
     std::snprintf(b, sizeof b, " %p", (const void*)j);
@@ -410,7 +417,7 @@ int launch_round(fpm_server* s, const std::vector<Job*>& js) {
         }
       }
     auto nr = std::make_unique<Round>();
-    const int rc = build_round(nr.get(), js);
+    const int rc = build_round(nr.get(), js, key.compare(0, 3, "mix") == 0);
     if (rc) {
       cudaGetLastError();
       destroy_round(nr.get());
@@ -491,6 +498,14 @@ int fpm_server_set_admission(fpm_server* s, int32_t order) {
   if (!s) return FPM_ERR_ARG;
   if (order != FPM_ADMIT_ARRIVAL && order != FPM_ADMIT_SMALLEST) return srv_fail(s, FPM_ERR_ARG, "unknown admission order");
   s->admission = order;
+  return FPM_OK;
+}
+
+int fpm_server_set_grouping(fpm_server* s, int32_t grouping) {
+  if (!s) return FPM_ERR_ARG;
+  if (grouping < FPM_GROUP_CONFIG || grouping > FPM_GROUP_MIXED) return srv_fail(s, FPM_ERR_ARG, "unknown grouping");
+  if (!s->rounds.empty() || !s->active.empty()) return srv_fail(s, FPM_ERR_STATE, "grouping set with jobs resident");
+  s->grouping = grouping;
   return FPM_OK;
 }
 
@@ -579,7 +594,7 @@ int fpm_server_tick(fpm_server* s, int32_t* n_active, int32_t* n_queued) {
   for (Job* j : s->active) {
     if (j->in_flight) continue;
     if (groupable(j)) {
-      groups[group_key(j)].push_back(j);
+      groups[group_key(s, j)].push_back(j);
     } else if (launch_epoch(j)) {
       fail_job(s, j, fpm_last_error(j->h));
     }

@@ -40,7 +40,7 @@ EXPORTS = ("fpm_create", "fpm_set_hparams", "fpm_get_hparams", "fpm_load", "fpm_
            "fpm_server_tick", "fpm_server_status", "fpm_server_result", "fpm_server_clock", "fpm_server_stats",
            "fpm_server_error", "fpm_server_destroy", "fpm_destroy", "fpm_last_error",
            "fpm_set_step_form", "fpm_get_step_form", "fpm_check_wait_timeout", "fpm_probe_fp32_fma",
-           "fpm_set_memory_limit", "fpm_memory_used", "fpm_server_set_admission",
+           "fpm_set_memory_limit", "fpm_memory_used", "fpm_server_set_admission", "fpm_server_set_grouping",
            "fpm_set_pupil", "fpm_get_pupil", "fpm_pupil_gradient")
 
 

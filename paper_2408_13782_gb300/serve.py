@@ -45,6 +45,7 @@ def _declare(L):
                              i32),
         "fpm_server_error": ([vp], ctypes.c_char_p),
         "fpm_server_set_admission": ([vp, i32], i32),
+        "fpm_server_set_grouping": ([vp, i32], i32),
         "fpm_server_destroy": ([vp], None),
     }
     for name, (args, res) in sig.items():
@@ -78,10 +79,12 @@ def footprint(desc) -> int:
 
 
 ADMISSION = {"arrival": 0, "smallest": 1}
+GROUPING = {"config": 0, "size": 1, "mixed": 2}
 
 
 class Server:
-    def __init__(self, hbm_budget_bytes: int, max_active: int = 64, admission: str = "arrival"):
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 64, admission: str = "arrival",
+                 grouping: str = "size"):
         L = lib()
         _declare(L)
         h = ctypes.c_void_p()
@@ -90,6 +93,11 @@ class Server:
             raise FpmError(rc, "server creation failed")
         self._h = h
         self._check(L.fpm_server_set_admission(h, ADMISSION[admission]))
+        self.set_grouping(grouping)
+
+    def set_grouping(self, grouping: str):
+        """Which resident jobs share a round: "config", "size" or "mixed" (fpm.h)."""
+        self._check(lib().fpm_server_set_grouping(self._h, GROUPING[grouping]))
 
     def _check(self, rc):
         if rc:

@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 import oracle as orc
-from paper_2408_13782_gb300 import Engine
+from paper_2408_13782_gb300 import Engine, FpmError
 from paper_2408_13782_gb300 import serve as sv
 from synth import recipes as S
 from tests.gpu_common import record
@@ -27,8 +27,8 @@ def _job(N, grid, seed, max_epochs=6, rel_tol=0.0, c=None):
     return c, desc, stack
 
 
-def _serve(jobs, budget=8 << 30, max_active=16):
-    srv = sv.Server(budget, max_active)
+def _serve(jobs, budget=8 << 30, max_active=16, grouping="size"):
+    srv = sv.Server(budget, max_active, grouping=grouping)
     ids, st, wall = sv.run_arrivals(srv, [(d, s, t) for (c, d, s), t in jobs])
     res = [srv.result(i, c.N, c.n_leds) for i, ((c, d, s), t) in zip(ids, jobs)]
     srv.close()
@@ -141,7 +141,7 @@ def test_mixed_sizes_share_one_launch_and_match_alone():
     layout as the single-job kernel) equals a direct engine run bit for bit, and
     the m = 128 job (128-thread CTAs instead of 256) within FP32 rounding."""
     jobs = [_job(256, 7, 40, max_epochs=3), _job(512, 7, 41, max_epochs=3), _job(1024, 7, 42, max_epochs=3)]
-    srv = sv.Server(8 << 30, 16)
+    srv = sv.Server(8 << 30, 16, grouping="mixed")
     ids, st, wall = sv.run_arrivals(srv, [(d, s, 0.0) for c, d, s in jobs])
     stats = srv.stats()
     res = [srv.result(i, c.N, c.n_leds) for i, (c, d, s) in zip(ids, jobs)]
@@ -150,7 +150,7 @@ def test_mixed_sizes_share_one_launch_and_match_alone():
     assert stats["max_jobs_per_round"] == 3
     assert stats["round_epochs"] == 9
     for job, r in zip(jobs, res):
-        st1, res1 = _serve([(job, 0.0)])
+        st1, res1 = _serve([(job, 0.0)], grouping="mixed")
         assert np.array_equal(res1[0]["object"], r["object"])
         assert np.array_equal(res1[0]["gamma"], r["gamma"])
     for (c, desc, stack), r, exact in zip(jobs[:2], res[:2], (True, False)):
@@ -172,6 +172,31 @@ def test_mixed_sizes_share_one_launch_and_match_alone():
             assert rel_l2(r["object"], O) <= 1e-4
 
 
+def test_grouping_policies_give_the_same_results():
+    """The three grouping policies put the same jobs in different rounds (by
+    kernel configuration, by size, sizes mixed); each job's result is the same
+    under the size and mixed policies bit for bit (the same mixed-size launch
+    body), and within rounding under the configuration policy; the policy
+    cannot change while jobs are resident."""
+    jobs = [_job(256, 7, 45, max_epochs=2), _job(256, 7, 46, max_epochs=2), _job(1024, 7, 47, max_epochs=2)]
+    out = {}
+    for pol in ("config", "size", "mixed"):
+        st, res = _serve([(j, 0.0) for j in jobs], grouping=pol)
+        assert all(x["state"] == sv.JOB_DONE for x in st)
+        out[pol] = res
+    for k in range(3):
+        assert np.array_equal(out["size"][k]["object"], out["mixed"][k]["object"])
+        assert rel_l2(out["config"][k]["object"], out["size"][k]["object"]) <= 1e-4
+    assert np.array_equal(out["config"][0]["object"], out["size"][0]["object"])   # m = 64: the same layout
+    srv = sv.Server(8 << 30, 4)
+    c, d, s = jobs[0]
+    srv.submit(d, s)
+    srv.tick()
+    with pytest.raises(FpmError):
+        srv.set_grouping("mixed")
+    srv.close()
+
+
 def test_mixed_size_job_equals_the_oracle():
     """An m = 128 job served in a mixed-size round (beside an m = 256 job)
     against the FP64 oracle's reconstruction on the same schedule. The object
@@ -179,7 +204,7 @@ def test_mixed_size_job_equals_the_oracle():
     second epoch's, summed over batches taken after FP32 updates whose rounding
     Adam amplifies, so it is held to 1e-4."""
     a, b = _job(512, 7, 43, max_epochs=2), _job(1024, 7, 44, max_epochs=2)
-    st, res = _serve([(a, 0.0), (b, 0.0)])
+    st, res = _serve([(a, 0.0), (b, 0.0)], grouping="mixed")
     c, desc, stack = a
     assert st[0]["state"] == sv.JOB_DONE and st[0]["epochs"] == 2
     nominal = S.led_grid(c.grid, c.pitch, c.jitter, c.seed)[0]
@@ -192,6 +217,19 @@ def test_mixed_size_job_equals_the_oracle():
     err = rel_l2(res[0]["object"], rec.O)
     record("serving.mixed.m128.object", err)
     record("serving.mixed.m128.loss", abs(st[0]["loss"] - losses[-1]) / losses[-1])
+    # the same schedule run directly (the single-job kernel, 256-thread CTAs): the
+    # reference for how far FP32 rounding alone carries this trajectory
+    eng = Engine(c.m, c.s, nominal, c.R, c.lambda_um, c.dk_per_um, c.edge)
+    eng.set_hparams(lr=dict(object=0.5))
+    eng.load(stack, init=True)
+    for e in range(2):
+        perm = S.epoch_permutation(c.n_leds, c.seed, e)
+        nfull = c.n_leds // c.B
+        eng.run(perm[:nfull * c.B].reshape(nfull, c.B))
+        if c.n_leds % c.B:
+            eng.step(perm[nfull * c.B:])
+    record("serving.direct.m128.object", rel_l2(eng.get()["object"], rec.O))
+    eng.close()
     assert err <= 1e-3, err
     assert abs(st[0]["loss"] - losses[-1]) <= 1e-4 * losses[-1]
 
