@@ -303,7 +303,7 @@ def serving_jobs(n_jobs: int, rate_hz: float, seed: int, shape=None):
     return jobs
 
 
-def serving_run(jobs, budget: int, max_active: int, admission: str = "arrival", grouping: str = "size"):
+def serving_run(jobs, budget: int, max_active: int, admission: str = "arrival", grouping: str = "config"):
     from paper_2408_13782_gb300 import serve as sv
     srv = sv.Server(budget, max_active, admission, grouping)
     ids, st, wall = sv.run_arrivals(srv, [(d, s, t) for d, s, t, _, _ in jobs])
@@ -352,7 +352,7 @@ def serving_section(n_jobs=100, rate_hz=40.0, seed=5):
     runs = {"continuous": serving_run(jobs, budget, max_active=64),
             "continuous_smallest_first": serving_run(jobs, budget, max_active=64, admission="smallest"),
             "continuous_8_active": serving_run(jobs, budget, max_active=8),
-            "continuous_group_by_config": serving_run(jobs, budget, max_active=64, grouping="config"),
+            "continuous_group_by_size": serving_run(jobs, budget, max_active=64, grouping="size"),
             "continuous_sizes_mixed": serving_run(jobs, budget, max_active=64, grouping="mixed"),
             "serial": serving_run(jobs, budget, max_active=1)}
     same = serving_jobs(16, 1000.0, seed + 1, shape=(512, 11))
@@ -364,8 +364,8 @@ def serving_section(n_jobs=100, rate_hz=40.0, seed=5):
     return {"what": f"{n_jobs} jobs, Poisson arrivals {rate_hz:g}/s, ROI from {{256,512,1024,2048}}^2 at "
                     "upsample 4, LED grids {7,11,15}^2, stop at relative epoch-loss change < 1e-4 or 40 epochs; "
                     "continuous batching (jobs admitted by device-memory footprint, overlapping; jobs with "
-                    "the same steps per epoch stepped together in one launch per step, grouped by low-res size "
-                    "(default), by kernel configuration, or with sizes 64/128/256 mixed in one launch; admission "
+                    "the same steps per epoch stepped together in one launch per step, grouped by kernel "
+                    "configuration (default), by low-res size, or with sizes 64/128/256 mixed in one launch; admission "
                     "in arrival order or smallest expected work first; at most 64 or 8 resident) vs the same "
                     "jobs one at a time (FCFS) on the same GPU",
             "mix_counts": mix, "hbm_budget_bytes": budget, **runs,

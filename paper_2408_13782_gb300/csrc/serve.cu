@@ -89,7 +89,7 @@ struct fpm_server {
   int64_t budget = 0, used = 0;
   int max_active = 0;
   int admission = FPM_ADMIT_ARRIVAL;
-  int grouping = FPM_GROUP_SIZE;
+  int grouping = FPM_GROUP_CONFIG;
   std::deque<Job*> queue;
   std::vector<Job*> active;
   std::map<int64_t, std::unique_ptr<Job>> jobs;

@@ -84,7 +84,7 @@ GROUPING = {"config": 0, "size": 1, "mixed": 2}
 
 class Server:
     def __init__(self, hbm_budget_bytes: int, max_active: int = 64, admission: str = "arrival",
-                 grouping: str = "size"):
+                 grouping: str = "config"):
         L = lib()
         _declare(L)
         h = ctypes.c_void_p()

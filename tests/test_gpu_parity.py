@@ -86,6 +86,38 @@ def test_gradients_builtin_loss(m, loss):
         assert v <= TOL_G, (k, v)
 
 
+@pytest.mark.parametrize("R", [56.0, 63.0])
+def test_m256_boxes_on_both_sides_of_the_pruned_form(R):
+    """m = 256 in the per-LED cluster kernel with box half-widths h = 58 (the
+    pruned transforms, h < 64) and h = 65 (full transforms): forward
+    intensities, both losses' gradients and one step against the oracle."""
+    c, I, g, prm, O = multiparam_problem(m=256, grid=3, pitch=32.0, R=R, seed=21)
+    eng = engine_for(g)
+    assert eng.box == 2 * (int(np.floor(R + 0.5 + np.sqrt(2.0))) + 1) + 1
+    eng.load(I, init=False)
+    push(eng, O, prm)
+    idx = np.arange(g.n_leds)
+    err = rel_l2(eng.forward(idx), orc.forward(O, prm, g, idx))
+    record(f"forward.m256.R{R:g}", err)
+    assert err <= TOL_I
+    b = [4, 0, 7]
+    for loss in ("amplitude", "intensity"):
+        eng.set_hparams(loss=loss)
+        got = eng.backward(b)
+        L, ref, _ = orc.loss_and_grad(O, prm, g, b, I.astype(np.float64), loss)
+        assert abs(got["loss"] - L) <= TOL_I * L
+        for k, v in _grad_errors(f"m256.R{R:g}.{loss}", got, ref, b, g.n_leds).items():
+            assert v <= TOL_G, (loss, k, v)
+    hp = orc.Hparams(lr=dict(object=0.5, zernike=0.01, defocus=0.1, gamma=0.01, offset=0.01),
+                     learn=("object", "zernike", "defocus", "gamma", "offset"))
+    hparams_to_engine(eng, hp)
+    push(eng, O, prm)
+    rec = orc.Reconstruction(g, I, hp, O0=O, prm=prm)
+    L_ref = rec.step(b)
+    assert abs(eng.step(b) - L_ref) <= TOL_I * L_ref
+    assert rel_l2(eng.get()["object"], rec.O) <= TOL_G
+
+
 def test_gradients_upstream():
     c, I, g, prm, O = multiparam_problem(m=64, seed=9)
     eng = engine_for(g)

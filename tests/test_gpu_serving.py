@@ -27,7 +27,7 @@ def _job(N, grid, seed, max_epochs=6, rel_tol=0.0, c=None):
     return c, desc, stack
 
 
-def _serve(jobs, budget=8 << 30, max_active=16, grouping="size"):
+def _serve(jobs, budget=8 << 30, max_active=16, grouping="config"):
     srv = sv.Server(budget, max_active, grouping=grouping)
     ids, st, wall = sv.run_arrivals(srv, [(d, s, t) for (c, d, s), t in jobs])
     res = [srv.result(i, c.N, c.n_leds) for i, ((c, d, s), t) in zip(ids, jobs)]
