@@ -197,6 +197,42 @@ def test_grouping_policies_give_the_same_results():
     srv.close()
 
 
+def test_served_job_with_a_learned_pupil_field():
+    """A job that learns the free-form pupil field beside the object runs the
+    field's instantiation of the serving launches (same-configuration and
+    mixed-size); both equal a direct engine run of its schedule bit for bit
+    (m = 64: the same CTA layout in all three)."""
+    c = S.serving_job_config(256, 7, 48)
+    nominal, truth = S.led_grid(c.grid, c.pitch, c.jitter, c.seed)
+    eng = Engine(c.m, c.s, truth, c.R, c.lambda_um, c.dk_per_um, c.edge)
+    eng.set_object_field(S.make_object(c.N, c.seed))
+    stack = eng.forward(np.arange(c.n_leds))
+    eng.close()
+    lr = dict(object=0.5, pupil=0.02)
+    desc = sv.job_desc(c.m, c.s, nominal, c.R, c.lambda_um, c.dk_per_um, c.edge, batch=c.B, max_epochs=3,
+                       rel_tol=0.0, seed=c.seed, lr=lr, learn=("object", "pupil"))
+    res = {}
+    for pol in ("config", "mixed"):
+        st, r = _serve([((c, desc, stack), 0.0)], grouping=pol)
+        assert st[0]["state"] == sv.JOB_DONE and st[0]["epochs"] == 3
+        res[pol] = r[0]["object"]
+    eng = Engine(c.m, c.s, nominal, c.R, c.lambda_um, c.dk_per_um, c.edge)
+    eng.set_hparams(lr=lr, learn=("object", "pupil"))
+    eng.load(stack, init=True)
+    for e in range(3):
+        perm = S.epoch_permutation(c.n_leds, c.seed, e)
+        nfull = c.n_leds // c.B
+        eng.run(perm[:nfull * c.B].reshape(nfull, c.B))
+        if c.n_leds % c.B:
+            eng.step(perm[nfull * c.B:])
+    O = eng.get()["object"]
+    P, on = eng.get_pupil()
+    eng.close()
+    assert on and np.max(np.abs(P - 1)) > 1e-4          # the field moved
+    assert np.array_equal(res["config"], O)
+    assert np.array_equal(res["mixed"], O)
+
+
 def test_mixed_size_job_equals_the_oracle():
     """An m = 128 job served in a mixed-size round (beside an m = 256 job)
     against the FP64 oracle's reconstruction on the same schedule. The object
