@@ -11,17 +11,17 @@
 // CTA r of the cluster owns a slice of box columns (phases A and C) and a
 // slice of image rows (phase B). T / U live in the owners' shared memory and
 // are gathered / scattered through distributed shared memory in phase B.
-// The CTA's slice of O (a disk holding every support, one contiguous run per
-// box column) and its rows of the measured image are copied into shared memory
-// at the start by bulk copies (the TMA engine) that complete on two mbarriers,
-// so each kernel exposes global-memory latency about once.
+// The CTA's slice of O (support pixels only) and its rows of the measured
+// image are copied into shared memory with cp.async at the start, so each
+// kernel exposes global-memory latency about once. (Bulk copies on mbarriers
+// gave the same kernel time and a step window longer by 0.6-1 us beside the
+// update kernel's prologue, so the per-thread form stays.)
 #include <cooperative_groups.h>
 
 #include "../../include/fpm.h"
 #include "device.cuh"
 #include "internal.h"
 #include "pixel.cuh"
-#include "tc.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -62,9 +62,9 @@ struct LedLayout {
   static size_t bytes(int W) {
     const int chunk = (W + C - 1) / C;
     return sizeof(float) * (size_t)ROWS * M +
-           sizeof(float2) * ((size_t)chunk * TS + (size_t)NG * FS + M + NTW2 + (size_t)chunk * (W + 1) + 1 +
-                             (PUSH ? (size_t)RS * W + 1 : 0)) +   // + 1s: 16-byte alignment of O and the staging rows
-           sizeof(float) * (NPOLY + 14 * 15 + 2 + (size_t)NW * NACC) + sizeof(double) * 16 + sizeof(uint64_t) * 2;
+           sizeof(float2) * ((size_t)chunk * TS + (size_t)NG * FS + M + NTW2 + (size_t)chunk * W +
+                             (PUSH ? (size_t)RS * W + 1 : 0)) +   // + 1: 16-byte alignment of the staging rows
+           sizeof(float) * (NPOLY + 14 * 15 + 2 + (size_t)NW * NACC) + sizeof(double) * 16;
   }
 };
 
@@ -84,10 +84,6 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
-
-// Bound of the waits for the prologue's bulk copies (a wait that gives up sets
-// DERR_TIMEOUT; the host reports FPM_ERR_TIMEOUT).
-constexpr unsigned long long LED_WAIT_NS = 200000000ull;
 
 // Programmatic dependent launch: let the next kernel in the stream be
 // scheduled early / wait here until the previous kernel's writes are visible.
@@ -134,19 +130,14 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k, const in
   float2* fb = T + (size_t)chunk * TS;                    // [NG][FS] transform buffers
   float2* tws = fb + NG * FS;                             // [M] twiddle table
   float2* tw2 = tws + M;                                  // [15][16] second-pass twiddles (M = 256)
-  // [chunk][WS] O on this CTA's box columns (16-byte aligned for the bulk copies;
-  // the even stride WS and a shift of one element keep each column's run on
-  // 16-byte boundaries in both memories)
-  const int WS = W + 1;
-  float2* Ob = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(tw2 + L::NTW2) + 15) & ~(uintptr_t)15);
+  float2* Ob = tw2 + L::NTW2;                             // [chunk][W] O on this CTA's box columns
   // [W][RS] this CTA's rows of T by box column (push form), 16-byte aligned
-  float2* Rw = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(Ob + (size_t)chunk * WS) + 15) & ~(uintptr_t)15);
+  float2* Rw = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(Ob + (size_t)chunk * W) + 15) & ~(uintptr_t)15);
   float* poly = L::PUSH ? reinterpret_cast<float*>(Rw + (size_t)L::RS * W)      // K[15] Dx[10] Dy[10]
-                        : reinterpret_cast<float*>(Ob + (size_t)chunk * WS);
+                        : reinterpret_cast<float*>(Ob + (size_t)chunk * W);
   float* zmt = poly + L::NPOLY;                           // [14 * 15] Zernike -> monomial table
   float* red = zmt + 14 * 15 + 2;                         // [NW][NACC]
   double* dsum = reinterpret_cast<double*>(red + NW * NACC);  // [16] (8-byte aligned: float counts are even)
-  uint64_t* bar = reinterpret_cast<uint64_t*>(dsum + 16);     // [2] mbarriers: O slice, image rows
 
   const int tid = threadIdx.x;
   const int4 slot = a.slot[k];  // (LED, crop row, crop col): one load gives every address
@@ -172,52 +163,25 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k, const in
   // and row ky of it sits at offset N/2 + n_row + ky
   const size_t col0 = (size_t)(N / 2 + slot.z - h);
   const int row0 = N / 2 + slot.y;
-  // element (column cl, box row r) of the O slice sits at Ob[cl * WS + sh + r]:
-  // sh is the parity of the box's first spectrum row, so an element has the
-  // same parity (16-byte position) in global and shared memory (N, WS even)
-  const int sh = (row0 - h) & 1;
+  {
+    // O on a disk that contains the support for every admissible delta
+    // (|delta| <= sqrt(2) * bound), so the copy does not wait for delta
+    const float rs = (a.hard_edge ? a.R : a.R + 0.5f) + 1.41422f * FPM_OFFSET_BOUND_PX + 1e-3f;
+    const int ncol = c1 > c0 ? c1 - c0 : 0;
+    for (int q = tid; q < ncol * W; q += NT) {
+      const int cl = q / W, r = q - cl * W;
+      const float px = (float)(c0 + cl - h), py = (float)(r - h);
+      if (px * px + py * py <= rs * rs)
+        cp_async8(Ob + q, a.Ot + (col0 + c0 + cl) * N + (row0 - h + r));
+    }
+  }
+  cp_async_commit();  // group 1: O (needed by phase A)
+  // group 2: this CTA's image rows (needed by phase B), arriving during phase A
   const bool fwd_only = a.mode == MODE_FORWARD || a.mode == MODE_FORWARD_STORE;
   const bool stored = a.mode == MODE_UPSTREAM_STORED;  // psi comes from memory: no inverse transforms
   const float* rows_src = a.mode == MODE_LOSS ? a.meas + ((size_t)led * M + y0) * M
                         : (a.mode == MODE_UPSTREAM || stored) ? a.dLdI + ((size_t)k * M + y0) * M : nullptr;
-  // the image rows go by one bulk copy when the caller's rows are 16-byte
-  // aligned (always for the stack; an upstream dL/dI may be a view), else by cp.async
-  const bool bulk_rows = rows_src && ((reinterpret_cast<uintptr_t>(rows_src) & 15) == 0);
-  if (tid == 0) {
-    // O on a disk that contains the support for every admissible delta
-    // (|delta| <= sqrt(2) * bound), so the copy does not wait for delta: per
-    // box column one run of rows [r0, r1], rounded out to 16-byte boundaries
-    // (an even number of elements). Rows 0 and W - 1 are never in a support
-    // (h exceeds the disk's radius), so the rounding may step back from them.
-    const float rs = (a.hard_edge ? a.R : a.R + 0.5f) + 1.41422f * FPM_OFFSET_BOUND_PX + 1e-3f;
-    const int ncol = c1 > c0 ? c1 - c0 : 0;
-    tc::mbar_init(bar, 1);
-    tc::mbar_init(bar + 1, 1);
-    tc::mbar_fence_init();
-    uint32_t bytes = 0;
-    for (int pass = 0; pass < 2; ++pass) {
-      if (pass == 1) tc::mbar_expect_tx(bar, bytes);  // arrives once: the phase completes with the bytes
-      for (int cl = 0; cl < ncol; ++cl) {
-        const float px = (float)(c0 + cl - h), d2 = rs * rs - px * px;
-        if (d2 < 0.f) continue;
-        const int d = (int)sqrtf(d2) + 1;  // one row of margin against rounding of the disk test
-        int r0 = max(0, h - d), r1 = min(W - 1, h + d);
-        r0 -= (sh + r0) & 1;
-        r1 += (sh + r1 + 1) & 1;
-        if (r0 < 0) r0 += 2;
-        if (r1 > W - 1) r1 -= 2;
-        if (r1 < r0) continue;
-        const uint32_t nb = 8u * (uint32_t)(r1 - r0 + 1);
-        if (pass == 0)
-          bytes += nb;
-        else
-          tc::bulk_g2s(Ob + (size_t)cl * WS + sh + r0, a.Ot + (col0 + c0 + cl) * N + (row0 - h + r0), nb, bar);
-      }
-    }
-    tc::mbar_expect_tx(bar + 1, bulk_rows ? (uint32_t)(sizeof(float) * ROWS * M) : 0u);
-    if (bulk_rows) tc::bulk_g2s(ms, rows_src, (uint32_t)(sizeof(float) * ROWS * M), bar + 1);
-  }
-  if (rows_src && !bulk_rows)  // group 1: this CTA's image rows, arriving during phase A
+  if (rows_src)
     for (int q = tid; q < ROWS * M / 4; q += NT) cp_async16(ms + 4 * q, rows_src + 4 * q);
   cp_async_commit();
   float zc = 0.f;
@@ -235,8 +199,8 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k, const in
   const int grp = tid / G, j = tid % G;
   float2* buf = fb + grp * FS;
   if (tid < 14) red[tid] = zc;   // the aberration coefficients, via the (still unused) reduction area
-  cp_async_wait<1>();  // group 0: the constant tables
-  __syncthreads();     // (also orders the mbarriers' initialisation before every wait on them)
+  cp_async_wait<2>();  // group 0: the constant tables
+  __syncthreads();
   if (tid < 35) poly[tid] = theta_poly_entry_tab(red, zmt, tid);  // aberration phase as monomials of q/R
   FftTw<(M >= 256) ? 128 : M> TW;  // radix-8 path: per-thread twiddles in registers
   __syncthreads();                // twiddle table
@@ -249,14 +213,14 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k, const in
   }
   // the O slice (a wait that gives up flags the launch; the kernel runs on, so
   // the CTA stays resident while the copies could still land)
-  if (!tc::mbar_wait(bar, 0, LED_WAIT_NS) && tid == 0) atomicOr(a.err, DERR_TIMEOUT);
+  cp_async_wait<1>();  // all but the most recent group: the O slice
   __syncthreads();     // O slice in shared memory
 
   // ---------------- phase A: column inverse transforms over ky -------------
   for (int cb = c0; cb < (stored ? c0 : c1); cb += NG) {
     const int c = cb + grp;
     const bool act = c < c1;
-    const float2* Oc = Ob + (size_t)(act ? c - c0 : 0) * WS + sh + h;   // index by ky
+    const float2* Oc = Ob + (size_t)(act ? c - c0 : 0) * W + h;   // index by ky
     const float qx = (float)(c - h) - dlx, qx2 = qx * qx;
     ColPoly cp;  // the aberration phase along this column
     col_poly(qx * P.Rinv, poly, cp);
@@ -300,11 +264,7 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k, const in
     }
     __syncwarp();
   }
-  if (bulk_rows) {  // image rows
-    if (!tc::mbar_wait(bar + 1, 0, LED_WAIT_NS) && tid == 0) atomicOr(a.err, DERR_TIMEOUT);
-  } else {
-    cp_async_wait<0>();
-  }
+  cp_async_wait<0>();  // image rows
   cluster.sync();      // (also a block-wide barrier for the rows)
 
   // ---------------- phase B: rows: psi, residual, adjoint row transform ----
@@ -434,7 +394,7 @@ __device__ __forceinline__ void led_body(const LedArgs& a, const int k, const in
       transform<M, -1>(buf, TW, tws, tw2, j);
     }
     if (act) {
-      const float2* Oc = Ob + (size_t)(c - c0) * WS + sh + h;
+      const float2* Oc = Ob + (size_t)(c - c0) * W + h;
       const float qx = (float)(c - h) - dlx, qx2 = qx * qx;
       ColPoly cp;  // the aberration phase along this column
       col_poly(qx * P.Rinv, poly, cp);
