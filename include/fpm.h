@@ -450,8 +450,8 @@ int fpm_server_set_admission(fpm_server* s, int32_t order);
  *                   LEDs share clusters of 16 CTAs), other sizes as SIZE.
  * A round steps at the pace of its slowest job, so mixing sizes trades the
  * small jobs' time to converge for fewer launches; on a stream of 100 uneven
- * jobs the three policies gave the same throughput within 2 %, CONFIG the
- * lowest median time to converge, MIXED 40 % fewer launches. A job's result does not
+ * jobs the three policies gave the same throughput and median time to converge
+ * within the run-to-run spread, MIXED about 40 % fewer launches. A job's result does not
  * depend on the other jobs of its round; at m = 64 it also equals a direct run
  * bit for bit (the same CTA layout), at m = 128 and 256 within rounding. */
 #define FPM_GROUP_CONFIG 0
