@@ -86,19 +86,19 @@ def test_gradients_builtin_loss(m, loss):
         assert v <= TOL_G, (k, v)
 
 
-@pytest.mark.parametrize("R", [56.0, 63.0])
-def test_m256_boxes_on_both_sides_of_the_pruned_form(R):
+@pytest.mark.parametrize("R,edge", [(56.0, "aa"), (56.0, "hard"), (63.0, "aa")])
+def test_m256_boxes_on_both_sides_of_the_pruned_form(R, edge):
     """m = 256 in the per-LED cluster kernel with box half-widths h = 58 (the
-    pruned transforms, h < 64) and h = 65 (full transforms): forward
-    intensities, both losses' gradients and one step against the oracle."""
-    c, I, g, prm, O = multiparam_problem(m=256, grid=3, pitch=32.0, R=R, seed=21)
+    pruned transforms, h < 64; both pupil edges) and h = 65 (full transforms):
+    forward intensities, both losses' gradients and one step against the oracle."""
+    c, I, g, prm, O = multiparam_problem(m=256, grid=3, pitch=32.0, R=R, edge=edge, seed=21)
     eng = engine_for(g)
     assert eng.box == 2 * (int(np.floor(R + 0.5 + np.sqrt(2.0))) + 1) + 1
     eng.load(I, init=False)
     push(eng, O, prm)
     idx = np.arange(g.n_leds)
     err = rel_l2(eng.forward(idx), orc.forward(O, prm, g, idx))
-    record(f"forward.m256.R{R:g}", err)
+    record(f"forward.m256.R{R:g}.{edge}", err)
     assert err <= TOL_I
     b = [4, 0, 7]
     for loss in ("amplitude", "intensity"):
@@ -106,7 +106,7 @@ def test_m256_boxes_on_both_sides_of_the_pruned_form(R):
         got = eng.backward(b)
         L, ref, _ = orc.loss_and_grad(O, prm, g, b, I.astype(np.float64), loss)
         assert abs(got["loss"] - L) <= TOL_I * L
-        for k, v in _grad_errors(f"m256.R{R:g}.{loss}", got, ref, b, g.n_leds).items():
+        for k, v in _grad_errors(f"m256.R{R:g}.{edge}.{loss}", got, ref, b, g.n_leds).items():
             assert v <= TOL_G, (loss, k, v)
     hp = orc.Hparams(lr=dict(object=0.5, zernike=0.01, defocus=0.1, gamma=0.01, offset=0.01),
                      learn=("object", "zernike", "defocus", "gamma", "offset"))
@@ -366,6 +366,25 @@ def test_global_and_sequential_modes():
         got = eng.run(np.stack(sched))
         assert rel_l2(got, ref) <= 1e-5
         assert rel_l2(eng.get()["object"], rec.O) <= 1e-4
+
+
+def test_global_and_sequential_modes_m256():
+    """Eq. (6) and Eq. (7) on 256-point images (the pruned transforms): one
+    batch of all 9 LEDs, and batches of one, two passes each, every
+    parameter learned, against the oracle."""
+    c, I, g_t, prm, O = multiparam_problem(m=256, grid=3, pitch=32.0, R=50.0, seed=52)
+    hp = orc.Hparams(lr=dict(object=0.5, zernike=0.01, defocus=0.1, gamma=0.01, offset=0.01),
+                     learn=("object", "zernike", "defocus", "gamma", "offset"))
+    for B in (g_t.n_leds, 1):
+        sched = S.schedule(g_t.n_leds, B, 2, seed=3, shuffle=True)
+        rec, eng = _oracle_and_engine(c, I, g_t, hp)
+        ref = rec.run(sched)
+        got = eng.run(np.stack(sched))
+        e_loss, e_obj = rel_l2(got, ref), rel_l2(eng.get()["object"], rec.O)
+        record(f"modes.m256.B{B}.loss", e_loss)
+        record(f"modes.m256.B{B}.object", e_obj)
+        assert e_loss <= 1e-5
+        assert e_obj <= 1e-4
 
 
 # --------------------------------------------------------------------------
