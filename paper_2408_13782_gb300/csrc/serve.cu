@@ -58,6 +58,8 @@ struct Job {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
   double* pinned = nullptr;  // running FP64 loss sum after the epoch in flight
+  int4* h_slots = nullptr;   // pinned: the slot table of the epoch a round is about to run
+  float4* h_coef = nullptr;  // pinned: that epoch's optimiser coefficients per step
   bool in_flight = false;
   int epochs = 0;
   double acc_prev = 0.0, loss = 0.0, loss_prev = -1.0;
@@ -77,8 +79,6 @@ struct Round {
   cudaGraphExec_t exec = nullptr;
   int steps = 0;
   bool mixed = false;            // the mixed-size per-LED launch
-  std::vector<int4*> h_slots;    // pinned, per job: the epoch's slot table
-  std::vector<float4*> h_coef;   // pinned, per job: optimiser coefficients per step
   unsigned char* d_tables = nullptr;  // LedArgs / UpdArgs tables and maps of all steps
   bool in_flight = false;
 };
@@ -94,6 +94,11 @@ struct fpm_server {
   std::vector<Job*> active;
   std::map<int64_t, std::unique_ptr<Job>> jobs;
   std::map<std::string, std::unique_ptr<Round>> rounds;  // by composition
+  // Pinned host buffers, reused across jobs (size classes of powers of two):
+  // freeing pinned memory can wait for the whole device, so blocks go back to
+  // the pool instead and are freed only with the server.
+  std::multimap<size_t, void*> pin_free;
+  std::map<void*, size_t> pin_size;
   int64_t n_rounds = 0, n_round_epochs = 0, max_round_jobs = 0, n_launches = 0;
   int64_t next_id = 1;
   std::chrono::steady_clock::time_point t0;
@@ -117,16 +122,36 @@ int srv_fail(fpm_server* s, int code, const std::string& m) {
   return code;
 }
 
+// A retired round's tables go back to the stream-ordered pool (a plain
+// cudaFree would wait for every other round in flight).
 void destroy_round(Round* r) {
   if (r->stream) cudaStreamSynchronize(r->stream);
   if (r->exec) cudaGraphExecDestroy(r->exec);
-  for (auto p : r->h_slots)
-    if (p) cudaFreeHost(p);
-  for (auto p : r->h_coef)
-    if (p) cudaFreeHost(p);
-  if (r->d_tables) cudaFree(r->d_tables);
+  if (r->d_tables) cudaFreeAsync(r->d_tables, r->stream);
   if (r->ev) cudaEventDestroy(r->ev);
   if (r->stream) cudaStreamDestroy(r->stream);
+}
+
+void* pin_get(fpm_server* s, size_t bytes) {
+  size_t cls = 64;
+  while (cls < bytes) cls <<= 1;
+  auto it = s->pin_free.find(cls);
+  if (it != s->pin_free.end()) {
+    void* p = it->second;
+    s->pin_free.erase(it);
+    return p;
+  }
+  void* p = nullptr;
+  if (cudaMallocHost(&p, cls) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  s->pin_size[p] = cls;
+  return p;
+}
+
+void pin_put(fpm_server* s, void* p) {
+  if (p) s->pin_free.emplace(s->pin_size[p], p);
 }
 
 void forget_rounds_of(fpm_server* s, const Job* j) {
@@ -149,8 +174,12 @@ void release(fpm_server* s, Job* j) {
   j->ev = nullptr;
   if (j->stream) cudaStreamDestroy(j->stream);
   j->stream = nullptr;
-  if (j->pinned) cudaFreeHost(j->pinned);
+  pin_put(s, j->pinned);
+  pin_put(s, j->h_slots);
+  pin_put(s, j->h_coef);
   j->pinned = nullptr;
+  j->h_slots = nullptr;
+  j->h_coef = nullptr;
   s->used -= j->footprint;
 }
 
@@ -178,12 +207,16 @@ int launch_epoch(Job* j) {
 
 int admit(fpm_server* s, Job* j) {
   const fpm_job_desc& d = j->desc;
+  const int steps_per_epoch = (d.geometry.n_leds + d.batch - 1) / d.batch;
   if (cudaStreamCreateWithFlags(&j->stream, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming) != cudaSuccess ||
-      cudaMallocHost(&j->pinned, sizeof(double)) != cudaSuccess) {
+      cudaEventCreateWithFlags(&j->ev, cudaEventDisableTiming) != cudaSuccess) {
     cudaGetLastError();
     return FPM_ERR_CUDA;
   }
+  j->pinned = static_cast<double*>(pin_get(s, sizeof(double)));
+  j->h_slots = static_cast<int4*>(pin_get(s, sizeof(int4) * d.geometry.n_leds));
+  j->h_coef = static_cast<float4*>(pin_get(s, sizeof(float4) * steps_per_epoch));
+  if (!j->pinned || !j->h_slots || !j->h_coef) return FPM_ERR_OOM;
   fpm_geometry g = d.geometry;
   g.led_offset = j->offsets.data();
   int rc = fpm_create(&g, d.pupil_radius_px, d.upsample, j->stream, &j->h);
@@ -281,12 +314,6 @@ int build_round(Round* r, const std::vector<Job*>& js, bool mixed) {
   if (cudaStreamCreateWithFlags(&r->stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&r->ev, cudaEventDisableTiming) != cudaSuccess)
     return FPM_ERR_CUDA;
-  r->h_slots.assign(J, nullptr);
-  r->h_coef.assign(J, nullptr);
-  for (int q = 0; q < J; ++q)
-    if (cudaMallocHost(&r->h_slots[q], sizeof(int4) * js[q]->er.n_leds) != cudaSuccess ||
-        cudaMallocHost(&r->h_coef[q], sizeof(float4) * S) != cudaSuccess)
-      return FPM_ERR_OOM;
   // per step: J LedArgs, J UpdArgs, the per-LED map and the update-CTA map.
   // Same-configuration rounds map each cluster to (job, slot); the mixed
   // launch maps each CTA to (job, slot, rank among the LED's CTAs, m), the
@@ -340,7 +367,7 @@ int build_round(Round* r, const std::vector<Job*>& js, bool mixed) {
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   const size_t o_upd = up(sizeof(LedArgs) * led.size()), o_lmap = o_upd + up(sizeof(UpdArgs) * upd.size());
   const size_t o_umap = o_lmap + up(sizeof(int4) * lm), bytes = o_umap + sizeof(int2) * um;
-  if (cudaMalloc(&r->d_tables, bytes) != cudaSuccess) return FPM_ERR_OOM;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&r->d_tables), bytes, r->stream) != cudaSuccess) return FPM_ERR_OOM;
   LedArgs* d_led = reinterpret_cast<LedArgs*>(r->d_tables);
   UpdArgs* d_upd = reinterpret_cast<UpdArgs*>(r->d_tables + o_upd);
   int4* d_lmap = reinterpret_cast<int4*>(r->d_tables + o_lmap);
@@ -360,21 +387,25 @@ int build_round(Round* r, const std::vector<Job*>& js, bool mixed) {
   std::vector<int2> lpairs;
   if (!r->mixed)
     for (const int4& e : lmaps) lpairs.push_back(make_int2(e.x, e.y));
-  if (cudaMemcpy(d_led, led.data(), sizeof(LedArgs) * led.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(d_upd, upd.data(), sizeof(UpdArgs) * upd.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-      (r->mixed ? cudaMemcpy(d_lmap, lmaps.data(), sizeof(int4) * lm, cudaMemcpyHostToDevice)
-                : cudaMemcpy(d_lmap, lpairs.data(), sizeof(int2) * lm, cudaMemcpyHostToDevice)) != cudaSuccess ||
-      cudaMemcpy(d_umap, umaps.data(), sizeof(int2) * um, cudaMemcpyHostToDevice) != cudaSuccess)
+  // (pageable sources: each copy returns once its source has been staged)
+  const auto up_copy = [&](void* dst, const void* src, size_t n) {
+    return cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, r->stream);
+  };
+  if (up_copy(d_led, led.data(), sizeof(LedArgs) * led.size()) != cudaSuccess ||
+      up_copy(d_upd, upd.data(), sizeof(UpdArgs) * upd.size()) != cudaSuccess ||
+      (r->mixed ? up_copy(d_lmap, lmaps.data(), sizeof(int4) * lm)
+                : up_copy(d_lmap, lpairs.data(), sizeof(int2) * lm)) != cudaSuccess ||
+      up_copy(d_umap, umaps.data(), sizeof(int2) * um) != cudaSuccess)
     return FPM_ERR_CUDA;
   // the graph: schedules and coefficients in, S steps of two launches, losses out
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(r->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return FPM_ERR_CUDA;
   cudaError_t e = cudaSuccess;
   for (int q = 0; q < J && e == cudaSuccess; ++q) {
-    e = cudaMemcpyAsync(js[q]->er.slots, r->h_slots[q], sizeof(int4) * js[q]->er.n_leds, cudaMemcpyHostToDevice,
+    e = cudaMemcpyAsync(js[q]->er.slots, js[q]->h_slots, sizeof(int4) * js[q]->er.n_leds, cudaMemcpyHostToDevice,
                         r->stream);
     if (e == cudaSuccess)
-      e = cudaMemcpyAsync(js[q]->er.coef, r->h_coef[q], sizeof(float4) * S, cudaMemcpyHostToDevice, r->stream);
+      e = cudaMemcpyAsync(js[q]->er.coef, js[q]->h_coef, sizeof(float4) * S, cudaMemcpyHostToDevice, r->stream);
   }
   const int2* d_lpairs = reinterpret_cast<const int2*>(d_lmap);
   for (int st = 0; st < S && e == cudaSuccess; ++st) {
@@ -432,8 +463,8 @@ int launch_round(fpm_server* s, const std::vector<Job*>& js) {
     Job* j = js[q];
     std::vector<int32_t> perm(j->er.n_leds);
     fpm_epoch_permutation(j->er.n_leds, j->desc.seed, j->epochs, perm.data());
-    engine_round_slots(j->h, perm.data(), j->er.n_leds, r->h_slots[q]);
-    engine_round_coef(j->h, r->steps, r->h_coef[q]);
+    engine_round_slots(j->h, perm.data(), j->er.n_leds, j->h_slots);
+    engine_round_coef(j->h, r->steps, j->h_coef);
     if (j->fresh) {  // order the job's load before its first round
       if (cudaStreamWaitEvent(r->stream, j->ev, 0) != cudaSuccess) return FPM_ERR_CUDA;
       j->fresh = false;
@@ -489,6 +520,7 @@ void fpm_server_destroy(fpm_server* s) {
     if (j->stream) cudaStreamSynchronize(j->stream);
   for (auto& kv : s->jobs)
     if (kv.second->state == FPM_JOB_ACTIVE) release(s, kv.second.get());
+  for (auto& kv : s->pin_size) cudaFreeHost(kv.first);
   delete s;
 }
 
