@@ -169,7 +169,7 @@ cudaError_t led_mixed_prepare();
 cudaError_t launch_led_mixed(const LedArgs* jobs, const int4* map, int n_ctas, size_t smem, cudaStream_t s, bool pdl,
                              bool ff);
 cudaError_t launch_update_jobs(const UpdArgs* jobs, const int2* map, int n_ctas, int B_max, cudaStream_t s,
-                               bool pdl);
+                               bool pdl, int opt);  // opt: the optimiser of every job, or -1 if they differ
 int update_ctas(const UpdArgs& a);  // CTAs of one job's update launch
 
 // A handle as seen by the serving loop.

@@ -408,6 +408,9 @@ int build_round(Round* r, const std::vector<Job*>& js, bool mixed) {
       e = cudaMemcpyAsync(js[q]->er.coef, js[q]->h_coef, sizeof(float4) * S, cudaMemcpyHostToDevice, r->stream);
   }
   const int2* d_lpairs = reinterpret_cast<const int2*>(d_lmap);
+  int opt = upd[0].opt;  // one optimiser for the whole round, or -1
+  for (const UpdArgs& ua : upd)
+    if (ua.opt != opt) opt = -1;
   for (int st = 0; st < S && e == cudaSuccess; ++st) {
     if (r->mixed)
       e = launch_led_mixed(d_led + (size_t)st * J, d_lmap + loff[st], (int)lmap[st].size(), smem, r->stream, st > 0,
@@ -417,7 +420,7 @@ int build_round(Round* r, const std::vector<Job*>& js, bool mixed) {
                           r->stream, st > 0, ff);
     if (e == cudaSuccess)
       e = launch_update_jobs(d_upd + (size_t)st * J, d_umap + uoff[st], (int)umap[st].size(), bmax[st], r->stream,
-                             true);
+                             true, opt);
   }
   for (int q = 0; q < J && e == cudaSuccess; ++q)
     e = cudaMemcpyAsync(js[q]->pinned, js[q]->er.epoch, sizeof(double), cudaMemcpyDeviceToHost, r->stream);

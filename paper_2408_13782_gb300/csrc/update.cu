@@ -328,14 +328,16 @@ template <int OPT>
 __global__ void __launch_bounds__(UPD_NT) update_kernel(const UpdArgs a) { update_body<OPT>(a, (int)blockIdx.x); }
 
 // Several jobs in one launch (the serving loop): CTA q is CTA map[q].y of the
-// update of job map[q].x, whose arguments are copied to shared memory.
+// update of job map[q].x, whose arguments are copied to shared memory. OPT:
+// the optimiser every job of the launch uses (Adam), or -1 to branch per job.
+template <int OPT>
 __global__ void __launch_bounds__(UPD_NT) update_kernel_jobs(const UpdArgs* __restrict__ jobs,
                                                              const int2* __restrict__ map) {
   __shared__ UpdArgs sa;
   const int2 q = map[blockIdx.x];
   if (threadIdx.x == 0) sa = jobs[q.x];
   __syncthreads();
-  update_body<-1>(sa, q.y);
+  update_body<OPT>(sa, q.y);
 }
 
 int update_ctas(const UpdArgs& a) { return a.n_cols + NSC + update_decay_ctas(a) + a.pupil_cols; }
@@ -348,12 +350,15 @@ cudaError_t update_prepare() {
                                                cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
   }
-  return cudaFuncSetAttribute(update_kernel_jobs, cudaFuncAttributePreferredSharedMemoryCarveout,
+  const cudaError_t e = cudaFuncSetAttribute(update_kernel_jobs<-1>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                             cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(update_kernel_jobs<FPM_OPT_ADAM>, cudaFuncAttributePreferredSharedMemoryCarveout,
                               cudaSharedmemCarveoutMaxShared);
 }
 
 cudaError_t launch_update_jobs(const UpdArgs* jobs, const int2* map, int n_ctas, int B_max, cudaStream_t s,
-                               bool pdl) {
+                               bool pdl, int opt) {
   if (n_ctas < 1) return cudaErrorInvalidValue;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)n_ctas, 1, 1);
@@ -365,7 +370,8 @@ cudaError_t launch_update_jobs(const UpdArgs* jobs, const int2* map, int n_ctas,
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = pdl ? 1 : 0;
-  return cudaLaunchKernelEx(&cfg, update_kernel_jobs, jobs, map);
+  return opt == FPM_OPT_ADAM ? cudaLaunchKernelEx(&cfg, update_kernel_jobs<FPM_OPT_ADAM>, jobs, map)
+                             : cudaLaunchKernelEx(&cfg, update_kernel_jobs<-1>, jobs, map);
 }
 
 cudaError_t launch_update(const UpdArgs& a, cudaStream_t s, bool pdl) {

@@ -66,6 +66,38 @@ def test_served_job_equals_a_direct_run():
     assert np.array_equal(eng.get()["object"], res[0]["object"])
 
 
+def test_served_jobs_with_other_optimisers_equal_direct_runs():
+    """Rounds whose jobs share Adam use the serving update kernel with the rule
+    fixed at compile time; a round that holds an AdamW job and a NAdam job
+    branches per job. Each served result equals a direct engine run bit for bit."""
+    specs = [("adamw", 0.01, 50), ("nadam", 0.0, 51)]
+    jobs = []
+    for opt, wd, seed in specs:
+        c = S.serving_job_config(256, 7, seed)
+        nominal, truth = S.led_grid(c.grid, c.pitch, c.jitter, c.seed)
+        eng = Engine(c.m, c.s, truth, c.R, c.lambda_um, c.dk_per_um, c.edge)
+        eng.set_object_field(S.make_object(c.N, c.seed))
+        stack = eng.forward(np.arange(c.n_leds))
+        eng.close()
+        desc = sv.job_desc(c.m, c.s, nominal, c.R, c.lambda_um, c.dk_per_um, c.edge, batch=c.B, max_epochs=3,
+                           rel_tol=0.0, seed=c.seed, lr=dict(object=0.5), optimizer=opt, weight_decay=wd)
+        jobs.append(((c, desc, stack), nominal, opt, wd))
+    st, res = _serve([(j[0], 0.0) for j in jobs])
+    for ((c, desc, stack), nominal, opt, wd), r, x in zip(jobs, res, st):
+        assert x["state"] == sv.JOB_DONE and x["epochs"] == 3
+        eng = Engine(c.m, c.s, nominal, c.R, c.lambda_um, c.dk_per_um, c.edge)
+        eng.set_hparams(lr=dict(object=0.5), optimizer=opt, weight_decay=wd)
+        eng.load(stack, init=True)
+        for e in range(3):
+            perm = S.epoch_permutation(c.n_leds, c.seed, e)
+            nfull = c.n_leds // c.B
+            eng.run(perm[:nfull * c.B].reshape(nfull, c.B))
+            if c.n_leds % c.B:
+                eng.step(perm[nfull * c.B:])
+        assert np.array_equal(eng.get()["object"], r["object"]), opt
+        eng.close()
+
+
 def test_served_job_equals_the_oracle():
     """A served job against the FP64 oracle's reconstruction on the same schedule:
     each epoch a fresh permutation (Eq. 13-14), its full batches, then the short one."""
