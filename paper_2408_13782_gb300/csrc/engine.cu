@@ -332,7 +332,7 @@ bool uses_step(const fpm_handle* h) {
 
 int ensure_batch(fpm_handle* h, int B) {
   if (h->hp.precision != FPM_PRECISION_FP32_FFT && h->cap_gscr < B) {
-    const size_t add = h->gp.slot_bytes * (size_t)B;
+    const size_t add = h->gp.slot_bytes * (size_t)h->gp.ncta * (size_t)B;
     if (!mem_fits(h, mem_of(h, h->gscr), add)) return over_limit(h, mem_of(h, h->gscr), add);
     CK(h, dfree(h, h->gscr));
     h->cap_gscr = 0;
@@ -447,7 +447,7 @@ UpdArgs upd_args(fpm_handle* h, const int4* slot_dev, int B, int step_off, doubl
   u.N = h->N;
   u.n_leds = h->n;
   u.B = B;
-  u.C = h->hp.precision != FPM_PRECISION_FP32_FFT ? 1 : h->C;  // partials per LED
+  u.C = h->hp.precision != FPM_PRECISION_FP32_FFT ? h->gp.ncta : h->C;  // partials per LED
   u.h = h->h;
   u.W = h->W;
   u.lr_obj = h->hp.lr_object;
@@ -586,7 +586,7 @@ int fpmk::engine_round_reserve(fpm_handle* h, int n_steps, int B, EngineRound* o
   if ((rc = grow(h, &h->losses, &h->cap_losses, n_steps))) return rc;
   if ((rc = grow(h, &h->coef, &h->cap_coef, n_steps))) return rc;
   out->m = h->m;
-  out->C = h->hp.precision != FPM_PRECISION_FP32_FFT ? 1 : h->C;
+  out->C = h->hp.precision != FPM_PRECISION_FP32_FFT ? h->gp.ncta : h->C;
   out->W = h->W;
   out->n_leds = h->n;
   // rounds group jobs of the per-LED cluster form; a job in the dataflow form

@@ -18,6 +18,11 @@
 // data's rows), steps 2 and 4 put it in B; so every intermediate that leaves
 // tensor memory is one row per thread, written out without a transpose.
 // Data operands go through a per-slot scratch area in global memory (L2).
+// At m = 256 (two row tiles) an LED takes a cluster of two CTAs: each builds
+// half of the box spectrum Phi, then runs steps 1-4 for one row tile; the two
+// tiles' partial sums of step 4 are exchanged through global memory and each
+// CTA finishes the box gradients of half of the box rows.
+#include <cooperative_groups.h>
 #include <cuda_bf16.h>
 
 #include "../../include/fpm.h"
@@ -93,6 +98,7 @@ struct GemmArgs {
   const unsigned char* cst;  // constant DFT factors
   unsigned char* scr;        // per-slot scratch
   int m, Wp, YT, ntile, X, nchunk, ks1, ks3, ks4, ns, kps;
+  int ncta;                  // CTAs per LED: 2 (a cluster, one row tile each) or 1
   size_t aux;
   uint32_t S1, S2, S3, S4, SP, SA, SB, SU, stage;
   size_t c2_base, c3_base, c4_base, slot_bytes, o_phi, o_at, o_bg, o_au, o_spill;
@@ -219,11 +225,13 @@ __global__ void __launch_bounds__(GT, 1) gemm_led_kernel(const GemmArgs g) {
   const int quarter = warp & 3, half = warp >> 2;
   const int row = quarter * 32 + lane;  // the TMEM lane (accumulator row) this thread reads
   const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-  const int k = blockIdx.x;
+  const bool pair = g.ncta == 2;   // (uniform over the launch)
+  const int rank = pair ? (int)cooperative_groups::this_cluster().block_rank() : 0;
+  const int k = blockIdx.x / g.ncta;
   const int4 slot = a.slot[k];
   const int led = slot.x;
-  if (led < 0 || led >= a.n_leds) {
-    if (tid == 0) atomicOr(a.err, DERR_INDEX);
+  if (led < 0 || led >= a.n_leds) {  // the same for both CTAs of a pair: no barrier is left waiting
+    if (tid == 0 && rank == 0) atomicOr(a.err, DERR_INDEX);
     return;
   }
   const int m = g.m, N = a.N, h = a.h, W = a.W, Wp = g.Wp, YT = g.YT, X = g.X;
@@ -258,8 +266,8 @@ __global__ void __launch_bounds__(GT, 1) gemm_led_kernel(const GemmArgs g) {
   if (tid < 35) poly[tid] = theta_poly_entry_tab(red, zmt, tid);
   __syncthreads();
 
-  unsigned char* scr = g.scr + (size_t)k * g.slot_bytes;
-  unsigned char* phi = scr + g.o_phi;
+  unsigned char* scr = g.scr + ((size_t)k * g.ncta + rank) * g.slot_bytes;   // this CTA's operands
+  unsigned char* phi = g.scr + (size_t)k * g.ncta * g.slot_bytes + g.o_phi;  // shared by a pair
   unsigned char* at = scr + g.o_at;
   unsigned char* bg = scr + g.o_bg;
   unsigned char* au = scr + g.o_au;
@@ -296,9 +304,11 @@ __global__ void __launch_bounds__(GT, 1) gemm_led_kernel(const GemmArgs g) {
   tc::cp_async_wait_all();
   __syncthreads();
 
-  // ---- Phi = O x M on the box, as the B operand of step 1 (rows c, K = [Re r | Im r])
-  for (int it = tid; it < Wp * (Wp / 8); it += GT) {
-    const int c = it % Wp, r0 = (it / Wp) * 8;
+  // ---- Phi = O x M on the box, as the B operand of step 1 (rows c, K = [Re r | Im r]);
+  // a pair builds half of the box columns each
+  const int pc = pair ? Wp / 2 : Wp;
+  for (int it = tid; it < pc * (Wp / 8); it += GT) {
+    const int c = rank * pc + it % pc, r0 = (it / pc) * 8;
     const float qx = (float)(c - h) - dlx, qx2 = qx * qx;
     ColPoly cp;  // the aberration phase along column c
     col_poly(qx * P.Rinv, poly, cp);
@@ -318,6 +328,11 @@ __global__ void __launch_bounds__(GT, 1) gemm_led_kernel(const GemmArgs g) {
     }
     put8<TF32, SPLIT>(phi, phi + g.SP, Wp, c, r0, re);
     put8<TF32, SPLIT>(phi, phi + g.SP, Wp, c, Wp + r0, im);
+  }
+
+  if (pair) {  // the other half of Phi, written by the partner, before any bulk copy reads it
+    tc::fence_proxy_async_global();
+    cooperative_groups::this_cluster().sync();
   }
 
   uint32_t q = 0, ngemm = 0;  // ring position (threads 0 and 32), contractions so far
@@ -354,7 +369,8 @@ __global__ void __launch_bounds__(GT, 1) gemm_led_kernel(const GemmArgs g) {
   BoxAcc bacc;
   box_acc_zero(bacc);
   bool ok = true;
-  for (int t = 0; t < g.ntile && ok; ++t) {
+  const int t_lo = pair ? rank : 0, t_hi = pair ? rank + 1 : g.ntile;  // this CTA's row tiles
+  for (int t = t_lo; t < t_hi && ok; ++t) {
     // ---- step 1: T = E Phi for the rows y of this tile (TMEM cols [0, Wp) Re, [128, 128 + Wp) Im)
     {
       Call c{};
@@ -476,11 +492,24 @@ __global__ void __launch_bounds__(GT, 1) gemm_led_kernel(const GemmArgs g) {
       c.dcol[0] = 256;
       c.id = tc::idesc(FMT, 128, 2 * Wp);
       c.accum = 0;
-      if (t == g.ntile - 1) fetch_box();  // lands while step 4 runs
+      if (t == t_hi - 1) fetch_box();  // lands while step 4 runs
       ok = run(c);
       tc::cp_async_wait_all();
       __syncthreads();
       if (!ok) break;
+    }
+    if (pair) {  // the partner's half of the box rows, this tile's part, to this CTA's scratch row
+      for (int r0 = (1 - rank) * (Wp / 2) + half * 8; r0 < (2 - rank) * (Wp / 2); r0 += 16) {
+        float re[8], im[8];
+        tc::tmem_ld8(tbase + lane_off + 256u + (uint32_t)r0, re);
+        tc::tmem_ld8(tbase + lane_off + 256u + (uint32_t)(Wp + r0), im);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          spill[r0 + e] = re[e];
+          spill[Wp + r0 + e] = im[e];
+        }
+      }
+      continue;  // this CTA's own half is finished after the exchange below
     }
     // box column c = row: sum over tiles (in this thread's scratch row), then
     // the object and pupil-parameter gradients per box pixel
@@ -530,9 +559,51 @@ __global__ void __launch_bounds__(GT, 1) gemm_led_kernel(const GemmArgs g) {
     }
   }
 
+  if (pair && a.mode != MODE_FORWARD) {
+    // both CTAs reach this barrier whatever happened above (a wait that gave up
+    // only skips work), then each adds the partner's part of its half of the
+    // box rows and finishes their box gradients
+    __threadfence();
+    cooperative_groups::this_cluster().sync();
+    const float* other = reinterpret_cast<const float*>(g.scr + ((size_t)k * 2 + (1 - rank)) * g.slot_bytes +
+                                                        g.o_spill) + (size_t)row * 2 * Wp;
+    const int c = row;
+    const bool mine = ok && c < W;  // (the tensor-memory loads below are warp-wide: every lane runs them)
+    const float2* Oc = ob + (mine ? c : 0) * W;
+    const float qx = (float)(c - h) - dlx, qx2 = qx * qx;
+    ColPoly cp;  // the aberration phase along column c
+    col_poly(qx * P.Rinv, poly, cp);
+    float S[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    float2* gb = a.gbox + ((size_t)k * W + (mine ? c : 0)) * W;
+    for (int r0 = rank * (Wp / 2) + half * 8; r0 < (rank + 1) * (Wp / 2); r0 += 16) {
+      float re[8], im[8];
+      tc::tmem_ld8(tbase + lane_off + 256u + (uint32_t)r0, re);
+      tc::tmem_ld8(tbase + lane_off + 256u + (uint32_t)(Wp + r0), im);
+      if (!mine) continue;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        re[e] += __ldcg(other + r0 + e);
+        im[e] += __ldcg(other + Wp + r0 + e);
+      }
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int r = r0 + e;
+        if (r >= W) continue;
+        const float qy = (float)(r - h) - dly, r2 = fmaf(qy, qy, qx2);
+        float2 out = make_float2(0.f, 0.f);
+        float rad;
+        const float A = pupil_amp_r2(r2, P, rad);
+        if (A > 0.f)
+          out = box_pixel_col(qy, qx, r2, A, rad, make_float2(re[e] * inv_m2, im[e] * inv_m2), Oc[r], P, cp, zdef,
+                              S, bacc);
+        gb[r] = out;
+      }
+    }
+    if (mine) col_fold(cp, S, bacc);
+  }
   if (ok && a.mode != MODE_FORWARD)
     write_partials(acc_loss, acc_g, bacc, a.mode == MODE_LOSS && a.loss == 0, sg, red, reinterpret_cast<float*>(dsum), zmt,
-                   a.part + (size_t)k * NPART);
+                   a.part + ((size_t)k * g.ncta + rank) * NPART);
   tc::fence_before_sync();
   __syncthreads();
   if (warp == 0) {
@@ -620,6 +691,7 @@ int gemm_plan(int m, int W, int h, int prec, GemmPlan* p, const char** why) {
   p->ntile = m / p->YT;
   p->X = m < 128 ? m : 128;
   p->nchunk = m / p->X;
+  p->ncta = p->ntile == 2 ? 2 : 1;  // one row tile per CTA of a pair
   const int KE = 32 / p->e;  // K elements per K-step
   p->ks1 = 2 * Wp / KE;
   p->ks3 = 2 * p->X / KE;
@@ -771,16 +843,28 @@ cudaError_t launch_led_gemm(const GemmPlan& p, const LedArgs& a, const unsigned 
   g.o_bg = p.o_bg;
   g.o_au = p.o_au;
   g.o_spill = p.o_spill;
+  g.ncta = p.ncta;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)a.B, 1, 1);
+  cfg.gridDim = dim3((unsigned)(a.B * p.ncta), 1, 1);
   cfg.blockDim = dim3(GT, 1, 1);
   cfg.dynamicSmemBytes = p.smem;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute attr[2];
+  int na = 0;
+  if (p.ncta > 1) {
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = (unsigned)p.ncta;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+  }
+  if (pdl) {
+    attr[na].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[na].val.programmaticStreamSerializationAllowed = 1;
+    ++na;
+  }
   cfg.attrs = attr;
-  cfg.numAttrs = pdl ? 1 : 0;
+  cfg.numAttrs = na;
   if (p.tf32) {
     if (p.split) return cudaLaunchKernelEx(&cfg, gemm_led_kernel<true, true>, g);
     return cudaLaunchKernelEx(&cfg, gemm_led_kernel<true, false>, g);

@@ -208,6 +208,7 @@ struct GemmPlan {
   size_t SP = 0, SA = 0, SB = 0, SU = 0;     // one hi copy of each data operand
   size_t o_phi = 0, o_at = 0, o_bg = 0, o_au = 0, o_spill = 0, slot_bytes = 0;
   int ns = 0, kps = 0;                       // pipeline stages, K-steps per stage
+  int ncta = 1;                              // CTAs per LED (a cluster of 2 at m = 256), scratch slots per LED
   size_t stage = 0, aux = 0, smem = 0;       // stage bytes, staging area of per-pixel inputs
 };
 
